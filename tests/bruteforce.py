@@ -1,0 +1,291 @@
+"""Brute-force restatements of the paper's definitions, for tiny hypergraphs.
+
+These pin the oracle to the mathematics: every function here works on the
+ORIGINAL neurons and axons (Sec. 2) with Python sets, and shares no code and
+no formulation shortcut with the oracle. A super-node is just its set of
+member neurons; a partition of level-l vertices is judged by the neurons it
+holds.
+
+* Conn            - Eq. connectivity, from the distinct partitions of each axon.
+* constraints     - Sec. 3: |p| <= Omega, |union in(n)| <= Delta,
+                    sum |in(n)| <= Phi, evaluated on member neurons.
+* score / overlap - Eq. neigh_histogram: summed weight of axons that touch both
+                    super-nodes; |in(n) & in(m)| on original axons.
+* matching        - the recursive characterisation of Eq. matching, memoised.
+* refinement      - a move's gain is the Conn it removes; a prefix's updated
+                    gains are Conn differences after each move; validity is a
+                    direct constraint check of every partition.
+"""
+from __future__ import annotations
+
+import functools
+import itertools
+
+import numpy as np
+
+
+def hedges(hg):
+    """Original axons as (src, frozenset(dsts), weight); axons with no
+    destination never reach the partitioner's objective or limits."""
+    out = []
+    for a in range(hg.E):
+        p = hg.pins[hg.off[a]:hg.off[a + 1]].tolist()
+        out.append((p[0], frozenset(p[1:]), int(hg.w[a])))
+    return out
+
+
+def in_sets(hg):
+    """in(n): axons having n as a destination (Sec. 2)."""
+    ins = [set() for _ in range(hg.V)]
+    for a, (s, d, w) in enumerate(hedges(hg)):
+        for q in d:
+            ins[q].add(a)
+    return ins
+
+
+def conn(hg, rho0):
+    """Eq. connectivity on the original hypergraph."""
+    tot = 0
+    for s, d, w in hedges(hg):
+        parts = {int(rho0[s])} | {int(rho0[q]) for q in d}
+        tot += w * (len(parts) - 1)
+    return tot
+
+
+def group_ok(hg, neurons, prm, ins=None):
+    """Sec. 3 limits for one core holding ``neurons``."""
+    ins = ins if ins is not None else in_sets(hg)
+    if len(neurons) > prm.omega:
+        return False
+    if sum(len(ins[q]) for q in neurons) > prm.phi:
+        return False
+    u = set()
+    for q in neurons:
+        u |= ins[q]
+    return len(u) <= prm.delta
+
+
+def feasible(hg, rho0, prm):
+    ins = in_sets(hg)
+    groups = {}
+    for n in range(hg.V):
+        groups.setdefault(int(rho0[n]), []).append(n)
+    return all(group_ok(hg, g, prm, ins) for g in groups.values())
+
+
+def members(cid_chain, V0):
+    """Level-l vertex -> set of original neurons, from cid maps 0..l-1."""
+    img = np.arange(V0)
+    for cid in cid_chain:
+        img = np.asarray(cid)[img]
+    VL = int(img.max()) + 1 if V0 else 0
+    mem = [set() for _ in range(VL)]
+    for q in range(V0):
+        mem[int(img[q])].add(q)
+    return img, mem
+
+
+def level_state(hg, img, mem):
+    """size, inpins, in_count, in_internal of each super-node, from members."""
+    ins = in_sets(hg)
+    size = [len(m) for m in mem]
+    inpins = [sum(len(ins[q]) for q in m) for m in mem]
+    in_count = []
+    for m in mem:
+        u = set()
+        for q in m:
+            u |= ins[q]
+        in_count.append(len(u))
+    internal = [0] * len(mem)
+    for s, d, w in hedges(hg):
+        if not d:
+            continue
+        pins = {int(img[s])} | {int(img[q]) for q in d}
+        if len(pins) == 1:
+            internal[int(img[s])] += 1
+    return size, inpins, in_count, internal
+
+
+def coarse_hedges(hg, img):
+    """Coarse hyperedges as sorted (s, selfdst, D, w, k) from the images of
+    the original axons that still span two super-nodes."""
+    groups = {}
+    for s, d, w in hedges(hg):
+        if not d:
+            continue
+        s2 = int(img[s])
+        dimg = {int(img[q]) for q in d}
+        D = tuple(sorted(dimg - {s2}))
+        if not D:
+            continue
+        key = (s2, int(s2 in dimg), D)
+        g = groups.setdefault(key, [0, 0])
+        g[0] += w
+        g[1] += 1
+    return sorted((k[0], k[1], k[2], v[0], v[1]) for k, v in groups.items())
+
+
+def score_ov(hg, img):
+    """score(n, m) and |in(n) & in(m)| for every ordered pair of distinct
+    super-nodes that share an axon."""
+    sc, ov = {}, {}
+    for s, d, w in hedges(hg):
+        if not d:
+            continue
+        pins = {int(img[s])} | {int(img[q]) for q in d}
+        dimg = {int(img[q]) for q in d}
+        for n in pins:
+            for m in pins:
+                if n != m:
+                    sc[(n, m)] = sc.get((n, m), 0) + w
+        for n in dimg:
+            for m in dimg:
+                if n != m:
+                    ov[(n, m)] = ov.get((n, m), 0) + 1
+    return sc, ov
+
+
+def candidates(hg, img, mem, prm):
+    """cand(n) by argmax over valid neighbours, ties to the lower id; the
+    merged super-node's limits are checked on the union of members."""
+    sc, ov = score_ov(hg, img)
+    ins = in_sets(hg)
+    VL = len(mem)
+    cand = [-1] * VL
+    cscore = [0] * VL
+    cov = [0] * VL
+    for n in range(VL):
+        best = None
+        for m in range(VL):
+            if m == n or (n, m) not in sc:
+                continue
+            if not group_ok(hg, mem[n] | mem[m], prm, ins):
+                continue
+            key = (sc[(n, m)], -m)
+            if best is None or key > best:
+                best = key
+        if best is not None:
+            m = -best[1]
+            cand[n], cscore[n], cov[n] = m, sc[(n, m)], ov.get((n, m), 0)
+    return cand, cscore, cov
+
+
+def matching(cand, cscore):
+    """Eq. matching, evaluated literally by memoised recursion."""
+    V = len(cand)
+    children = [[] for _ in range(V)]
+    for m in range(V):
+        if cand[m] >= 0:
+            children[cand[m]].append(m)
+
+    @functools.lru_cache(maxsize=None)
+    def M(n):
+        c = cand[n]
+        if c >= 0 and (cand[c] == n or M(c) == n):
+            return c
+        if children[n]:
+            return max(children[n], key=lambda m: (cscore[m], -m))
+        return -1
+
+    return [M(n) for n in range(V)]
+
+
+def refine_round(hg, img, VL, rho, K, prm):
+    """One refinement round on level-l vertices (``img`` maps neurons to
+    them). Returns (new rho, n_props, istar, gain)."""
+    ins = in_sets(hg)
+    mem = [set() for _ in range(VL)]
+    for q in range(hg.V):
+        mem[int(img[q])].add(q)
+    rho = list(rho)
+
+    def proj(r):
+        return [r[int(img[q])] for q in range(hg.V)]
+
+    def part_neurons(r, p):
+        s = set()
+        for n in range(VL):
+            if r[n] == p:
+                s |= mem[n]
+        return s
+
+    base = conn(hg, proj(rho))
+    props = []
+    for n in range(VL):
+        best = None
+        for p in range(K):
+            if p == rho[n]:
+                continue
+            if not group_ok(hg, part_neurons(rho, p) | mem[n], prm, ins):
+                continue
+            r2 = list(rho)
+            r2[n] = p
+            g = base - conn(hg, proj(r2))
+            if best is None or (g, -p) > best:
+                best = (g, -p)
+        if best is not None and best[0] > 0:
+            props.append((n, rho[n], -best[1], best[0]))
+    props.sort(key=lambda t: (-t[3], t[0]))
+    cur = list(rho)
+    c0 = base
+    G, bestG, istar = 0, 0, 0
+    for i, (n, f, t, _) in enumerate(props):
+        cur[n] = t
+        c1 = conn(hg, proj(cur))
+        G += c0 - c1
+        c0 = c1
+        valid = all(group_ok(hg, part_neurons(cur, p), prm, ins) for p in set(cur))
+        if valid and G > 0 and G > bestG:
+            bestG, istar = G, i + 1
+    out = list(rho)
+    for n, f, t, _ in props[:istar]:
+        out[n] = t
+    return out, len(props), istar, bestG
+
+
+def set_partitions(V):
+    """All partitions of range(V) as restricted growth strings."""
+    def rec(i, a, mx):
+        if i == V:
+            yield list(a)
+            return
+        for b in range(mx + 2):
+            a.append(b)
+            yield from rec(i + 1, a, max(mx, b))
+            a.pop()
+    yield from rec(0, [], -1)
+
+
+def optimum(hg, prm):
+    """Exhaustive minimum of Eq. connectivity over feasible partitions."""
+    best = None
+    for rho in set_partitions(hg.V):
+        if not feasible(hg, rho, prm):
+            continue
+        c = conn(hg, rho)
+        if best is None or c < best:
+            best = c
+    return best
+
+
+def components_fit(hg, prm):
+    """True if every connected component of the hypergraph fits one core."""
+    parent = list(range(hg.V))
+
+    def find(x):
+        while parent[x] != x:
+            parent[x] = parent[parent[x]]
+            x = parent[x]
+        return x
+
+    for s, d, w in hedges(hg):
+        for q in d:
+            parent[find(q)] = find(s)
+    comps = {}
+    for n in range(hg.V):
+        comps.setdefault(find(n), set()).add(n)
+    ins = in_sets(hg)
+    return all(group_ok(hg, c, prm, ins) for c in comps.values())
+
+
+__all__ = [n for n in dir() if not n.startswith("_") and n not in ("functools", "itertools", "np")]
