@@ -1,0 +1,227 @@
+/*
+ * snnmap.h - C ABI of the GB300 multilevel hypergraph partitioning pass for
+ * mapping spiking neural networks onto neuromorphic cores.
+ *
+ * The operation is the partitioning problem of Ronzani & Silvano, "GPU-
+ * Accelerated Hypergraph Partitioning and Placement to Map SNNs on
+ * Neuromorphic Hardware", Sec. 3 (Partitioning Definition): given the SNN
+ * hypergraph G = (N, E, omega) of Sec. 2 (one vertex per neuron, one
+ * hyperedge per axon with one source and its destination synapses, omega(e)
+ * the axon's spike frequency) and the per-core limits Omega (neurons),
+ * Delta (distinct inbound axons) and Phi (inbound synapses), find rho : N -> P
+ * that respects the three limits in every partition and keeps the
+ * connectivity Conn = sum_e omega(e) * (lambda(e) - 1) low (Eq. connectivity),
+ * with the multilevel method of Sec. 4.1 (coarsening by constrained matching,
+ * then uncoarsening with prefix-validated refinement).
+ *
+ * Conventions shared by every call:
+ *  - All arithmetic is integer and exact; results are deterministic and do
+ *    not depend on thread scheduling.
+ *  - Pointers named d_* are CUDA device pointers; h_* are host pointers.
+ *    The caller owns every buffer it passes; the library never frees them.
+ *  - stream is a cudaStream_t passed as void*; NULL means the legacy default
+ *    stream. Every call enqueues its work on that stream and synchronizes the
+ *    stream before returning, so outputs are ready on return.
+ *  - Every call returns SNNMAP_OK or one of the SNNMAP_ERR_* codes, and never
+ *    throws; snnmap_last_error() then describes the failure (per thread).
+ *  - A handle is not thread safe: one call at a time per handle.
+ */
+#ifndef SNNMAP_H
+#define SNNMAP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SNNMAP_OK 0
+#define SNNMAP_ERR_INVALID 1        /* malformed input or arguments */
+#define SNNMAP_ERR_INFEASIBLE 2     /* one neuron alone breaks Delta or Phi */
+#define SNNMAP_ERR_OOM 3            /* device or host allocation failed */
+#define SNNMAP_ERR_DEVICE_TIMEOUT 4 /* a bounded device wait ran out */
+#define SNNMAP_ERR_CUDA 5           /* a CUDA runtime call failed */
+#define SNNMAP_ERR_STATE 6          /* call not valid in the handle's state */
+
+/* Per-core limits (Sec. 2, "SNN and Hardware Models"; Sec. 3 constraints)
+ * and stopping rules. */
+typedef struct {
+    int32_t omega;             /* max neurons per core, >= 1 */
+    int32_t delta;             /* max distinct inbound axons per core, >= 0 */
+    int32_t phi;               /* max inbound synapses per core, >= 0 */
+    int32_t max_levels;        /* cap on contractions; coarsening otherwise stops
+                                  when no vertex has a candidate (Sec. 4.1) */
+    int32_t max_refine_rounds; /* cap on refinement rounds per level */
+} snnmap_params;
+
+/* Summary of one snnmap_partition call. */
+typedef struct {
+    int32_t levels;          /* contractions performed */
+    int32_t n_parts;         /* partition ids range over [0, n_parts): the
+                                vertices of the coarsest level */
+    int32_t nonempty_parts;  /* partitions holding at least one neuron */
+    int32_t rounds;          /* refinement rounds that enacted moves */
+    int64_t moves;           /* moves enacted in total */
+    int64_t cost_initial;    /* Conn of the coarsest-level partition */
+    int64_t cost;            /* final Conn (Eq. connectivity) */
+    int64_t pins_total;      /* sum over levels of the pins processed */
+} snnmap_stats;
+
+/* One refinement round's outcome (Sec. 4.1, Uncoarsening and Refinement). */
+typedef struct {
+    int32_t level, round;
+    int32_t n_props;  /* vertices that proposed a move */
+    int32_t istar;    /* length of the enacted prefix (0: none) */
+    int64_t gain;     /* Conn removed by the enacted prefix */
+} snnmap_round_log;
+
+/* One coarsening level (Sec. 4.1, Coarsening). */
+typedef struct {
+    int32_t V, E;
+    int64_t P;
+    int32_t n_cand;   /* vertices with a valid candidate */
+    int32_t n_pairs;  /* matched pairs */
+} snnmap_level_log;
+
+typedef struct snnmap_hgraph snnmap_hgraph;
+
+/* Defaults: max_levels 1024, max_refine_rounds 16; omega/delta/phi as given. */
+snnmap_params snnmap_default_params(int32_t omega, int32_t delta, int32_t phi);
+
+/*
+ * Level 0 of the hierarchy from an SNN hypergraph (Sec. 2).
+ *   n_vertices  neurons, ids 0..n_vertices-1.
+ *   n_hedges    axons.
+ *   d_offsets   int64[n_hedges+1], d_offsets[0] = 0, non-decreasing; axon a's
+ *               pins are d_pins[d_offsets[a] .. d_offsets[a+1]).
+ *   d_pins      int32[d_offsets[n_hedges]]: the first pin of each axon is its
+ *               source neuron, the others its destination neurons, distinct
+ *               and different from the source, in any order.
+ *   d_w         int32[n_hedges], spike frequencies >= 0.
+ * The library copies the input (the caller keeps its buffers) and drops axons
+ * with no destination. Errors: SNNMAP_ERR_INVALID for an axon without pins,
+ * a pin id out of range, a repeated destination, the source listed as a
+ * destination, a negative weight or bad params; SNNMAP_ERR_INFEASIBLE if a
+ * neuron alone has more than Delta inbound axons or Phi inbound synapses.
+ * On success *out receives a new handle; release it with snnmap_free.
+ */
+int snnmap_build_hgraph(const snnmap_params* params, int32_t n_vertices, int32_t n_hedges,
+                        const int64_t* d_offsets, const int32_t* d_pins, const int32_t* d_w,
+                        void* stream, snnmap_hgraph** out);
+
+/*
+ * One coarsening step on the current coarsest level (Sec. 4.1, Coarsening):
+ * the neighbour histogram and candidate of every vertex (Eq.
+ * neigh_histogram: score = summed weight of shared hyperedges, candidates
+ * filtered by Omega, Phi and Delta on the merged inbound set, ties to the
+ * lower id) and the matching of Eq. matching over the candidate
+ * pseudo-forest. *n_cand_out = vertices with a candidate, *n_pairs_out =
+ * matched pairs (0 when no vertex has a candidate: coarsening is over).
+ */
+int snnmap_coarsen_level(snnmap_hgraph* h, void* stream, int32_t* n_cand_out,
+                         int32_t* n_pairs_out);
+
+/*
+ * Materializes the next level from the last snnmap_coarsen_level matching
+ * (Sec. 4.1: each super-node carries size, inbound-axon set size and
+ * inbound pin count; pins are remapped, duplicate pins and duplicate
+ * hyperedges removed, hyperedges inside one super-node dropped).
+ * Outputs the new level's vertex, hyperedge and pin counts.
+ * SNNMAP_ERR_STATE if the last coarsening found no pair.
+ */
+int snnmap_contract(snnmap_hgraph* h, void* stream, int32_t* V_out, int32_t* E_out,
+                    int64_t* P_out);
+
+/* Number of levels held (level 0 is the input) and the sizes of one. */
+int snnmap_num_levels(const snnmap_hgraph* h, int32_t* n_levels);
+int snnmap_level_dims(const snnmap_hgraph* h, int32_t level, int32_t* V, int32_t* E, int64_t* P);
+
+/*
+ * Projection (Sec. 4.1, Uncoarsening): d_rho_fine[n] = d_rho_coarse[cid(n)]
+ * for the vertices n of `level`, cid mapping them to level+1.
+ * d_rho_coarse: int32[V(level+1)], d_rho_fine: int32[V(level)], device.
+ */
+int snnmap_project(snnmap_hgraph* h, int32_t level, const int32_t* d_rho_coarse,
+                   int32_t* d_rho_fine, void* stream);
+
+/*
+ * Refinement of one level (Sec. 4.1, Uncoarsening and Refinement), in place
+ * on d_rho (int32[V(level)], device, values in [0, n_parts)). Each round
+ * computes pins(p, e), every vertex's best feasible positive-gain move to an
+ * adjacent partition (gain = save - loss), sorts the moves by decreasing
+ * gain (ties: lower vertex id), recomputes each move's gain as if all earlier
+ * moves were applied, checks Omega/Phi/Delta after every move with signed
+ * events, and enacts the valid prefix of largest positive total gain; rounds
+ * repeat until none enacts a move or max_refine_rounds is reached.
+ * n_parts is the number of partition ids (vertices of the coarsest level).
+ * *cost_out = Conn after refinement. The input must already respect the
+ * limits (SNNMAP_ERR_INVALID otherwise).
+ */
+int snnmap_refine(snnmap_hgraph* h, int32_t level, int32_t n_parts, int32_t* d_rho,
+                  void* stream, int64_t* cost_out);
+
+/*
+ * The whole pass (Sec. 4.1, Fig. partitioning_flow): coarsen and contract
+ * until no candidate remains (or max_levels), one partition per coarsest
+ * vertex, then project and refine level by level down to level 0.
+ * d_rho_out: int32[n_vertices] device output, partition of every neuron.
+ * *cost_out = Conn (Eq. connectivity). stats may be NULL.
+ * The handle's levels beyond 0 are rebuilt by each call.
+ */
+int snnmap_partition(snnmap_hgraph* h, void* stream, int32_t* d_rho_out, int64_t* cost_out,
+                     snnmap_stats* stats);
+
+/*
+ * Convenience for callers holding host arrays: copies the SNN hypergraph
+ * (same layout as snnmap_build_hgraph, host memory) to the device, runs
+ * snnmap_partition and copies the partition back into h_rho_out
+ * (int32[n_vertices], host). Device memory is released before returning.
+ */
+int snnmap_partition_host(const snnmap_params* params, int32_t n_vertices, int32_t n_hedges,
+                          const int64_t* h_offsets, const int32_t* h_pins, const int32_t* h_w,
+                          int32_t* h_rho_out, int64_t* cost_out, snnmap_stats* stats,
+                          void* stream);
+
+/*
+ * Inspection of a level for verification. Every pointer is a device buffer
+ * of the stated size, or NULL to skip that array:
+ *   d_off int64[E+1], d_pins int32[P] (source first, destinations
+ *   ascending), d_w int64[E], d_k int32[E] (original axons merged),
+ *   d_selfdst uint8[E] (some merged axon ends inside the source),
+ *   d_size, d_inpins, d_in_count, d_in_internal int32[V] (super-node state).
+ * Hyperedge order within a level is unspecified.
+ */
+int snnmap_level_copy(const snnmap_hgraph* h, int32_t level, int64_t* d_off, int32_t* d_pins,
+                      int64_t* d_w, int32_t* d_k, uint8_t* d_selfdst, int32_t* d_size,
+                      int32_t* d_inpins, int32_t* d_in_count, int32_t* d_in_internal,
+                      void* stream);
+
+/*
+ * Results of the last snnmap_coarsen_level, device int32/int64[V] buffers or
+ * NULL: candidate (-1: none), its score, the shared inbound count with it,
+ * and the matched partner (-1: unmatched).
+ */
+int snnmap_last_matching(const snnmap_hgraph* h, int32_t* d_cand, int64_t* d_cscore,
+                         int32_t* d_cov, int32_t* d_match, void* stream);
+
+/* cid map of `level` (int32[V(level)] into level+1), device buffer. */
+int snnmap_level_cid(const snnmap_hgraph* h, int32_t level, int32_t* d_cid, void* stream);
+
+/* Logs of the last snnmap_partition (or refine) calls: copies up to cap
+ * entries, *n receives the number available. */
+int snnmap_round_logs(const snnmap_hgraph* h, snnmap_round_log* out, int32_t cap, int32_t* n);
+int snnmap_level_logs(const snnmap_hgraph* h, snnmap_level_log* out, int32_t cap, int32_t* n);
+
+/* Bytes of device memory the handle currently holds. */
+int snnmap_device_bytes(const snnmap_hgraph* h, int64_t* bytes);
+
+void snnmap_free(snnmap_hgraph* h);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* snnmap_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SNNMAP_H */

@@ -1,0 +1,15 @@
+"""GB300-native multilevel hypergraph partitioning for mapping spiking
+neural networks onto neuromorphic cores (Ronzani & Silvano, Sec. 4.1).
+
+The work runs in libsnnmap (hand-written CUDA kernels for sm_103a behind the
+C ABI of include/snnmap.h); this package is its Python binding plus a small
+convenience layer that keeps inputs in torch device tensors.
+"""
+from ._native import (  # noqa: F401
+    Params, Stats, SnnmapError, lib,
+    snnmap_default_params, snnmap_build_hgraph, snnmap_coarsen_level, snnmap_contract,
+    snnmap_num_levels, snnmap_level_dims, snnmap_project, snnmap_refine, snnmap_partition,
+    snnmap_partition_host, snnmap_level_copy, snnmap_last_matching, snnmap_level_cid,
+    snnmap_round_logs, snnmap_level_logs, snnmap_device_bytes, snnmap_free, snnmap_last_error,
+)
+from .api import HGraph, params_for, partition  # noqa: F401

@@ -1,0 +1,233 @@
+"""ctypes binding of libsnnmap (include/snnmap.h): the same entry points,
+argument marshalling only. Every step of the partitioning pass runs in the
+library's CUDA kernels; there is no Python or CPU fallback, and loading
+fails loudly if the library has not been built."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsnnmap.so")
+
+OK, ERR_INVALID, ERR_INFEASIBLE, ERR_OOM, ERR_DEVICE_TIMEOUT, ERR_CUDA, ERR_STATE = range(7)
+
+
+class Params(C.Structure):
+    _fields_ = [("omega", C.c_int32), ("delta", C.c_int32), ("phi", C.c_int32),
+                ("max_levels", C.c_int32), ("max_refine_rounds", C.c_int32)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("levels", C.c_int32), ("n_parts", C.c_int32), ("nonempty_parts", C.c_int32),
+                ("rounds", C.c_int32), ("moves", C.c_int64), ("cost_initial", C.c_int64),
+                ("cost", C.c_int64), ("pins_total", C.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class RoundLog(C.Structure):
+    _fields_ = [("level", C.c_int32), ("round", C.c_int32), ("n_props", C.c_int32),
+                ("istar", C.c_int32), ("gain", C.c_int64)]
+
+
+class LevelLog(C.Structure):
+    _fields_ = [("V", C.c_int32), ("E", C.c_int32), ("P", C.c_int64), ("n_cand", C.c_int32),
+                ("n_pairs", C.c_int32)]
+
+
+class SnnmapError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"snnmap error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+_lock = threading.Lock()
+
+# name -> (restype, argtypes)
+_vp, _i32, _i64 = C.c_void_p, C.c_int32, C.c_int64
+_SIGS = {
+    "snnmap_default_params": (Params, [_i32, _i32, _i32]),
+    "snnmap_build_hgraph": (C.c_int, [C.POINTER(Params), _i32, _i32, _vp, _vp, _vp, _vp,
+                                      C.POINTER(_vp)]),
+    "snnmap_coarsen_level": (C.c_int, [_vp, _vp, C.POINTER(_i32), C.POINTER(_i32)]),
+    "snnmap_contract": (C.c_int, [_vp, _vp, C.POINTER(_i32), C.POINTER(_i32), C.POINTER(_i64)]),
+    "snnmap_num_levels": (C.c_int, [_vp, C.POINTER(_i32)]),
+    "snnmap_level_dims": (C.c_int, [_vp, _i32, C.POINTER(_i32), C.POINTER(_i32), C.POINTER(_i64)]),
+    "snnmap_project": (C.c_int, [_vp, _i32, _vp, _vp, _vp]),
+    "snnmap_refine": (C.c_int, [_vp, _i32, _i32, _vp, _vp, C.POINTER(_i64)]),
+    "snnmap_partition": (C.c_int, [_vp, _vp, _vp, C.POINTER(_i64), C.POINTER(Stats)]),
+    "snnmap_partition_host": (C.c_int, [C.POINTER(Params), _i32, _i32, _vp, _vp, _vp, _vp,
+                                        C.POINTER(_i64), C.POINTER(Stats), _vp]),
+    "snnmap_level_copy": (C.c_int, [_vp, _i32] + [_vp] * 9 + [_vp]),
+    "snnmap_last_matching": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "snnmap_level_cid": (C.c_int, [_vp, _i32, _vp, _vp]),
+    "snnmap_round_logs": (C.c_int, [_vp, _vp, _i32, C.POINTER(_i32)]),
+    "snnmap_level_logs": (C.c_int, [_vp, _vp, _i32, C.POINTER(_i32)]),
+    "snnmap_device_bytes": (C.c_int, [_vp, C.POINTER(_i64)]),
+    "snnmap_free": (None, [_vp]),
+    "snnmap_last_error": (C.c_char_p, []),
+}
+
+
+def lib():
+    """Loads libsnnmap.so; raises if it is missing (build it first)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(
+                    f"{LIB_PATH} is missing: build the CUDA library first "
+                    "(python -c 'import __graft_entry__ as g; g.build()')")
+            L = C.CDLL(LIB_PATH)
+            for name, (res, args) in _SIGS.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+        return _lib
+
+
+def check(rc):
+    if rc != OK:
+        raise SnnmapError(rc, lib().snnmap_last_error().decode())
+    return rc
+
+
+def _p(x):
+    """Device pointer of a torch tensor, or an int address, or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+# --- the C entry points under their own names --------------------------------
+
+def snnmap_default_params(omega, delta, phi):
+    return lib().snnmap_default_params(int(omega), int(delta), int(phi))
+
+
+def snnmap_build_hgraph(params, n_vertices, n_hedges, d_offsets, d_pins, d_w, stream=None):
+    h = C.c_void_p()
+    check(lib().snnmap_build_hgraph(C.byref(params), int(n_vertices), int(n_hedges), _p(d_offsets),
+                                    _p(d_pins), _p(d_w), _stream(stream), C.byref(h)))
+    return h
+
+
+def snnmap_coarsen_level(h, stream=None):
+    nc, npairs = C.c_int32(), C.c_int32()
+    check(lib().snnmap_coarsen_level(h, _stream(stream), C.byref(nc), C.byref(npairs)))
+    return nc.value, npairs.value
+
+
+def snnmap_contract(h, stream=None):
+    V, E, P = C.c_int32(), C.c_int32(), C.c_int64()
+    check(lib().snnmap_contract(h, _stream(stream), C.byref(V), C.byref(E), C.byref(P)))
+    return V.value, E.value, P.value
+
+
+def snnmap_num_levels(h):
+    n = C.c_int32()
+    check(lib().snnmap_num_levels(h, C.byref(n)))
+    return n.value
+
+
+def snnmap_level_dims(h, level):
+    V, E, P = C.c_int32(), C.c_int32(), C.c_int64()
+    check(lib().snnmap_level_dims(h, int(level), C.byref(V), C.byref(E), C.byref(P)))
+    return V.value, E.value, P.value
+
+
+def snnmap_project(h, level, d_rho_coarse, d_rho_fine, stream=None):
+    check(lib().snnmap_project(h, int(level), _p(d_rho_coarse), _p(d_rho_fine), _stream(stream)))
+
+
+def snnmap_refine(h, level, n_parts, d_rho, stream=None):
+    c = C.c_int64()
+    check(lib().snnmap_refine(h, int(level), int(n_parts), _p(d_rho), _stream(stream), C.byref(c)))
+    return c.value
+
+
+def snnmap_partition(h, d_rho_out, stream=None):
+    c = C.c_int64()
+    st = Stats()
+    check(lib().snnmap_partition(h, _stream(stream), _p(d_rho_out), C.byref(c), C.byref(st)))
+    return c.value, st.as_dict()
+
+
+def snnmap_partition_host(params, n_vertices, n_hedges, h_offsets, h_pins, h_w, h_rho_out,
+                          stream=None):
+    """Host buffers: numpy arrays or pinned torch CPU tensors (int64/int32)."""
+    def hp(a):
+        if a is None:
+            return None
+        if hasattr(a, "ctypes"):
+            return a.ctypes.data
+        return a.data_ptr()
+    c = C.c_int64()
+    st = Stats()
+    check(lib().snnmap_partition_host(C.byref(params), int(n_vertices), int(n_hedges),
+                                      hp(h_offsets), hp(h_pins), hp(h_w), hp(h_rho_out),
+                                      C.byref(c), C.byref(st), _stream(stream)))
+    return c.value, st.as_dict()
+
+
+def snnmap_level_copy(h, level, d_off=None, d_pins=None, d_w=None, d_k=None, d_selfdst=None,
+                      d_size=None, d_inpins=None, d_in_count=None, d_in_internal=None,
+                      stream=None):
+    check(lib().snnmap_level_copy(h, int(level), _p(d_off), _p(d_pins), _p(d_w), _p(d_k),
+                                  _p(d_selfdst), _p(d_size), _p(d_inpins), _p(d_in_count),
+                                  _p(d_in_internal), _stream(stream)))
+
+
+def snnmap_last_matching(h, d_cand=None, d_cscore=None, d_cov=None, d_match=None, stream=None):
+    check(lib().snnmap_last_matching(h, _p(d_cand), _p(d_cscore), _p(d_cov), _p(d_match),
+                                     _stream(stream)))
+
+
+def snnmap_level_cid(h, level, d_cid, stream=None):
+    check(lib().snnmap_level_cid(h, int(level), _p(d_cid), _stream(stream)))
+
+
+def snnmap_round_logs(h):
+    n = C.c_int32()
+    check(lib().snnmap_round_logs(h, None, 0, C.byref(n)))
+    buf = (RoundLog * max(1, n.value))()
+    check(lib().snnmap_round_logs(h, buf, n.value, C.byref(n)))
+    return [{f: getattr(buf[i], f) for f, _ in RoundLog._fields_} for i in range(n.value)]
+
+
+def snnmap_level_logs(h):
+    n = C.c_int32()
+    check(lib().snnmap_level_logs(h, None, 0, C.byref(n)))
+    buf = (LevelLog * max(1, n.value))()
+    check(lib().snnmap_level_logs(h, buf, n.value, C.byref(n)))
+    return [{f: getattr(buf[i], f) for f, _ in LevelLog._fields_} for i in range(n.value)]
+
+
+def snnmap_device_bytes(h):
+    b = C.c_int64()
+    check(lib().snnmap_device_bytes(h, C.byref(b)))
+    return b.value
+
+
+def snnmap_free(h):
+    if h:
+        lib().snnmap_free(h)
+
+
+def snnmap_last_error():
+    return lib().snnmap_last_error().decode()

@@ -1,0 +1,131 @@
+"""Convenience layer over the C ABI: device tensors from torch, a handle
+object that frees itself, and one-call partitioning."""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import _native as N
+
+
+def params_for(omega, delta, phi, max_levels=1024, max_refine_rounds=16) -> N.Params:
+    return N.Params(int(omega), int(delta), int(phi), int(max_levels), int(max_refine_rounds))
+
+
+def to_device(hg, device="cuda"):
+    """(off, pins, w) of a snngen.Hypergraph as device tensors."""
+    off = torch.from_numpy(np.ascontiguousarray(hg.off, np.int64)).to(device)
+    pins = torch.from_numpy(np.ascontiguousarray(hg.pins, np.int32)).to(device)
+    w = torch.from_numpy(np.ascontiguousarray(hg.w, np.int32)).to(device)
+    return off, pins, w
+
+
+class HGraph:
+    """Owns an snnmap handle built from device tensors."""
+
+    def __init__(self, params, V, off, pins, w, stream=None):
+        self.V = int(V)
+        self.params = params
+        self.stream = stream
+        self._h = N.snnmap_build_hgraph(params, V, off.shape[0] - 1, off, pins, w, stream)
+
+    @classmethod
+    def from_hypergraph(cls, hg, params=None, device="cuda", stream=None, **kw):
+        off, pins, w = to_device(hg, device)
+        params = params or params_for(hg.omega, hg.delta, hg.phi, **kw)
+        return cls(params, hg.V, off, pins, w, stream)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            N.snnmap_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def partition(self, rho_out=None):
+        if rho_out is None:
+            rho_out = torch.empty(self.V, dtype=torch.int32, device="cuda")
+        cost, stats = N.snnmap_partition(self._h, rho_out, self.stream)
+        return rho_out, cost, stats
+
+    def coarsen_level(self):
+        return N.snnmap_coarsen_level(self._h, self.stream)
+
+    def contract(self):
+        return N.snnmap_contract(self._h, self.stream)
+
+    def num_levels(self):
+        return N.snnmap_num_levels(self._h)
+
+    def level_dims(self, level):
+        return N.snnmap_level_dims(self._h, level)
+
+    def level_arrays(self, level):
+        """Copies of one level's arrays as host numpy arrays."""
+        V, E, P = self.level_dims(level)
+        dev = "cuda"
+        t = {
+            "off": torch.empty(E + 1, dtype=torch.int64, device=dev),
+            "pins": torch.empty(max(P, 1), dtype=torch.int32, device=dev),
+            "w": torch.empty(max(E, 1), dtype=torch.int64, device=dev),
+            "k": torch.empty(max(E, 1), dtype=torch.int32, device=dev),
+            "selfdst": torch.empty(max(E, 1), dtype=torch.uint8, device=dev),
+            "size": torch.empty(max(V, 1), dtype=torch.int32, device=dev),
+            "inpins": torch.empty(max(V, 1), dtype=torch.int32, device=dev),
+            "in_count": torch.empty(max(V, 1), dtype=torch.int32, device=dev),
+            "in_internal": torch.empty(max(V, 1), dtype=torch.int32, device=dev),
+        }
+        N.snnmap_level_copy(self._h, level, t["off"], t["pins"], t["w"], t["k"], t["selfdst"],
+                            t["size"], t["inpins"], t["in_count"], t["in_internal"], self.stream)
+        sizes = {"off": E + 1, "pins": P, "w": E, "k": E, "selfdst": E, "size": V, "inpins": V,
+                 "in_count": V, "in_internal": V}
+        out = {k: v.cpu().numpy()[:sizes[k]] for k, v in t.items()}
+        out.update(V=V, E=E, P=P)
+        return out
+
+    def last_matching(self):
+        V = self.level_dims(self.num_levels() - 1)[0]
+        t = [torch.empty(max(V, 1), dtype=d, device="cuda")
+             for d in (torch.int32, torch.int64, torch.int32, torch.int32)]
+        N.snnmap_last_matching(self._h, *t, stream=self.stream)
+        return [x.cpu().numpy()[:V] for x in t]
+
+    def level_cid(self, level):
+        V = self.level_dims(level)[0]
+        t = torch.empty(max(V, 1), dtype=torch.int32, device="cuda")
+        N.snnmap_level_cid(self._h, level, t, self.stream)
+        return t.cpu().numpy()[:V]
+
+    def refine(self, level, n_parts, rho):
+        return N.snnmap_refine(self._h, level, n_parts, rho, self.stream)
+
+    def project(self, level, rho_coarse, rho_fine):
+        N.snnmap_project(self._h, level, rho_coarse, rho_fine, self.stream)
+
+    def round_logs(self):
+        return N.snnmap_round_logs(self._h)
+
+    def level_logs(self):
+        return N.snnmap_level_logs(self._h)
+
+    def device_bytes(self):
+        return N.snnmap_device_bytes(self._h)
+
+
+def partition(hg, device="cuda", **kw):
+    """One call: build from a snngen.Hypergraph, partition, return (rho numpy,
+    cost, stats)."""
+    g = HGraph.from_hypergraph(hg, device=device, **kw)
+    try:
+        rho, cost, stats = g.partition()
+        return rho.cpu().numpy(), cost, stats
+    finally:
+        g.close()

@@ -1,0 +1,380 @@
+// Level 0 of the hierarchy (the SNN hypergraph of Sec. 2) and the per-level
+// helpers every stage shares: size buckets, incidence lists, level memory.
+#include "internal.cuh"
+
+namespace snn {
+
+// ---------------------------------------------------------------------------
+// scalars
+
+Status read_scalars(snnmap_hgraph* h)
+{
+    SNN_CUDA(cudaMemcpyAsync(h->h_scal, h->d_scal, SC_COUNT * sizeof(int64_t),
+                             cudaMemcpyDeviceToHost, h->stream));
+    SNN_CUDA(cudaStreamSynchronize(h->stream));
+    return Status{};
+}
+
+Status zero_scalars(snnmap_hgraph* h)
+{
+    SNN_CUDA(cudaMemsetAsync(h->d_scal, 0, SC_COUNT * sizeof(int64_t), h->stream));
+    return Status{};
+}
+
+// ---------------------------------------------------------------------------
+// level memory
+
+Status level_alloc(snnmap_hgraph* h, Level& L, LevelExtra& X, int32_t V, int32_t E, int64_t P)
+{
+    Carver c;
+    L.V = V;
+    L.E = E;
+    L.P = P;
+    c.add(&L.hoff, (int64_t)E + 1);
+    c.add(&L.hpins, P);
+    c.add(&L.hw, E);
+    c.add(&L.hk, E);
+    c.add(&L.hsd, E);
+    c.add(&L.voff, (int64_t)V + 1);
+    c.add(&L.vinc, P);
+    c.add(&L.vsize, V);
+    c.add(&L.vinpins, V);
+    c.add(&L.vincnt, V);
+    c.add(&L.vinint, V);
+    c.add(&L.cid, V);
+    c.add(&X.seg.list, E);
+    c.add(&X.seg.meta, 8);
+    void* p = nullptr;
+    SNN_CUDA(cudaMallocAsync(&p, c.total, h->stream));
+    c.assign(p);
+    L.block = p;
+    L.bytes = c.total;
+    return Status{};
+}
+
+void level_free(snnmap_hgraph* h, Level& L)
+{
+    if (L.block) cudaFreeAsync(L.block, h->stream);
+    L = Level{};
+}
+
+// ---------------------------------------------------------------------------
+// size buckets
+
+__device__ __forceinline__ int seg_bucket(int64_t len)
+{
+    return len <= 32 ? 0 : (len <= SEG_B1_CAP ? 1 : (len <= SEG_B2_CAP ? 2 : 3));
+}
+
+__global__ void k_seg_flags(const int64_t* __restrict__ hoff, int32_t E, int64_t* pa, int64_t* pb)
+{
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < E;
+         a += (int64_t)gridDim.x * blockDim.x) {
+        int b = seg_bucket(hoff[a + 1] - hoff[a]);
+        pa[a] = (int64_t)(b == 0) | ((int64_t)(b == 1) << 32);
+        pb[a] = (int64_t)(b == 2) | ((int64_t)(b == 3) << 32);
+    }
+}
+
+__global__ void k_seg_meta(const int64_t* ta, const int64_t* tb, int32_t* meta)
+{
+    int32_t c0 = (int32_t)(*ta & 0xffffffff), c1 = (int32_t)(*ta >> 32);
+    int32_t c2 = (int32_t)(*tb & 0xffffffff), c3 = (int32_t)(*tb >> 32);
+    meta[0] = 0;
+    meta[1] = c0;
+    meta[2] = c0 + c1;
+    meta[3] = c0 + c1 + c2;
+    meta[4] = c0;
+    meta[5] = c1;
+    meta[6] = c2;
+    meta[7] = c3;
+}
+
+__global__ void k_seg_scatter(const int64_t* __restrict__ hoff, int32_t E,
+                              const int64_t* __restrict__ pa, const int64_t* __restrict__ pb,
+                              const int32_t* __restrict__ meta, int32_t* list)
+{
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < E;
+         a += (int64_t)gridDim.x * blockDim.x) {
+        int b = seg_bucket(hoff[a + 1] - hoff[a]);
+        int64_t pos = b == 0 ? (pa[a] & 0xffffffff)
+                    : b == 1 ? (pa[a] >> 32)
+                    : b == 2 ? (pb[a] & 0xffffffff)
+                             : (pb[a] >> 32);
+        list[meta[b] + pos] = (int32_t)a;
+    }
+}
+
+Status seg_classify(const int64_t* hoff, int32_t E, int32_t maxlen, SegBuckets& b, Arena& ar,
+                    cudaStream_t s)
+{
+    int64_t *pa, *pb, *tot;
+    SNN_TRY(ar.alloc(&pa, E));
+    SNN_TRY(ar.alloc(&pb, E));
+    SNN_TRY(ar.alloc(&tot, 2));
+    b.b3_cap = 0;
+    if (maxlen > SEG_B2_CAP) {
+        int64_t c = SEG_B2_CAP;
+        while (c < maxlen) c <<= 1;
+        b.b3_cap = c;
+    }
+    if (E > 0) {
+        k_seg_flags<<<grid_for(E, 256), 256, 0, s>>>(hoff, E, pa, pb);
+        SNN_CUDA(cudaGetLastError());
+    }
+    SNN_TRY(scan_exclusive_i64(pa, pa, E, tot, ar, s));
+    SNN_TRY(scan_exclusive_i64(pb, pb, E, tot + 1, ar, s));
+    k_seg_meta<<<1, 1, 0, s>>>(tot, tot + 1, b.meta);
+    SNN_CUDA(cudaGetLastError());
+    if (E > 0) {
+        k_seg_scatter<<<grid_for(E, 256), 256, 0, s>>>(hoff, E, pa, pb, b.meta, b.list);
+        SNN_CUDA(cudaGetLastError());
+    }
+    return Status{};
+}
+
+// ---------------------------------------------------------------------------
+// incidence lists: degree count, scan, scatter with the source bit
+
+__global__ void k_count_deg(const int32_t* __restrict__ pins, int64_t P, int32_t* deg)
+{
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < P;
+         j += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&deg[pins[j]], 1);
+}
+
+__global__ void k_csc_fill(const int64_t* __restrict__ hoff, const int32_t* __restrict__ pins,
+                           int32_t E, const int64_t* __restrict__ voff, int32_t* cursor,
+                           int32_t* vinc)
+{
+    int lane = threadIdx.x & 31;
+    int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t a = gw; a < E; a += nw) {
+        int64_t b = hoff[a], e = hoff[a + 1];
+        for (int64_t j = b + lane; j < e; j += 32) {
+            int32_t q = pins[j];
+            int32_t slot = atomicAdd(&cursor[q], 1);
+            vinc[voff[q] + slot] = (int32_t)((uint32_t)a | (j == b ? SRC_BIT : 0u));
+        }
+    }
+}
+
+Status build_incidence(snnmap_hgraph* h, Level& L)
+{
+    cudaStream_t s = h->stream;
+    Arena& ar = h->scratch;
+    int32_t *deg, *cursor;
+    SNN_TRY(ar.alloc(&deg, L.V));
+    SNN_TRY(ar.alloc(&cursor, L.V));
+    if (L.V > 0) {
+        SNN_CUDA(cudaMemsetAsync(deg, 0, (size_t)L.V * sizeof(int32_t), s));
+        SNN_CUDA(cudaMemsetAsync(cursor, 0, (size_t)L.V * sizeof(int32_t), s));
+    }
+    if (L.P > 0) {
+        k_count_deg<<<grid_for(L.P, 256), 256, 0, s>>>(L.hpins, L.P, deg);
+        SNN_CUDA(cudaGetLastError());
+    }
+    SNN_TRY(scan_exclusive_i32_to_i64(deg, L.voff, L.V, L.voff + L.V, ar, s));
+    if (L.E > 0) {
+        k_csc_fill<<<grid_for((int64_t)L.E * 32, 256), 256, 0, s>>>(L.hoff, L.hpins, L.E, L.voff,
+                                                                    cursor, L.vinc);
+        SNN_CUDA(cudaGetLastError());
+    }
+    return Status{};
+}
+
+// ---------------------------------------------------------------------------
+// S0: validation, copy, canonical destination order, vertex state
+
+__global__ void k_in_hedges(const int64_t* __restrict__ off, const int32_t* __restrict__ w,
+                            int32_t E, int32_t* kept, int64_t* klen, int64_t* scal)
+{
+    int32_t bad = 0;
+    int64_t mx = 0, wsum = 0;
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < E;
+         a += (int64_t)gridDim.x * blockDim.x) {
+        int64_t len = off[a + 1] - off[a];
+        if (len < 1 || len > 0x7fffffff || w[a] < 0) bad = 1;
+        int k = len >= 2 ? 1 : 0;
+        kept[a] = k;
+        klen[a] = k ? len : 0;
+        if (len > mx) mx = len;
+        wsum += w[a] > 0 ? w[a] : 0;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        int64_t m2 = __shfl_xor_sync(FULL, mx, o);
+        mx = m2 > mx ? m2 : mx;
+        wsum += __shfl_xor_sync(FULL, wsum, o);
+        bad |= __shfl_xor_sync(FULL, bad, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (bad) atomicOr((int*)&scal[SC_STATUS], ST_INVALID);
+        atomicMax((unsigned long long*)&scal[SC_C], (unsigned long long)mx);
+        atomicAdd((unsigned long long*)&scal[SC_D], (unsigned long long)wsum);
+    }
+}
+
+__global__ void k_in_pins(const int32_t* __restrict__ pins, int64_t P, int32_t V, int64_t* scal)
+{
+    int bad = 0;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < P;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        int32_t q = pins[j];
+        if (q < 0 || q >= V) bad = 1;
+    }
+    if (__any_sync(FULL, bad) && (threadIdx.x & 31) == 0) atomicOr((int*)&scal[SC_STATUS], ST_INVALID);
+}
+
+__global__ void k_copy_hedges(const int64_t* __restrict__ off, const int32_t* __restrict__ pins,
+                              const int32_t* __restrict__ w, int32_t E,
+                              const int32_t* __restrict__ kept, const int32_t* __restrict__ newid,
+                              const int64_t* __restrict__ newoff, Level L)
+{
+    int lane = threadIdx.x & 31;
+    int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t a = gw; a < E; a += nw) {
+        if (!kept[a]) continue;
+        int32_t e = newid[a];
+        int64_t src = off[a], dst = newoff[a], len = off[a + 1] - off[a];
+        for (int64_t j = lane; j < len; j += 32) L.hpins[dst + j] = pins[src + j];
+        if (lane == 0) {
+            L.hoff[e] = dst;
+            L.hw[e] = w[a];
+            L.hk[e] = 1;
+            L.hsd[e] = 0;
+        }
+    }
+}
+
+__global__ void k_set_last_off(int64_t* hoff, int32_t E, const int64_t* P)
+{
+    hoff[E] = *P;
+}
+
+// Sorts each hyperedge's destinations in place and flags repeated
+// destinations and the source listed as a destination.
+struct BuildCheckJob {
+    const int64_t* hoff;
+    int32_t* pins;
+    int64_t* scal;
+    __device__ int len(int32_t a) const { return (int)(hoff[a + 1] - hoff[a] - 1); }
+    __device__ uint32_t load(int32_t a, int i) const { return (uint32_t)pins[hoff[a] + 1 + i]; }
+    __device__ void finish(int32_t a, const uint32_t* s, int n) const
+    {
+        int lane = threadIdx.x & 31;
+        int64_t base = hoff[a];
+        uint32_t src = (uint32_t)pins[base];
+        int bad = 0;
+        for (int c = 0; c < n; c += 32) {
+            int i = c + lane;
+            if (i < n) {
+                uint32_t v = s[i];
+                if ((i > 0 && s[i - 1] == v) || v == src) bad = 1;
+                pins[base + 1 + i] = (int32_t)v;
+            }
+        }
+        if (__any_sync(FULL, bad) && lane == 0) atomicOr((int*)&scal[SC_STATUS], ST_INVALID);
+    }
+};
+
+__global__ void k_count_inpins(const int64_t* __restrict__ hoff, const int32_t* __restrict__ pins,
+                               int32_t E, int32_t* inpins)
+{
+    int lane = threadIdx.x & 31;
+    int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t a = gw; a < E; a += nw) {
+        for (int64_t j = hoff[a] + 1 + lane; j < hoff[a + 1]; j += 32) atomicAdd(&inpins[pins[j]], 1);
+    }
+}
+
+__global__ void k_vertex_init(Level L, int32_t delta, int32_t phi, int64_t* scal)
+{
+    int bad = 0;
+    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < L.V;
+         n += (int64_t)gridDim.x * blockDim.x) {
+        int32_t ip = L.vinpins[n];
+        L.vsize[n] = 1;
+        L.vincnt[n] = ip;
+        L.vinint[n] = 0;
+        if (ip > phi || ip > delta) bad = 1;
+    }
+    if (__any_sync(FULL, bad) && (threadIdx.x & 31) == 0)
+        atomicOr((int*)&scal[SC_STATUS], ST_INFEASIBLE);
+}
+
+Status build_level0(snnmap_hgraph* h, int32_t V, int32_t E, const int64_t* d_off,
+                    const int32_t* d_pins, const int32_t* d_w)
+{
+    cudaStream_t s = h->stream;
+    Arena& ar = h->scratch;
+    int64_t ends[2] = {0, 0};
+    SNN_CUDA(cudaMemcpyAsync(&ends[0], d_off, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    SNN_CUDA(cudaMemcpyAsync(&ends[1], d_off + E, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    SNN_CUDA(cudaStreamSynchronize(s));
+    if (ends[0] != 0 || ends[1] < E) return Status{SNNMAP_ERR_INVALID, "offsets: first must be 0 and every hyperedge needs a pin"};
+    int64_t Pin = ends[1];
+    SNN_TRY(zero_scalars(h));
+    int32_t *kept, *newid;
+    int64_t *klen, *newoff;
+    SNN_TRY(ar.alloc(&kept, E));
+    SNN_TRY(ar.alloc(&newid, E));
+    SNN_TRY(ar.alloc(&klen, E));
+    SNN_TRY(ar.alloc(&newoff, E));
+    if (E > 0) {
+        k_in_hedges<<<grid_for(E, 256), 256, 0, s>>>(d_off, d_w, E, kept, klen, h->d_scal);
+        SNN_CUDA(cudaGetLastError());
+    }
+    if (Pin > 0) {
+        k_in_pins<<<grid_for(Pin, 256), 256, 0, s>>>(d_pins, Pin, V, h->d_scal);
+        SNN_CUDA(cudaGetLastError());
+    }
+    SNN_TRY(scan_exclusive_i32(kept, newid, E, (int32_t*)(h->d_scal + SC_A), ar, s));
+    SNN_TRY(scan_exclusive_i64(klen, newoff, E, h->d_scal + SC_B, ar, s));
+    SNN_TRY(read_scalars(h));
+    if (h->h_scal[SC_STATUS] & ST_INVALID)
+        return Status{SNNMAP_ERR_INVALID, "hyperedge without pins, negative weight or pin id out of range"};
+    int32_t E0 = (int32_t)(h->h_scal[SC_A] & 0xffffffff);
+    int64_t P0 = h->h_scal[SC_B];
+    int32_t maxlen = (int32_t)h->h_scal[SC_C];
+    h->wide = (uint64_t)h->h_scal[SC_D] >= 0xffffffffull;
+
+    h->levels.emplace_back();
+    h->extra.emplace_back();
+    Level& L = h->levels.back();
+    LevelExtra& X = h->extra.back();
+    SNN_TRY(level_alloc(h, L, X, V, E0, P0));
+    L.maxlen = maxlen;
+    if (E > 0) {
+        k_copy_hedges<<<grid_for((int64_t)E * 32, 256), 256, 0, s>>>(d_off, d_pins, d_w, E, kept,
+                                                                      newid, newoff, L);
+        SNN_CUDA(cudaGetLastError());
+    }
+    k_set_last_off<<<1, 1, 0, s>>>(L.hoff, E0, h->d_scal + SC_B);
+    SNN_CUDA(cudaGetLastError());
+    SNN_TRY(seg_classify(L.hoff, E0, maxlen, X.seg, ar, s));
+    BuildCheckJob job{L.hoff, L.hpins, h->d_scal};
+    SNN_TRY(seg_run(job, X.seg, E0, ar, s));
+    if (V > 0) SNN_CUDA(cudaMemsetAsync(L.vinpins, 0, (size_t)V * sizeof(int32_t), s));
+    if (E0 > 0) {
+        k_count_inpins<<<grid_for((int64_t)E0 * 32, 256), 256, 0, s>>>(L.hoff, L.hpins, E0, L.vinpins);
+        SNN_CUDA(cudaGetLastError());
+    }
+    if (V > 0) {
+        k_vertex_init<<<grid_for(V, 256), 256, 0, s>>>(L, h->prm.delta, h->prm.phi, h->d_scal);
+        SNN_CUDA(cudaGetLastError());
+    }
+    SNN_TRY(build_incidence(h, L));
+    SNN_TRY(read_scalars(h));
+    h->scratch.reset();
+    if (h->h_scal[SC_STATUS] & ST_INVALID)
+        return Status{SNNMAP_ERR_INVALID, "repeated destination or source listed as a destination"};
+    if (h->h_scal[SC_STATUS] & ST_INFEASIBLE)
+        return Status{SNNMAP_ERR_INFEASIBLE, "a neuron alone exceeds Delta or Phi"};
+    return Status{};
+}
+
+}  // namespace snn

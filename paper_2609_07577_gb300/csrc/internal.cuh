@@ -1,0 +1,76 @@
+// Handle layout and the host-side entry points of each pipeline stage.
+#pragma once
+#include "../../include/snnmap.h"
+#include "common.cuh"
+#include "segsort.cuh"
+
+#include <vector>
+
+namespace snn {
+
+// Device scalar slots (int64) read back by the host at synchronization points.
+enum Scalar : int {
+    SC_STATUS = 0,   // int32 status bits live in the low word of this slot
+    SC_A, SC_B, SC_C, SC_D, SC_E, SC_F, SC_G,
+    SC_COUNT = 16,
+};
+
+struct LevelExtra {
+    SegBuckets seg;     // hyperedge size buckets
+};
+
+}  // namespace snn
+
+struct snnmap_hgraph {
+    snnmap_params prm{};
+    int device = 0;
+    cudaStream_t stream = 0;
+    std::vector<snn::Level> levels;
+    std::vector<snn::LevelExtra> extra;
+    snn::Arena scratch;
+    int64_t* d_scal = nullptr;   // SC_COUNT device slots
+    int64_t* h_scal = nullptr;   // pinned mirror
+    // results of the last coarsening step (for the current coarsest level)
+    int32_t* cand = nullptr;
+    int64_t* cscore = nullptr;
+    int32_t* cov = nullptr;
+    int32_t* match = nullptr;
+    int32_t cap_v = 0;           // capacity of the four arrays above
+    bool have_matching = false;
+    int32_t last_pairs = 0;
+    bool wide = false;           // some neighbour score may reach 2^32
+    std::vector<snnmap_round_log> rlog;
+    std::vector<snnmap_level_log> llog;
+};
+
+namespace snn {
+
+// scalars: copy the SC_COUNT slots device->host and synchronize the stream
+Status read_scalars(snnmap_hgraph* h);
+Status zero_scalars(snnmap_hgraph* h);
+
+// level memory
+Status level_alloc(snnmap_hgraph* h, Level& L, LevelExtra& X, int32_t V, int32_t E, int64_t P);
+void level_free(snnmap_hgraph* h, Level& L);
+
+// S0: level 0 from the caller's arrays
+Status build_level0(snnmap_hgraph* h, int32_t V, int32_t E, const int64_t* d_off,
+                    const int32_t* d_pins, const int32_t* d_w);
+// incidence lists (CSC) of a level whose hoff/hpins are final
+Status build_incidence(snnmap_hgraph* h, Level& L);
+
+// S1 + S2 on the coarsest level: fills h->cand/cscore/cov/match
+Status coarsen_level(snnmap_hgraph* h, int32_t* n_cand, int32_t* n_pairs);
+// S3: next level from h->match
+Status contract_level(snnmap_hgraph* h);
+// S5
+Status project(snnmap_hgraph* h, int32_t level, const int32_t* rho_coarse, int32_t* rho_fine);
+// S6-S12 on one level; rho in place
+Status refine_level(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* rho, int64_t* cost,
+                    int64_t* cost_start);
+// caller-provided rho must index existing partitions
+Status check_rho(snnmap_hgraph* h, int32_t level, int32_t K, const int32_t* rho);
+// S12 alone
+Status level_cost(snnmap_hgraph* h, int32_t level, int32_t K, const int32_t* rho, int64_t* cost);
+
+}  // namespace snn

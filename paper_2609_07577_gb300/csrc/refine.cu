@@ -1,0 +1,1024 @@
+// Uncoarsening and refinement (Sec. 4.1).
+//
+// Projection: rho_l(n) = rho_{l+1}(cid(n)).
+//
+// One refinement round:
+//  S6  pins(p, e): per hyperedge, the sorted keys rho(q)*2 + [q is a
+//      destination] are run-length encoded into (p, cnt, dcnt) entries;
+//      e is inbound to p iff dcnt > 0. Partition state: size, inbound pins,
+//      and distinct inbound axons (internal axons + k of inbound hyperedges).
+//      Conn = sum omega(e) (lambda(e) - 1) comes out of the same pass.
+//  S7  per vertex: save = omega of incident hyperedges where it is its
+//      partition's last pin; for every other adjacent partition p the
+//      connection weight conn(p) (loss = W - conn) and the k of hyperedges
+//      where it is a destination and that are already inbound to p; gain =
+//      save - loss; the best feasible move (ties to the lower p) is proposed
+//      if its gain is positive.
+//  S8  moves sorted by decreasing gain, ties by vertex id (stable radix sort
+//      of compacted proposals, which are in vertex order).
+//  S9  per hyperedge, its moved pins are replayed in move order: each
+//      move's gain contribution omega([cnt(from)=1] - [cnt(to)=0]) is taken
+//      with every earlier move applied, and when a destination leaves the
+//      last / enters the first destination slot of a partition an inbound
+//      event (p, move, -/+k) is emitted. Prefix sums give each prefix's gain.
+//  S10 validity: per partition, its events (size/pins of every move, inbound
+//      events) sorted by move and scanned; after each move that touches the
+//      partition its limits are checked and changes of "violating" are added
+//      to the move's violation delta. A prefix is valid iff the prefix sum of
+//      violation deltas is zero.
+//  S11 the valid prefix with the largest positive gain (shortest on ties) is
+//      enacted.
+#include "histo.cuh"
+#include "internal.cuh"
+
+#include <algorithm>
+#include <climits>
+
+namespace snn {
+
+enum : int {
+    RS_M = SC_A,       // proposals
+    RS_MAXG = SC_B,    // largest proposed gain
+    RS_BEST = SC_C,    // best valid prefix gain
+    RS_ISTAR = SC_D,   // index of its last move
+    RS_COST = SC_E,    // Conn at round start
+    RS_NEV = SC_F,     // inbound events emitted
+    RS_NHV = SC_G,     // hyperedges replayed by the block tier
+    RS_DEG = 8,        // incidences of proposing vertices
+};
+
+constexpr int GAIN_WARPS = 8;
+constexpr int GAIN_T = 512;
+constexpr int GAIN_LOAD = GAIN_T * 3 / 4;
+constexpr int GAIN_BT = 8192;
+constexpr int GAIN_BLOAD = GAIN_BT * 3 / 4;
+constexpr int GAIN_BTHREADS = 256;
+constexpr int REPLAY_WARP_MAX = 32;
+
+struct PinCounts {
+    int32_t* p;
+    int32_t* cnt;
+    int32_t* dcnt;
+    int32_t* lam;
+};
+
+struct PState {
+    int64_t* size;
+    int64_t* inpins;
+    int64_t* pincnt;
+};
+
+// ---------------------------------------------------------------------------
+// S5
+
+__global__ void k_project(int32_t V, const int32_t* __restrict__ cid,
+                          const int32_t* __restrict__ rc, int32_t* rf)
+{
+    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < V;
+         n += (int64_t)gridDim.x * blockDim.x)
+        rf[n] = rc[cid[n]];
+}
+
+Status project(snnmap_hgraph* h, int32_t level, const int32_t* rho_coarse, int32_t* rho_fine)
+{
+    Level& L = h->levels[level];
+    if (L.V > 0) {
+        k_project<<<grid_for(L.V, 256), 256, 0, h->stream>>>(L.V, L.cid, rho_coarse, rho_fine);
+        SNN_CUDA(cudaGetLastError());
+    }
+    return Status{};
+}
+
+// ---------------------------------------------------------------------------
+// S6
+
+struct PinCountJob {
+    const int64_t* hoff;
+    const int32_t* hpins;
+    const uint8_t* hsd;
+    const int32_t* hk;
+    const int64_t* hw;
+    const int32_t* rho;
+    PinCounts pc;
+    int64_t* pincnt;
+    int64_t* scal;
+    __device__ int len(int32_t a) const { return (int)(hoff[a + 1] - hoff[a]); }
+    __device__ uint32_t load(int32_t a, int i) const
+    {
+        int64_t j = hoff[a] + i;
+        uint32_t d = (i > 0 || hsd[a]) ? 1u : 0u;
+        return ((uint32_t)rho[hpins[j]] << 1) | d;
+    }
+    __device__ void finish(int32_t a, const uint32_t* s, int n) const
+    {
+        int lane = threadIdx.x & 31;
+        int64_t base = hoff[a];
+        unsigned le = lanemask_lt() | (1u << lane);
+        int R = 0;
+        // pass 1: run starts (partition changes) and first destination of each run
+        for (int c = 0; c < n; c += 32) {
+            int i = c + lane;
+            bool valid = i < n;
+            uint32_t v = valid ? s[i] : KEY_PAD;
+            uint32_t pv = (valid && i > 0) ? s[i - 1] : KEY_PAD;
+            bool rs = valid && (i == 0 || (v >> 1) != (pv >> 1));
+            bool ds = valid && (v & 1) && (i == 0 || v != pv);
+            unsigned mr = __ballot_sync(FULL, rs);
+            int r = R + __popc(mr & le) - 1;
+            if (rs) {
+                pc.p[base + r] = (int32_t)(v >> 1);
+                pc.cnt[base + r] = i;
+                pc.dcnt[base + r] = -1;
+            }
+            __syncwarp();
+            if (ds) pc.dcnt[base + r] = i;
+            __syncwarp();
+            R += __popc(mr);
+        }
+        // pass 2: starts -> counts
+        for (int c = 0; c < R; c += 32) {
+            int r = c + lane;
+            int st = 0, nx = 0, dsx = -1;
+            if (r < R) {
+                st = pc.cnt[base + r];
+                nx = (r + 1 < R) ? pc.cnt[base + r + 1] : n;
+                dsx = pc.dcnt[base + r];
+            }
+            __syncwarp();
+            if (r < R) {
+                int dc = dsx >= 0 ? nx - dsx : 0;
+                pc.cnt[base + r] = nx - st;
+                pc.dcnt[base + r] = dc;
+                if (dc > 0) atomicAdd((unsigned long long*)&pincnt[pc.p[base + r]], (unsigned long long)hk[a]);
+            }
+            __syncwarp();
+        }
+        if (lane == 0) {
+            pc.lam[a] = R;
+            if (R > 1) atomicAdd((unsigned long long*)&scal[RS_COST], (unsigned long long)(hw[a] * (R - 1)));
+        }
+    }
+};
+
+__global__ void k_pstate_vertices(Level L, const int32_t* __restrict__ rho, PState ps)
+{
+    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < L.V;
+         n += (int64_t)gridDim.x * blockDim.x) {
+        int32_t p = rho[n];
+        atomicAdd((unsigned long long*)&ps.size[p], (unsigned long long)L.vsize[n]);
+        atomicAdd((unsigned long long*)&ps.inpins[p], (unsigned long long)L.vinpins[n]);
+        if (L.vinint[n]) atomicAdd((unsigned long long*)&ps.pincnt[p], (unsigned long long)L.vinint[n]);
+    }
+}
+
+__device__ __forceinline__ bool violates(int64_t sz, int64_t ip, int64_t pc, int32_t omega,
+                                         int32_t delta, int32_t phi)
+{
+    return sz > omega || ip > phi || pc > delta;
+}
+
+__global__ void k_check_pstate(int32_t K, PState ps, int32_t omega, int32_t delta, int32_t phi,
+                               int64_t* scal)
+{
+    int bad = 0;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < K;
+         p += (int64_t)gridDim.x * blockDim.x)
+        if (violates(ps.size[p], ps.inpins[p], ps.pincnt[p], omega, delta, phi)) bad = 1;
+    if (__any_sync(FULL, bad) && (threadIdx.x & 31) == 0) atomicOr((int*)&scal[SC_STATUS], ST_BADSTATE);
+}
+
+// ---------------------------------------------------------------------------
+// S7
+
+template <typename S>
+struct GainVis {
+    const Level& L;
+    const PinCounts& pc;
+    int32_t home;
+    const Table<S>& t;
+    int64_t W = 0, save = 0;
+    __device__ Seg<S> seg(int64_t i)
+    {
+        uint32_t inc = (uint32_t)L.vinc[i];
+        int32_t a = (int32_t)(inc & ~SRC_BIT);
+        Seg<S> g;
+        g.sd = L.hsd[a];
+        g.nd = !(inc & SRC_BIT) || g.sd;
+        g.b = L.hoff[a];
+        g.len = pc.lam[a];
+        g.w = (S)L.hw[a];
+        g.k = (uint32_t)L.hk[a];
+        W += L.hw[a];
+        return g;
+    }
+    __device__ bool elem(const Seg<S>& g, int32_t off)
+    {
+        int64_t e = g.b + off;
+        int32_t p = pc.p[e];
+        if (p == home) {
+            if (pc.cnt[e] == 1) save += (int64_t)g.w;
+            return true;
+        }
+        return t.add(p, g.w, (g.nd && pc.dcnt[e] > 0) ? g.k : 0u);
+    }
+};
+
+template <typename S>
+__device__ void scan_gain(const Table<S>& t, int32_t u0, int32_t nused, int32_t stride,
+                          int64_t base, int64_t sz, int64_t ip, int64_t ic, const PState& ps,
+                          int32_t omega, int32_t delta, int32_t phi, int64_t& bs, int32_t& bm)
+{
+    for (int32_t u = u0; u < nused; u += stride) {
+        int32_t slot = t.used[u];
+        int32_t p = t.key[slot];
+        int64_t conn = (int64_t)t.sc[slot];
+        uint32_t o = t.ov[slot];
+        t.key[slot] = -1;
+        t.sc[slot] = 0;
+        t.ov[slot] = 0;
+        int64_t gain = base + conn;
+        bool feas = ps.size[p] + sz <= omega && ps.inpins[p] + ip <= phi &&
+                    ps.pincnt[p] + ic - (int64_t)o <= delta;
+        if (feas && better(gain, p, bs, bm)) {
+            bs = gain;
+            bm = p;
+        }
+    }
+}
+
+template <typename S>
+__global__ void __launch_bounds__(GAIN_WARPS * 32)
+    k_gain_warp(Level L, PinCounts pc, const int32_t* __restrict__ rho, PState ps, int32_t omega,
+                int32_t delta, int32_t phi, int32_t* pto, int64_t* pgain, int32_t* heavy,
+                int64_t* heavy_slot)
+{
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ int32_t nfill[GAIN_WARPS];
+    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    Table<S> t = carve_table<S>(smem_raw + (size_t)warp * table_bytes<S>(GAIN_T), GAIN_T, &nfill[warp]);
+    for (int i = lane; i < GAIN_T; i += 32) {
+        t.key[i] = -1;
+        t.sc[i] = 0;
+        t.ov[i] = 0;
+    }
+    int64_t gw = blockIdx.x * (int64_t)GAIN_WARPS + warp;
+    int64_t nw = (int64_t)gridDim.x * GAIN_WARPS;
+    for (int64_t n = gw; n < L.V; n += nw) {
+        if (lane == 0) nfill[warp] = 0;
+        __syncwarp();
+        GainVis<S> vis{L, pc, rho[n], t};
+        bool ok = warp_flat_visit<S>(vis, L.voff[n], L.voff[n + 1], 32, &nfill[warp], GAIN_LOAD);
+        __syncwarp();
+        int32_t nused = nfill[warp];
+        if (!ok || nused > GAIN_T) {
+            for (int i = lane; i < GAIN_T; i += 32) {
+                t.key[i] = -1;
+                t.sc[i] = 0;
+                t.ov[i] = 0;
+            }
+            if (lane == 0) {
+                int32_t pos = atomicAdd((int*)heavy_slot, 1);
+                heavy[pos] = (int32_t)n;
+            }
+            __syncwarp();
+            continue;
+        }
+        int64_t W = warp_sum(vis.W), save = warp_sum(vis.save);
+        int64_t bs = 0;
+        int32_t bm = -1;
+        scan_gain<S>(t, lane, nused, 32, save - W, L.vsize[n], L.vinpins[n], L.vincnt[n], ps, omega,
+                     delta, phi, bs, bm);
+        uint32_t dummy = 0;
+        warp_argmax(bs, bm, dummy);
+        if (lane == 0) {
+            bool prop = bm >= 0 && bs > 0;
+            pto[n] = prop ? bm : -1;
+            pgain[n] = prop ? bs : 0;
+        }
+        __syncwarp();
+    }
+}
+
+template <typename S>
+__global__ void __launch_bounds__(GAIN_BTHREADS)
+    k_gain_block(Level L, PinCounts pc, const int32_t* __restrict__ rho, PState ps, int32_t omega,
+                 int32_t delta, int32_t phi, int32_t* pto, int64_t* pgain, const int32_t* list,
+                 const int64_t* count_slot, int32_t* next, int64_t* next_slot, unsigned char* gtab,
+                 int64_t cap)
+{
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ int32_t nfill;
+    __shared__ int sh_fail;
+    __shared__ unsigned long long sW, sSave;
+    __shared__ int64_t rs[GAIN_BTHREADS / 32];
+    __shared__ int32_t rm[GAIN_BTHREADS / 32];
+    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwarps = GAIN_BTHREADS / 32;
+    int64_t tcap = gtab ? cap : GAIN_BT;
+    int32_t limit = gtab ? (int32_t)(cap - 1) : GAIN_BLOAD;
+    Table<S> t = carve_table<S>(gtab ? gtab + (size_t)blockIdx.x * table_bytes<S>(cap) : smem_raw,
+                                (int32_t)tcap, &nfill);
+    if (!gtab) {
+        for (int i = threadIdx.x; i < GAIN_BT; i += GAIN_BTHREADS) {
+            t.key[i] = -1;
+            t.sc[i] = 0;
+            t.ov[i] = 0;
+        }
+    }
+    int32_t cnt = (int32_t)*count_slot;
+    for (int32_t idx = blockIdx.x; idx < cnt; idx += gridDim.x) {
+        int32_t n = list[idx];
+        if (threadIdx.x == 0) {
+            nfill = 0;
+            sh_fail = 0;
+            sW = 0;
+            sSave = 0;
+        }
+        __syncthreads();
+        GainVis<S> vis{L, pc, rho[n], t};
+        bool ok = warp_flat_visit<S>(vis, L.voff[n] + 32 * warp, L.voff[n + 1], 32 * nwarps,
+                                     &nfill, limit);
+        if (!ok) atomicOr(&sh_fail, 1);
+        int64_t w = warp_sum(vis.W), sv = warp_sum(vis.save);
+        if (lane == 0) {
+            atomicAdd(&sW, (unsigned long long)w);
+            atomicAdd(&sSave, (unsigned long long)sv);
+        }
+        __syncthreads();
+        int32_t nused = nfill;
+        if (sh_fail || nused > limit) {
+            for (int64_t i = threadIdx.x; i < tcap; i += GAIN_BTHREADS) {
+                t.key[i] = -1;
+                t.sc[i] = 0;
+                t.ov[i] = 0;
+            }
+            if (threadIdx.x == 0 && next) {
+                int32_t pos = atomicAdd((int*)next_slot, 1);
+                next[pos] = n;
+            }
+            __syncthreads();
+            continue;
+        }
+        int64_t base = (int64_t)sSave - (int64_t)sW;
+        int64_t bs = 0;
+        int32_t bm = -1;
+        scan_gain<S>(t, threadIdx.x, nused, GAIN_BTHREADS, base, L.vsize[n], L.vinpins[n],
+                     L.vincnt[n], ps, omega, delta, phi, bs, bm);
+        uint32_t dummy = 0;
+        warp_argmax(bs, bm, dummy);
+        if (lane == 0) {
+            rs[warp] = bs;
+            rm[warp] = bm;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int w2 = 1; w2 < nwarps; w2++)
+                if (better(rs[w2], rm[w2], bs, bm)) {
+                    bs = rs[w2];
+                    bm = rm[w2];
+                }
+            bool prop = bm >= 0 && bs > 0;
+            pto[n] = prop ? bm : -1;
+            pgain[n] = prop ? bs : 0;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// S8
+
+__global__ void k_prop_stats(Level L, const int32_t* __restrict__ pto,
+                             const int64_t* __restrict__ pgain, int32_t* flag, int64_t* scal)
+{
+    int64_t mg = 0, deg = 0;
+    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < L.V;
+         n += (int64_t)gridDim.x * blockDim.x) {
+        int f = pto[n] >= 0;
+        flag[n] = f;
+        if (f) {
+            mg = pgain[n] > mg ? pgain[n] : mg;
+            deg += L.voff[n + 1] - L.voff[n];
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        int64_t m2 = __shfl_xor_sync(FULL, mg, o);
+        mg = m2 > mg ? m2 : mg;
+        deg += __shfl_xor_sync(FULL, deg, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (mg) atomicMax((unsigned long long*)&scal[RS_MAXG], (unsigned long long)mg);
+        if (deg) atomicAdd((unsigned long long*)&scal[RS_DEG], (unsigned long long)deg);
+    }
+}
+
+__global__ void k_prop_keys(int32_t V, const int32_t* __restrict__ pto,
+                            const int64_t* __restrict__ pgain, const int32_t* __restrict__ pos,
+                            int64_t maxg, uint64_t* keys, uint32_t* vals)
+{
+    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < V;
+         n += (int64_t)gridDim.x * blockDim.x) {
+        if (pto[n] < 0) continue;
+        int32_t i = pos[n];
+        keys[i] = (uint64_t)(maxg - pgain[n]);
+        vals[i] = (uint32_t)n;
+    }
+}
+
+struct Moves {
+    int32_t* n;
+    int32_t* from;
+    int32_t* to;
+};
+
+__global__ void k_moves(int32_t M, const uint32_t* __restrict__ vals, const int32_t* __restrict__ rho,
+                        const int32_t* __restrict__ pto, Moves mv, int32_t* moveidx)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t n = (int32_t)vals[i];
+        mv.n[i] = n;
+        mv.from[i] = rho[n];
+        mv.to[i] = pto[n];
+        moveidx[n] = (int32_t)i;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// S9 / S10 events
+
+struct Events {
+    uint64_t* key;   // partition << ibits | move
+    uint32_t* idx;   // 0..n-1 (sort values)
+    int32_t* dsize;
+    int32_t* dinp;
+    int32_t* dpc;
+    int64_t cap;
+    int ibits;
+};
+
+__global__ void k_size_events(int32_t M, Moves mv, Level L, Events ev)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t n = mv.n[i];
+        int64_t e0 = 2 * i, e1 = 2 * i + 1;
+        ev.key[e0] = ((uint64_t)mv.from[i] << ev.ibits) | (uint64_t)i;
+        ev.key[e1] = ((uint64_t)mv.to[i] << ev.ibits) | (uint64_t)i;
+        ev.idx[e0] = (uint32_t)e0;
+        ev.idx[e1] = (uint32_t)e1;
+        ev.dsize[e0] = -L.vsize[n];
+        ev.dsize[e1] = L.vsize[n];
+        ev.dinp[e0] = -L.vinpins[n];
+        ev.dinp[e1] = L.vinpins[n];
+        ev.dpc[e0] = -L.vinint[n];
+        ev.dpc[e1] = L.vinint[n];
+    }
+}
+
+__device__ __forceinline__ void emit_inbound(const Events& ev, int64_t* scal, int64_t base,
+                                             int32_t p, int32_t mi, int32_t d)
+{
+    int64_t pos = base + (int64_t)atomicAdd((unsigned long long*)&scal[RS_NEV], 1ull);
+    if (pos >= ev.cap) {
+        atomicOr((int*)&scal[SC_STATUS], ST_CAPACITY);
+        return;
+    }
+    ev.key[pos] = ((uint64_t)p << ev.ibits) | (uint64_t)mi;
+    ev.idx[pos] = (uint32_t)pos;
+    ev.dsize[pos] = 0;
+    ev.dinp[pos] = 0;
+    ev.dpc[pos] = d;
+}
+
+// counts of partition p in hyperedge a at round start (entries sorted by p)
+__device__ __forceinline__ void lookup_count(const PinCounts& pc, int64_t b, int32_t lam, int32_t p,
+                                             int32_t& cnt, int32_t& dcnt)
+{
+    int32_t lo = 0, hi = lam;
+    while (lo < hi) {
+        int32_t mid = (lo + hi) >> 1;
+        if (pc.p[b + mid] < p) lo = mid + 1;
+        else hi = mid;
+    }
+    if (lo < lam && pc.p[b + lo] == p) {
+        cnt = pc.cnt[b + lo];
+        dcnt = pc.dcnt[b + lo];
+    } else {
+        cnt = 0;
+        dcnt = 0;
+    }
+}
+
+// one moved pin's replay given the deltas of earlier moves of the same hyperedge
+__device__ __forceinline__ void replay_one(const Level& L, const PinCounts& pc, int32_t a,
+                                           int32_t mi, int32_t f, int32_t t, int d, int dcf_c,
+                                           int dct_c, int dcf_d, int dct_d, int64_t* gp,
+                                           const Events& ev, int64_t* scal, int64_t evbase)
+{
+    int64_t b = L.hoff[a];
+    int32_t lam = pc.lam[a];
+    int32_t c0f, d0f, c0t, d0t;
+    lookup_count(pc, b, lam, f, c0f, d0f);
+    lookup_count(pc, b, lam, t, c0t, d0t);
+    int32_t cf = c0f + dcf_c, ct = c0t + dct_c;
+    int64_t g = (int64_t)L.hw[a] * ((cf == 1 ? 1 : 0) - (ct == 0 ? 1 : 0));
+    if (g) atomicAdd((unsigned long long*)&gp[mi], (unsigned long long)g);
+    if (d) {
+        if (d0f + dcf_d == 1) emit_inbound(ev, scal, evbase, f, mi, -L.hk[a]);
+        if (d0t + dct_d == 0) emit_inbound(ev, scal, evbase, t, mi, L.hk[a]);
+    }
+}
+
+__global__ void __launch_bounds__(256)
+    k_replay_warp(Level L, PinCounts pc, const int32_t* __restrict__ moveidx, Moves mv,
+                  uint32_t* mvbuf, int64_t* gp, Events ev, int64_t evbase, int32_t* heavy,
+                  int32_t* heavycnt, int64_t* scal)
+{
+    int lane = threadIdx.x & 31;
+    unsigned lt = lanemask_lt();
+    int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t a = gw; a < L.E; a += nw) {
+        int64_t b = L.hoff[a], e = L.hoff[a + 1];
+        int sd = L.hsd[a];
+        int cnt = 0;
+        for (int64_t cb = b; cb < e; cb += 32) {
+            int64_t j = cb + lane;
+            int32_t mi = -1;
+            if (j < e) mi = moveidx[L.hpins[j]];
+            bool moved = mi >= 0;
+            unsigned mk = __ballot_sync(FULL, moved);
+            if (moved) {
+                uint32_t d = (j != b || sd) ? 1u : 0u;
+                mvbuf[b + cnt + __popc(mk & lt)] = ((uint32_t)mi << 1) | d;
+            }
+            cnt += __popc(mk);
+        }
+        if (cnt == 0) continue;
+        __syncwarp();
+        if (cnt > REPLAY_WARP_MAX) {
+            if (lane == 0) {
+                int32_t pos = atomicAdd((int*)&scal[RS_NHV], 1);
+                heavy[pos] = (int32_t)a;
+                heavycnt[pos] = cnt;
+            }
+            continue;
+        }
+        uint32_t rec = lane < cnt ? mvbuf[b + lane] : 0u;
+        int32_t mi = (int32_t)(rec >> 1);
+        int d = rec & 1;
+        int32_t f = lane < cnt ? mv.from[mi] : -1;
+        int32_t t = lane < cnt ? mv.to[mi] : -1;
+        int dcf_c = 0, dct_c = 0, dcf_d = 0, dct_d = 0;
+        for (int jj = 0; jj < cnt; jj++) {
+            int32_t mj = __shfl_sync(FULL, mi, jj);
+            int32_t fj = __shfl_sync(FULL, f, jj);
+            int32_t tj = __shfl_sync(FULL, t, jj);
+            int dj = __shfl_sync(FULL, d, jj);
+            if (mj < mi) {
+                int ef = (tj == f) - (fj == f), et = (tj == t) - (fj == t);
+                dcf_c += ef;
+                dct_c += et;
+                if (dj) {
+                    dcf_d += ef;
+                    dct_d += et;
+                }
+            }
+        }
+        if (lane < cnt)
+            replay_one(L, pc, (int32_t)a, mi, f, t, d, dcf_c, dct_c, dcf_d, dct_d, gp, ev, scal, evbase);
+    }
+}
+
+__global__ void __launch_bounds__(256)
+    k_replay_block(Level L, PinCounts pc, Moves mv, const uint32_t* __restrict__ mvbuf, int64_t* gp,
+                   Events ev, int64_t evbase, const int32_t* __restrict__ heavy,
+                   const int32_t* __restrict__ heavycnt, int64_t* scal)
+{
+    int32_t nh = (int32_t)scal[RS_NHV];
+    for (int32_t h = blockIdx.x; h < nh; h += gridDim.x) {
+        int32_t a = heavy[h];
+        int32_t cnt = heavycnt[h];
+        int64_t b = L.hoff[a];
+        for (int32_t x = threadIdx.x; x < cnt; x += blockDim.x) {
+            uint32_t rec = mvbuf[b + x];
+            int32_t mi = (int32_t)(rec >> 1);
+            int d = rec & 1;
+            int32_t f = mv.from[mi], t = mv.to[mi];
+            int dcf_c = 0, dct_c = 0, dcf_d = 0, dct_d = 0;
+            for (int32_t y = 0; y < cnt; y++) {
+                uint32_t ry = mvbuf[b + y];
+                int32_t mj = (int32_t)(ry >> 1);
+                if (mj >= mi) continue;
+                int32_t fj = mv.from[mj], tj = mv.to[mj];
+                int ef = (tj == f) - (fj == f), et = (tj == t) - (fj == t);
+                dcf_c += ef;
+                dct_c += et;
+                if (ry & 1) {
+                    dcf_d += ef;
+                    dct_d += et;
+                }
+            }
+            replay_one(L, pc, a, mi, f, t, d, dcf_c, dct_c, dcf_d, dct_d, gp, ev, scal, evbase);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// S10
+
+__global__ void k_part_bounds(int64_t T, const uint64_t* __restrict__ key, int ibits, int32_t* pbeg,
+                              int32_t* pend)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < T;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t p = key[e] >> ibits;
+        if (e == 0 || (key[e - 1] >> ibits) != p) pbeg[p] = (int32_t)e;
+        if (e == T - 1 || (key[e + 1] >> ibits) != p) pend[p] = (int32_t)(e + 1);
+    }
+}
+
+__global__ void __launch_bounds__(256)
+    k_part_validity(int32_t K, const int32_t* __restrict__ pbeg, const int32_t* __restrict__ pend,
+                    Events ev, PState ps, int32_t omega, int32_t delta, int32_t phi, int32_t* dv)
+{
+    int lane = threadIdx.x & 31;
+    unsigned lt = lanemask_lt();
+    uint64_t imask = (ev.ibits >= 64) ? ~0ull : ((1ull << ev.ibits) - 1);
+    int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t p = gw; p < K; p += nw) {
+        int32_t beg = pbeg[p], end = pend[p];
+        if (beg >= end) continue;
+        int64_t s0 = ps.size[p], i0 = ps.inpins[p], c0 = ps.pincnt[p];
+        int64_t cs = 0, ci = 0, cc = 0;
+        int prev_viol = 0;
+        for (int32_t cb = beg; cb < end; cb += 32) {
+            int32_t e = cb + lane;
+            bool valid = e < end;
+            int64_t mi = -1, ds = 0, di = 0, dc = 0;
+            if (valid) {
+                mi = (int64_t)(ev.key[e] & imask);
+                uint32_t x = ev.idx[e];
+                ds = ev.dsize[x];
+                di = ev.dinp[x];
+                dc = ev.dpc[x];
+            }
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int64_t a1 = __shfl_up_sync(FULL, ds, o);
+                int64_t a2 = __shfl_up_sync(FULL, di, o);
+                int64_t a3 = __shfl_up_sync(FULL, dc, o);
+                if (lane >= o) {
+                    ds += a1;
+                    di += a2;
+                    dc += a3;
+                }
+            }
+            int64_t nmi = __shfl_down_sync(FULL, mi, 1);
+            if (lane == 31) nmi = (e + 1 < end) ? (int64_t)(ev.key[e + 1] & imask) : -1;
+            if (valid && e + 1 >= end) nmi = -1;
+            bool gend = valid && nmi != mi;
+            int viol = gend ? (violates(s0 + cs + ds, i0 + ci + di, c0 + cc + dc, omega, delta, phi) ? 1 : 0) : 0;
+            unsigned gm = __ballot_sync(FULL, gend);
+            unsigned below = gm & lt;
+            int src = below ? 31 - __clz(below) : lane;
+            int pv = __shfl_sync(FULL, viol, src);
+            if (!below) pv = prev_viol;
+            if (gend && viol != pv) atomicAdd(&dv[mi], viol - pv);
+            if (gm) prev_viol = __shfl_sync(FULL, viol, 31 - __clz(gm));
+            cs += __shfl_sync(FULL, ds, 31);
+            ci += __shfl_sync(FULL, di, 31);
+            cc += __shfl_sync(FULL, dc, 31);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// S11
+
+__global__ void k_best1(int32_t M, const int64_t* __restrict__ G, const int32_t* __restrict__ nviol,
+                        int64_t* scal)
+{
+    int64_t best = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M;
+         i += (int64_t)gridDim.x * blockDim.x)
+        if (nviol[i] == 0 && G[i] > best) best = G[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        int64_t b2 = __shfl_xor_sync(FULL, best, o);
+        best = b2 > best ? b2 : best;
+    }
+    if ((threadIdx.x & 31) == 0 && best > 0)
+        atomicMax((unsigned long long*)&scal[RS_BEST], (unsigned long long)best);
+}
+
+__global__ void k_best2(int32_t M, const int64_t* __restrict__ G, const int32_t* __restrict__ nviol,
+                        int64_t* scal)
+{
+    int64_t best = scal[RS_BEST];
+    if (best <= 0) return;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M;
+         i += (int64_t)gridDim.x * blockDim.x)
+        if (nviol[i] == 0 && G[i] == best) atomicMin((unsigned long long*)&scal[RS_ISTAR], (unsigned long long)i);
+}
+
+__global__ void k_apply(int32_t M, Moves mv, int32_t* rho, int32_t* moveidx, const int64_t* scal)
+{
+    int64_t istar = scal[RS_BEST] > 0 ? scal[RS_ISTAR] : -1;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (i <= istar) rho[mv.n[i]] = mv.to[i];
+        moveidx[mv.n[i]] = -1;
+    }
+}
+
+__global__ void k_round_init(int64_t* scal) { scal[RS_ISTAR] = INT64_MAX; }
+
+// ---------------------------------------------------------------------------
+
+template <typename S>
+static Status gains(snnmap_hgraph* h, Level& L, const PinCounts& pc, const int32_t* rho,
+                    const PState& ps, int32_t* pto, int64_t* pgain)
+{
+    cudaStream_t s = h->stream;
+    Arena& ar = h->scratch;
+    const snnmap_params& p = h->prm;
+    int32_t V = L.V;
+    int32_t *heavy, *heavy2;
+    int64_t* slots;
+    SNN_TRY(ar.alloc(&heavy, V));
+    SNN_TRY(ar.alloc(&heavy2, V));
+    SNN_TRY(ar.alloc(&slots, 2));
+    SNN_CUDA(cudaMemsetAsync(slots, 0, 2 * sizeof(int64_t), s));
+    static bool attrs = false;
+    size_t wsm = (size_t)GAIN_WARPS * table_bytes<S>(GAIN_T), bsm = table_bytes<S>(GAIN_BT);
+    if (!attrs) {
+        SNN_CUDA(cudaFuncSetAttribute(k_gain_warp<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsm));
+        SNN_CUDA(cudaFuncSetAttribute(k_gain_block<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm));
+        attrs = true;
+    }
+    int grid = (int)std::min<int64_t>(ceil_div(V, GAIN_WARPS), 152 * 3 * 8);
+    k_gain_warp<S><<<grid, GAIN_WARPS * 32, wsm, s>>>(L, pc, rho, ps, p.omega, p.delta, p.phi, pto,
+                                                       pgain, heavy, slots);
+    SNN_CUDA(cudaGetLastError());
+    k_gain_block<S><<<152, GAIN_BTHREADS, bsm, s>>>(L, pc, rho, ps, p.omega, p.delta, p.phi, pto,
+                                                     pgain, heavy, slots, heavy2, slots + 1,
+                                                     nullptr, 0);
+    SNN_CUDA(cudaGetLastError());
+    int64_t n2 = 0;
+    SNN_CUDA(cudaMemcpyAsync(&n2, slots + 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    SNN_CUDA(cudaStreamSynchronize(s));
+    if (n2 > 0) {
+        int64_t K = h->levels.back().V;
+        int64_t cap = 1024;
+        while (cap < 2 * K) cap <<= 1;
+        int64_t per = (int64_t)table_bytes<S>(cap);
+        int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(16, ((int64_t)1 << 30) / per));
+        if (blocks > n2) blocks = (int)n2;
+        unsigned char* gtab;
+        SNN_TRY(ar.alloc(&gtab, blocks * per));
+        SNN_TRY(init_global_tables<S>(gtab, blocks, cap, s));
+        k_gain_block<S><<<blocks, GAIN_BTHREADS, 0, s>>>(L, pc, rho, ps, p.omega, p.delta, p.phi,
+                                                          pto, pgain, heavy2, slots + 1, nullptr,
+                                                          nullptr, gtab, cap);
+        SNN_CUDA(cudaGetLastError());
+    }
+    return Status{};
+}
+
+// pin counts + partition state + Conn for rho
+static Status pin_counts(snnmap_hgraph* h, Level& L, LevelExtra& X, int32_t K, const int32_t* rho,
+                         PinCounts& pc, PState& ps)
+{
+    cudaStream_t s = h->stream;
+    Arena& ar = h->scratch;
+    SNN_TRY(ar.alloc(&pc.p, L.P));
+    SNN_TRY(ar.alloc(&pc.cnt, L.P));
+    SNN_TRY(ar.alloc(&pc.dcnt, L.P));
+    SNN_TRY(ar.alloc(&pc.lam, L.E));
+    SNN_TRY(ar.alloc(&ps.size, K));
+    SNN_TRY(ar.alloc(&ps.inpins, K));
+    SNN_TRY(ar.alloc(&ps.pincnt, K));
+    SNN_CUDA(cudaMemsetAsync(ps.size, 0, (size_t)K * 8, s));
+    SNN_CUDA(cudaMemsetAsync(ps.inpins, 0, (size_t)K * 8, s));
+    SNN_CUDA(cudaMemsetAsync(ps.pincnt, 0, (size_t)K * 8, s));
+    if (L.V > 0) {
+        k_pstate_vertices<<<grid_for(L.V, 256), 256, 0, s>>>(L, rho, ps);
+        SNN_CUDA(cudaGetLastError());
+    }
+    PinCountJob job{L.hoff, L.hpins, L.hsd, L.hk, L.hw, rho, pc, ps.pincnt, h->d_scal};
+    SNN_TRY(seg_run(job, X.seg, L.E, ar, s));
+    return Status{};
+}
+
+Status level_cost(snnmap_hgraph* h, int32_t level, int32_t K, const int32_t* rho, int64_t* cost)
+{
+    Level& L = h->levels[level];
+    LevelExtra& X = h->extra[level];
+    SNN_TRY(zero_scalars(h));
+    PinCounts pc;
+    PState ps;
+    SNN_TRY(pin_counts(h, L, X, K, rho, pc, ps));
+    SNN_TRY(read_scalars(h));
+    h->scratch.reset();
+    *cost = h->h_scal[RS_COST];
+    return Status{};
+}
+
+// One round; *applied = moves enacted, *gain = Conn removed, *cost = Conn at
+// round start.
+static Status refine_round(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* rho,
+                           int32_t* moveidx, int32_t* n_props, int32_t* applied, int64_t* gain,
+                           int64_t* cost)
+{
+    cudaStream_t s = h->stream;
+    Arena& ar = h->scratch;
+    Level& L = h->levels[level];
+    LevelExtra& X = h->extra[level];
+    const snnmap_params& prm = h->prm;
+    int32_t V = L.V;
+    *n_props = 0;
+    *applied = 0;
+    *gain = 0;
+    SNN_TRY(zero_scalars(h));
+    k_round_init<<<1, 1, 0, s>>>(h->d_scal);
+    SNN_CUDA(cudaGetLastError());
+
+    PinCounts pc;
+    PState ps;
+    SNN_TRY(pin_counts(h, L, X, K, rho, pc, ps));
+    k_check_pstate<<<grid_for(K, 256), 256, 0, s>>>(K, ps, prm.omega, prm.delta, prm.phi, h->d_scal);
+    SNN_CUDA(cudaGetLastError());
+
+    int32_t *pto, *flag, *pos;
+    int64_t* pgain;
+    SNN_TRY(ar.alloc(&pto, V));
+    SNN_TRY(ar.alloc(&pgain, V));
+    SNN_TRY(ar.alloc(&flag, V));
+    SNN_TRY(ar.alloc(&pos, V));
+    if (h->wide) {
+        SNN_TRY(gains<unsigned long long>(h, L, pc, rho, ps, pto, pgain));
+    } else {
+        SNN_TRY(gains<uint32_t>(h, L, pc, rho, ps, pto, pgain));
+    }
+    int gv = grid_for(V, 256);
+    k_prop_stats<<<gv, 256, 0, s>>>(L, pto, pgain, flag, h->d_scal);
+    SNN_CUDA(cudaGetLastError());
+    SNN_TRY(scan_exclusive_i32(flag, pos, V, (int32_t*)(h->d_scal + RS_M), ar, s));
+    SNN_TRY(read_scalars(h));
+    *cost = h->h_scal[RS_COST];
+    if (h->h_scal[SC_STATUS] & ST_BADSTATE)
+        return Status{SNNMAP_ERR_INVALID, "refinement input breaks a per-core limit"};
+    int32_t M = (int32_t)(h->h_scal[RS_M] & 0xffffffff);
+    int64_t maxg = h->h_scal[RS_MAXG];
+    int64_t deg = h->h_scal[RS_DEG];
+    *n_props = M;
+    if (M == 0) return Status{};
+
+    // S8
+    uint64_t *keys, *keys2;
+    uint32_t *vals, *vals2;
+    SNN_TRY(ar.alloc(&keys, M));
+    SNN_TRY(ar.alloc(&keys2, M));
+    SNN_TRY(ar.alloc(&vals, M));
+    SNN_TRY(ar.alloc(&vals2, M));
+    k_prop_keys<<<gv, 256, 0, s>>>(V, pto, pgain, pos, maxg, keys, vals);
+    SNN_CUDA(cudaGetLastError());
+    SNN_TRY(radix_sort_pairs(keys, vals, keys2, vals2, M, bits_for((uint64_t)maxg), ar, s));
+    Moves mv;
+    SNN_TRY(ar.alloc(&mv.n, M));
+    SNN_TRY(ar.alloc(&mv.from, M));
+    SNN_TRY(ar.alloc(&mv.to, M));
+    int gm = grid_for(M, 256);
+    k_moves<<<gm, 256, 0, s>>>(M, vals, rho, pto, mv, moveidx);
+    SNN_CUDA(cudaGetLastError());
+
+    // S9
+    int64_t *gp, *G;
+    int32_t *dv, *nviol;
+    SNN_TRY(ar.alloc(&gp, M));
+    SNN_TRY(ar.alloc(&G, M));
+    SNN_TRY(ar.alloc(&dv, M));
+    SNN_TRY(ar.alloc(&nviol, M));
+    SNN_CUDA(cudaMemsetAsync(gp, 0, (size_t)M * 8, s));
+    SNN_CUDA(cudaMemsetAsync(dv, 0, (size_t)M * 4, s));
+    Events ev;
+    ev.cap = 2 * (int64_t)M + 2 * deg;
+    ev.ibits = bits_for((uint64_t)M);
+    SNN_TRY(ar.alloc(&ev.key, ev.cap));
+    SNN_TRY(ar.alloc(&ev.idx, ev.cap));
+    SNN_TRY(ar.alloc(&ev.dsize, ev.cap));
+    SNN_TRY(ar.alloc(&ev.dinp, ev.cap));
+    SNN_TRY(ar.alloc(&ev.dpc, ev.cap));
+    k_size_events<<<gm, 256, 0, s>>>(M, mv, L, ev);
+    SNN_CUDA(cudaGetLastError());
+    uint32_t* mvbuf;
+    int32_t *hv, *hvc;
+    SNN_TRY(ar.alloc(&mvbuf, L.P));
+    SNN_TRY(ar.alloc(&hv, L.E));
+    SNN_TRY(ar.alloc(&hvc, L.E));
+    if (L.E > 0) {
+        k_replay_warp<<<grid_for((int64_t)L.E * 32, 256), 256, 0, s>>>(L, pc, moveidx, mv, mvbuf, gp,
+                                                                      ev, 2 * (int64_t)M, hv, hvc,
+                                                                      h->d_scal);
+        SNN_CUDA(cudaGetLastError());
+        k_replay_block<<<152 * 2, 256, 0, s>>>(L, pc, mv, mvbuf, gp, ev, 2 * (int64_t)M, hv, hvc,
+                                               h->d_scal);
+        SNN_CUDA(cudaGetLastError());
+    }
+    SNN_TRY(read_scalars(h));
+    if (h->h_scal[SC_STATUS] & ST_CAPACITY) return Status{SNNMAP_ERR_CUDA, "event buffer overflow"};
+    int64_t T = 2 * (int64_t)M + h->h_scal[RS_NEV];
+
+    // S10
+    uint64_t* ekey2;
+    uint32_t* eidx2;
+    SNN_TRY(ar.alloc(&ekey2, T));
+    SNN_TRY(ar.alloc(&eidx2, T));
+    int kbits = bits_for((uint64_t)K);
+    SNN_TRY(radix_sort_pairs(ev.key, ev.idx, ekey2, eidx2, T, ev.ibits + kbits, ar, s));
+    int32_t *pbeg, *pend;
+    SNN_TRY(ar.alloc(&pbeg, K));
+    SNN_TRY(ar.alloc(&pend, K));
+    SNN_CUDA(cudaMemsetAsync(pbeg, 0, (size_t)K * 4, s));
+    SNN_CUDA(cudaMemsetAsync(pend, 0, (size_t)K * 4, s));
+    k_part_bounds<<<grid_for(T, 256), 256, 0, s>>>(T, ev.key, ev.ibits, pbeg, pend);
+    SNN_CUDA(cudaGetLastError());
+    k_part_validity<<<grid_for((int64_t)K * 32, 256), 256, 0, s>>>(K, pbeg, pend, ev, ps, prm.omega,
+                                                                  prm.delta, prm.phi, dv);
+    SNN_CUDA(cudaGetLastError());
+
+    // S11
+    SNN_TRY(scan_inclusive_i64(gp, G, M, ar, s));
+    SNN_TRY(scan_inclusive_i32(dv, nviol, M, ar, s));
+    k_best1<<<gm, 256, 0, s>>>(M, G, nviol, h->d_scal);
+    k_best2<<<gm, 256, 0, s>>>(M, G, nviol, h->d_scal);
+    k_apply<<<gm, 256, 0, s>>>(M, mv, rho, moveidx, h->d_scal);
+    SNN_CUDA(cudaGetLastError());
+    SNN_TRY(read_scalars(h));
+    int64_t best = h->h_scal[RS_BEST];
+    int64_t istar = h->h_scal[RS_ISTAR];
+    if (best > 0 && istar < M) {
+        *applied = (int32_t)(istar + 1);
+        *gain = best;
+    }
+    return Status{};
+}
+
+__global__ void k_check_rho(int32_t V, const int32_t* __restrict__ rho, int32_t K, int64_t* scal)
+{
+    int bad = 0;
+    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < V;
+         n += (int64_t)gridDim.x * blockDim.x)
+        if (rho[n] < 0 || rho[n] >= K) bad = 1;
+    if (__any_sync(FULL, bad) && (threadIdx.x & 31) == 0) atomicOr((int*)&scal[SC_STATUS], ST_INVALID);
+}
+
+Status check_rho(snnmap_hgraph* h, int32_t level, int32_t K, const int32_t* rho)
+{
+    Level& L = h->levels[level];
+    SNN_TRY(zero_scalars(h));
+    if (L.V > 0) {
+        k_check_rho<<<grid_for(L.V, 256), 256, 0, h->stream>>>(L.V, rho, K, h->d_scal);
+        SNN_CUDA(cudaGetLastError());
+    }
+    SNN_TRY(read_scalars(h));
+    if (h->h_scal[SC_STATUS] & ST_INVALID) return Status{SNNMAP_ERR_INVALID, "rho value outside [0, n_parts)"};
+    return Status{};
+}
+
+Status refine_level(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* rho, int64_t* cost,
+                    int64_t* cost_start)
+{
+    Level& L = h->levels[level];
+    int32_t* moveidx;
+    SNN_CUDA(cudaMallocAsync(&moveidx, (size_t)(L.V > 0 ? L.V : 1) * sizeof(int32_t), h->stream));
+    Status st = fill_i32(moveidx, -1, L.V, h->stream);
+    int64_t c = 0;
+    bool have_cost = false;
+    for (int32_t r = 0; st.ok() && r < h->prm.max_refine_rounds; r++) {
+        int32_t props = 0, applied = 0;
+        int64_t g = 0, c0 = 0;
+        st = refine_round(h, level, K, rho, moveidx, &props, &applied, &g, &c0);
+        h->scratch.reset();
+        if (!st.ok()) break;
+        h->rlog.push_back(snnmap_round_log{level, r, props, applied, g});
+        if (!have_cost && cost_start) *cost_start = c0;
+        c = c0 - g;
+        have_cost = true;
+        if (applied == 0) break;
+    }
+    cudaFreeAsync(moveidx, h->stream);
+    if (!st.ok()) return st;
+    if (!have_cost) {
+        SNN_TRY(level_cost(h, level, K, rho, &c));
+        if (cost_start) *cost_start = c;
+    }
+    *cost = c;
+    return Status{};
+}
+
+}  // namespace snn

@@ -1,0 +1,126 @@
+"""CUDA path against the oracle, bit-exact: every level's arrays, candidates,
+scores, shared inbound counts, matching and cid maps, then the final
+partition, its Conn and the refinement logs, on seeded inputs of several
+shapes (scaled-down generators spanning many warps, blocks and all
+hyperedge size buckets, plus tiny random hypergraphs)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import snngen
+from gpu_helpers import lockstep
+from helpers import hypergraph
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2609_07577_gb300 as P
+    P.lib()
+    assert torch.cuda.is_available()
+
+
+@pytest.mark.parametrize("name", ["cfg1s", "cfg1", "cfg2s", "cfg3s"])
+def test_coarsening_lockstep(name):
+    hg = snngen.by_name(name)
+    n = lockstep(hg, max_levels=40)
+    assert n >= 1
+
+
+def _partition_both(hg, **kw):
+    from paper_2609_07577_gb300 import partition
+    prm = oracle.params_of(hg, **kw)
+    rho_o, cost_o, st_o, lv_o, rl_o = oracle.partition(hg, prm)
+    from paper_2609_07577_gb300 import HGraph, params_for
+    G = HGraph.from_hypergraph(hg, params=params_for(hg.omega, hg.delta, hg.phi, **kw))
+    try:
+        rho, cost, st = G.partition()
+        rl = G.round_logs()
+        lv = G.level_logs()
+    finally:
+        G.close()
+    return (rho.cpu().numpy(), cost, st, lv, rl), (rho_o, cost_o, st_o, lv_o, rl_o)
+
+
+@pytest.mark.parametrize("name", ["cfg1s", "cfg1", "cfg2s", "cfg3s"])
+def test_partition_parity(name):
+    hg = snngen.by_name(name)
+    (rho, cost, st, lv, rl), (rho_o, cost_o, st_o, lv_o, rl_o) = _partition_both(hg)
+    assert cost == cost_o
+    assert np.array_equal(rho, rho_o)
+    for k in ("levels", "n_parts", "nonempty_parts", "rounds", "moves", "cost_initial", "cost"):
+        assert st[k] == st_o[k], k
+    assert [(r["level"], r["round"], r["n_props"], r["istar"], r["gain"]) for r in rl] == \
+           [(r["level"], r["round"], r["n_props"], r["istar"], r["gain"]) for r in rl_o]
+    assert [(g["V"], g["E"], g["P"], g["n_cand"], g["n_pairs"]) for g in lv] == \
+           [(g["V"], g["E"], g["P"], g["n_cand"], g["n_pairs"]) for g in lv_o]
+
+
+def test_tiny_random_partitions():
+    n = 0
+    for seed in range(300):
+        hg = snngen.tiny_random(90_000 + seed)
+        try:
+            rho_o, cost_o, st_o, lv_o, rl_o = oracle.partition(hg)
+        except oracle.OracleError:
+            continue
+        (rho, cost, st, lv, rl), _ = _partition_both(hg)
+        assert cost == cost_o, seed
+        assert np.array_equal(rho, rho_o), seed
+        n += 1
+    assert n > 100
+
+
+def test_level_cap_and_no_refinement():
+    hg = snngen.by_name("cfg1s")
+    (rho, cost, st, lv, rl), (rho_o, cost_o, st_o, lv_o, rl_o) = _partition_both(
+        hg, max_levels=3, max_refine_rounds=0)
+    assert st["levels"] == 3 == st_o["levels"]
+    assert cost == cost_o and np.array_equal(rho, rho_o)
+    (rho, cost, st, lv, rl), (rho_o, cost_o, st_o, lv_o, rl_o) = _partition_both(
+        hg, max_levels=0, max_refine_rounds=3)
+    assert cost == cost_o and np.array_equal(rho, rho_o)
+
+
+def test_error_codes():
+    from paper_2609_07577_gb300 import HGraph, SnnmapError, params_for
+    import paper_2609_07577_gb300._native as N
+    cases = [
+        (hypergraph(3, [[0, 1, 1]], [1], 5, 5, 5), N.ERR_INVALID),
+        (hypergraph(3, [[0, 1, 0]], [1], 5, 5, 5), N.ERR_INVALID),
+        (hypergraph(3, [[0, 3]], [1], 5, 5, 5), N.ERR_INVALID),
+        (hypergraph(3, [[0, 1]], [-1], 5, 5, 5), N.ERR_INVALID),
+        (hypergraph(3, [[0, 2], [1, 2]], [1, 1], 5, 1, 5), N.ERR_INFEASIBLE),
+    ]
+    for hg, code in cases:
+        with pytest.raises(SnnmapError) as e:
+            HGraph.from_hypergraph(hg)
+        assert e.value.code == code
+    hg = hypergraph(3, [[0, 1]], [1], 5, 5, 5)
+    off = torch.tensor(hg.off)  # host memory: rejected, not dereferenced
+    with pytest.raises(SnnmapError) as e:
+        HGraph(params_for(5, 5, 5), 3, off, torch.tensor(hg.pins), torch.tensor(hg.w))
+    assert e.value.code == N.ERR_INVALID
+
+
+def test_empty_and_degenerate():
+    from paper_2609_07577_gb300 import partition
+    # no hyperedges: every neuron its own partition
+    hg = hypergraph(5, [], [], 3, 3, 3)
+    rho, cost, st = partition(hg)
+    assert cost == 0 and st["n_parts"] == 5 and list(rho) == [0, 1, 2, 3, 4]
+    # hyperedges without destinations are dropped
+    hg = hypergraph(4, [[0], [1, 2], [3]], [5, 1, 7], 4, 4, 4)
+    rho_o, cost_o, *_ = oracle.partition(hg)
+    rho, cost, st = partition(hg)
+    assert cost == cost_o and np.array_equal(rho, rho_o)
+    # a star: one pair per level until the level cap
+    hg = hypergraph(40, [list(range(40))], [3], 40, 100, 100)
+    rho_o, cost_o, st_o, *_ = oracle.partition(hg)
+    rho, cost, st = partition(hg)
+    assert cost == cost_o == 0 and np.array_equal(rho, rho_o)
+    assert st["levels"] == st_o["levels"]
