@@ -79,9 +79,20 @@ typedef struct {
 typedef struct {
     int32_t V, E;
     int64_t P;
-    int32_t n_cand;   /* vertices with a valid candidate */
-    int32_t n_pairs;  /* matched pairs */
+    int32_t n_cand;      /* vertices with a valid candidate */
+    int32_t n_pairs;     /* matched pairs */
+    int64_t pair_terms;  /* sum over hyperedges of |e|(|e|-1): neighbour-histogram updates */
 } snnmap_level_log;
+
+/* Device time of one pipeline stage, summed over the calls since the last
+ * snnmap_profile(h, 1) (CUDA events on the handle's stream). */
+typedef struct {
+    const char* name;  /* "build", "affinity", "match", "contract", "incidence",
+                          "pincount", "gains", "sortmoves", "replay", "validity",
+                          "apply" */
+    int64_t calls;     /* times the stage ran */
+    double ms;         /* summed device time */
+} snnmap_stage_time;
 
 typedef struct snnmap_hgraph snnmap_hgraph;
 
@@ -212,10 +223,20 @@ int snnmap_level_cid(const snnmap_hgraph* h, int32_t level, int32_t* d_cid, void
 int snnmap_round_logs(const snnmap_hgraph* h, snnmap_round_log* out, int32_t cap, int32_t* n);
 int snnmap_level_logs(const snnmap_hgraph* h, snnmap_level_log* out, int32_t cap, int32_t* n);
 
+/* Stage timing: on != 0 clears the counters and starts recording CUDA events
+ * around every stage; on == 0 stops. Recording adds two event records per
+ * stage call and no synchronization. */
+int snnmap_profile(snnmap_hgraph* h, int32_t on);
+/* Copies up to cap stage records; *n receives the number of stages. */
+int snnmap_stage_times(snnmap_hgraph* h, snnmap_stage_time* out, int32_t cap, int32_t* n);
+
 /* Bytes of device memory the handle currently holds. */
 int snnmap_device_bytes(const snnmap_hgraph* h, int64_t* bytes);
 
 void snnmap_free(snnmap_hgraph* h);
+
+/* Kernels launched by the library in this process so far. */
+int64_t snnmap_launch_count(void);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* snnmap_last_error(void);

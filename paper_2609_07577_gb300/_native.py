@@ -35,7 +35,11 @@ class RoundLog(C.Structure):
 
 class LevelLog(C.Structure):
     _fields_ = [("V", C.c_int32), ("E", C.c_int32), ("P", C.c_int64), ("n_cand", C.c_int32),
-                ("n_pairs", C.c_int32)]
+                ("n_pairs", C.c_int32), ("pair_terms", C.c_int64)]
+
+
+class StageTime(C.Structure):
+    _fields_ = [("name", C.c_char_p), ("calls", C.c_int64), ("ms", C.c_double)]
 
 
 class SnnmapError(RuntimeError):
@@ -68,6 +72,9 @@ _SIGS = {
     "snnmap_round_logs": (C.c_int, [_vp, _vp, _i32, C.POINTER(_i32)]),
     "snnmap_level_logs": (C.c_int, [_vp, _vp, _i32, C.POINTER(_i32)]),
     "snnmap_device_bytes": (C.c_int, [_vp, C.POINTER(_i64)]),
+    "snnmap_profile": (C.c_int, [_vp, _i32]),
+    "snnmap_stage_times": (C.c_int, [_vp, _vp, _i32, C.POINTER(_i32)]),
+    "snnmap_launch_count": (_i64, []),
     "snnmap_free": (None, [_vp]),
     "snnmap_last_error": (C.c_char_p, []),
 }
@@ -222,6 +229,21 @@ def snnmap_device_bytes(h):
     b = C.c_int64()
     check(lib().snnmap_device_bytes(h, C.byref(b)))
     return b.value
+
+
+def snnmap_profile(h, on):
+    check(lib().snnmap_profile(h, 1 if on else 0))
+
+
+def snnmap_stage_times(h):
+    n = C.c_int32()
+    buf = (StageTime * 32)()
+    check(lib().snnmap_stage_times(h, buf, 32, C.byref(n)))
+    return {buf[i].name.decode(): {"calls": buf[i].calls, "ms": buf[i].ms} for i in range(n.value)}
+
+
+def snnmap_launch_count():
+    return int(lib().snnmap_launch_count())
 
 
 def snnmap_free(h):

@@ -116,6 +116,12 @@ class HGraph:
     def level_logs(self):
         return N.snnmap_level_logs(self._h)
 
+    def profile(self, on=True):
+        N.snnmap_profile(self._h, on)
+
+    def stage_times(self):
+        return N.snnmap_stage_times(self._h)
+
     def device_bytes(self):
         return N.snnmap_device_bytes(self._h)
 

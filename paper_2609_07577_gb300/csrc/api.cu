@@ -85,8 +85,8 @@ snn::Status count_nonempty(snnmap_hgraph* h, int32_t V, int32_t K, const int32_t
     SNN_TRY(h->scratch.alloc(&used, K));
     SNN_CUDA(cudaMemsetAsync(used, 0, (size_t)K, h->stream));
     SNN_TRY(snn::zero_scalars(h));
-    if (V > 0) k_mark_used<<<snn::grid_for(V, 256), 256, 0, h->stream>>>(V, rho, used);
-    if (K > 0) k_count_used<<<snn::grid_for(K, 256), 256, 0, h->stream>>>(K, used, h->d_scal + snn::SC_A);
+    if (V > 0) SNN_L k_mark_used<<<snn::grid_for(V, 256), 256, 0, h->stream>>>(V, rho, used);
+    if (K > 0) SNN_L k_count_used<<<snn::grid_for(K, 256), 256, 0, h->stream>>>(K, used, h->d_scal + snn::SC_A);
     SNN_CUDA(cudaGetLastError());
     SNN_TRY(snn::read_scalars(h));
     *out = (int32_t)h->h_scal[snn::SC_A];
@@ -111,10 +111,13 @@ snnmap_params snnmap_default_params(int32_t omega, int32_t delta, int32_t phi)
 
 const char* snnmap_last_error(void) { return g_err.c_str(); }
 
+int64_t snnmap_launch_count(void) { return snn::launch_count(); }
+
 void snnmap_free(snnmap_hgraph* h)
 {
     if (!h) return;
     cudaStreamSynchronize(h->stream);
+    snn::prof_release(h);
     drop_levels_above(h, 0);
     h->scratch.release();
     if (h->cand) cudaFreeAsync(h->cand, h->stream);
@@ -178,7 +181,7 @@ int snnmap_coarsen_level(snnmap_hgraph* h, void* stream, int32_t* n_cand_out, in
     h->scratch.reset();
     if (!st.ok()) return fail(st);
     const snn::Level& L = h->levels.back();
-    h->llog.push_back(snnmap_level_log{L.V, L.E, L.P, nc, np});
+    h->llog.push_back(snnmap_level_log{L.V, L.E, L.P, nc, np, h->extra.back().pair_terms});
     *n_cand_out = nc;
     *n_pairs_out = np;
     return SNNMAP_OK;
@@ -263,7 +266,7 @@ int snnmap_partition(snnmap_hgraph* h, void* stream, int32_t* d_rho_out, int64_t
         h->scratch.reset();
         if (!s1.ok()) return fail(s1);
         const snn::Level& L = h->levels.back();
-        h->llog.push_back(snnmap_level_log{L.V, L.E, L.P, nc, np});
+        h->llog.push_back(snnmap_level_log{L.V, L.E, L.P, nc, np, h->extra.back().pair_terms});
         if (nc == 0 || np == 0) break;
         API_TRY(snn::contract_level(h));
     }
@@ -434,6 +437,35 @@ int snnmap_level_logs(const snnmap_hgraph* h, snnmap_level_log* out, int32_t cap
     if (!h || !n) return fail(SNNMAP_ERR_INVALID, "NULL argument");
     *n = (int32_t)h->llog.size();
     for (int32_t i = 0; out && i < cap && i < *n; i++) out[i] = h->llog[i];
+    return SNNMAP_OK;
+}
+
+int snnmap_profile(snnmap_hgraph* h, int32_t on)
+{
+    if (!h) return fail(SNNMAP_ERR_INVALID, "NULL handle");
+    cudaStreamSynchronize(h->stream);
+    snn::prof_collect(h);
+    if (on) {
+        for (int i = 0; i < snn::PS_N; i++) {
+            h->prof_ms[i] = 0;
+            h->prof_calls[i] = 0;
+        }
+    }
+    h->prof_on = on != 0;
+    return SNNMAP_OK;
+}
+
+int snnmap_stage_times(snnmap_hgraph* h, snnmap_stage_time* out, int32_t cap, int32_t* n)
+{
+    if (!h || !n) return fail(SNNMAP_ERR_INVALID, "NULL argument");
+    cudaStreamSynchronize(h->stream);
+    snn::prof_collect(h);
+    *n = snn::PS_N;
+    for (int32_t i = 0; out && i < cap && i < snn::PS_N; i++) {
+        out[i].name = snn::kStageNames[i];
+        out[i].calls = h->prof_calls[i];
+        out[i].ms = h->prof_ms[i];
+    }
     return SNNMAP_OK;
 }
 

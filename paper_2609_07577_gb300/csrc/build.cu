@@ -12,7 +12,66 @@ Status read_scalars(snnmap_hgraph* h)
     SNN_CUDA(cudaMemcpyAsync(h->h_scal, h->d_scal, SC_COUNT * sizeof(int64_t),
                              cudaMemcpyDeviceToHost, h->stream));
     SNN_CUDA(cudaStreamSynchronize(h->stream));
+    if (!h->prof_pend.empty()) prof_collect(h);
     return Status{};
+}
+
+// ---------------------------------------------------------------------------
+// profiler
+
+const char* const kStageNames[PS_N] = {"build",    "affinity",  "match",  "contract",
+                                       "incidence", "pincount", "gains",  "sortmoves",
+                                       "replay",   "validity",  "apply"};
+
+static cudaEvent_t prof_event(snnmap_hgraph* h)
+{
+    if (!h->prof_pool.empty()) {
+        cudaEvent_t e = h->prof_pool.back();
+        h->prof_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+ProfScope::ProfScope(snnmap_hgraph* h_, int stage_) : h(h_), stage(stage_)
+{
+    if (!h->prof_on) return;
+    a = prof_event(h);
+    b = prof_event(h);
+    if (a && b) cudaEventRecord(a, h->stream);
+}
+
+ProfScope::~ProfScope()
+{
+    if (!h->prof_on || !a || !b) return;
+    cudaEventRecord(b, h->stream);
+    h->prof_pend.push_back({stage, a, b});
+}
+
+void prof_collect(snnmap_hgraph* h)
+{
+    for (auto& p : h->prof_pend) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            h->prof_ms[p.stage] += ms;
+            h->prof_calls[p.stage] += 1;
+        } else {
+            cudaGetLastError();
+        }
+        h->prof_pool.push_back(p.a);
+        h->prof_pool.push_back(p.b);
+    }
+    h->prof_pend.clear();
+}
+
+void prof_release(snnmap_hgraph* h)
+{
+    cudaStreamSynchronize(h->stream);
+    prof_collect(h);
+    for (cudaEvent_t e : h->prof_pool) cudaEventDestroy(e);
+    h->prof_pool.clear();
 }
 
 Status zero_scalars(snnmap_hgraph* h)
@@ -66,14 +125,20 @@ __device__ __forceinline__ int seg_bucket(int64_t len)
     return len <= 32 ? 0 : (len <= SEG_B1_CAP ? 1 : (len <= SEG_B2_CAP ? 2 : 3));
 }
 
-__global__ void k_seg_flags(const int64_t* __restrict__ hoff, int32_t E, int64_t* pa, int64_t* pb)
+__global__ void k_seg_flags(const int64_t* __restrict__ hoff, int32_t E, int64_t* pa, int64_t* pb,
+                            int64_t* w2)
 {
+    int64_t acc = 0;
     for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < E;
          a += (int64_t)gridDim.x * blockDim.x) {
-        int b = seg_bucket(hoff[a + 1] - hoff[a]);
+        int64_t len = hoff[a + 1] - hoff[a];
+        int b = seg_bucket(len);
         pa[a] = (int64_t)(b == 0) | ((int64_t)(b == 1) << 32);
         pb[a] = (int64_t)(b == 2) | ((int64_t)(b == 3) << 32);
+        acc += len * (len - 1);
     }
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0 && acc) atomicAdd((unsigned long long*)w2, (unsigned long long)acc);
 }
 
 __global__ void k_seg_meta(const int64_t* ta, const int64_t* tb, int32_t* meta)
@@ -106,7 +171,7 @@ __global__ void k_seg_scatter(const int64_t* __restrict__ hoff, int32_t E,
 }
 
 Status seg_classify(const int64_t* hoff, int32_t E, int32_t maxlen, SegBuckets& b, Arena& ar,
-                    cudaStream_t s)
+                    cudaStream_t s, int64_t* w2)
 {
     int64_t *pa, *pb, *tot;
     SNN_TRY(ar.alloc(&pa, E));
@@ -119,15 +184,15 @@ Status seg_classify(const int64_t* hoff, int32_t E, int32_t maxlen, SegBuckets& 
         b.b3_cap = c;
     }
     if (E > 0) {
-        k_seg_flags<<<grid_for(E, 256), 256, 0, s>>>(hoff, E, pa, pb);
+        SNN_L k_seg_flags<<<grid_for(E, 256), 256, 0, s>>>(hoff, E, pa, pb, w2);
         SNN_CUDA(cudaGetLastError());
     }
     SNN_TRY(scan_exclusive_i64(pa, pa, E, tot, ar, s));
     SNN_TRY(scan_exclusive_i64(pb, pb, E, tot + 1, ar, s));
-    k_seg_meta<<<1, 1, 0, s>>>(tot, tot + 1, b.meta);
+    SNN_L k_seg_meta<<<1, 1, 0, s>>>(tot, tot + 1, b.meta);
     SNN_CUDA(cudaGetLastError());
     if (E > 0) {
-        k_seg_scatter<<<grid_for(E, 256), 256, 0, s>>>(hoff, E, pa, pb, b.meta, b.list);
+        SNN_L k_seg_scatter<<<grid_for(E, 256), 256, 0, s>>>(hoff, E, pa, pb, b.meta, b.list);
         SNN_CUDA(cudaGetLastError());
     }
     return Status{};
@@ -162,6 +227,7 @@ __global__ void k_csc_fill(const int64_t* __restrict__ hoff, const int32_t* __re
 
 Status build_incidence(snnmap_hgraph* h, Level& L)
 {
+    ProfScope prof(h, PS_INCIDENCE);
     cudaStream_t s = h->stream;
     Arena& ar = h->scratch;
     int32_t *deg, *cursor;
@@ -172,12 +238,12 @@ Status build_incidence(snnmap_hgraph* h, Level& L)
         SNN_CUDA(cudaMemsetAsync(cursor, 0, (size_t)L.V * sizeof(int32_t), s));
     }
     if (L.P > 0) {
-        k_count_deg<<<grid_for(L.P, 256), 256, 0, s>>>(L.hpins, L.P, deg);
+        SNN_L k_count_deg<<<grid_for(L.P, 256), 256, 0, s>>>(L.hpins, L.P, deg);
         SNN_CUDA(cudaGetLastError());
     }
     SNN_TRY(scan_exclusive_i32_to_i64(deg, L.voff, L.V, L.voff + L.V, ar, s));
     if (L.E > 0) {
-        k_csc_fill<<<grid_for((int64_t)L.E * 32, 256), 256, 0, s>>>(L.hoff, L.hpins, L.E, L.voff,
+        SNN_L k_csc_fill<<<grid_for((int64_t)L.E * 32, 256), 256, 0, s>>>(L.hoff, L.hpins, L.E, L.voff,
                                                                     cursor, L.vinc);
         SNN_CUDA(cudaGetLastError());
     }
@@ -325,11 +391,11 @@ Status build_level0(snnmap_hgraph* h, int32_t V, int32_t E, const int64_t* d_off
     SNN_TRY(ar.alloc(&klen, E));
     SNN_TRY(ar.alloc(&newoff, E));
     if (E > 0) {
-        k_in_hedges<<<grid_for(E, 256), 256, 0, s>>>(d_off, d_w, E, kept, klen, h->d_scal);
+        SNN_L k_in_hedges<<<grid_for(E, 256), 256, 0, s>>>(d_off, d_w, E, kept, klen, h->d_scal);
         SNN_CUDA(cudaGetLastError());
     }
     if (Pin > 0) {
-        k_in_pins<<<grid_for(Pin, 256), 256, 0, s>>>(d_pins, Pin, V, h->d_scal);
+        SNN_L k_in_pins<<<grid_for(Pin, 256), 256, 0, s>>>(d_pins, Pin, V, h->d_scal);
         SNN_CUDA(cudaGetLastError());
     }
     SNN_TRY(scan_exclusive_i32(kept, newid, E, (int32_t*)(h->d_scal + SC_A), ar, s));
@@ -349,26 +415,30 @@ Status build_level0(snnmap_hgraph* h, int32_t V, int32_t E, const int64_t* d_off
     SNN_TRY(level_alloc(h, L, X, V, E0, P0));
     L.maxlen = maxlen;
     if (E > 0) {
-        k_copy_hedges<<<grid_for((int64_t)E * 32, 256), 256, 0, s>>>(d_off, d_pins, d_w, E, kept,
+        SNN_L k_copy_hedges<<<grid_for((int64_t)E * 32, 256), 256, 0, s>>>(d_off, d_pins, d_w, E, kept,
                                                                       newid, newoff, L);
         SNN_CUDA(cudaGetLastError());
     }
-    k_set_last_off<<<1, 1, 0, s>>>(L.hoff, E0, h->d_scal + SC_B);
+    SNN_L k_set_last_off<<<1, 1, 0, s>>>(L.hoff, E0, h->d_scal + SC_B);
     SNN_CUDA(cudaGetLastError());
-    SNN_TRY(seg_classify(L.hoff, E0, maxlen, X.seg, ar, s));
+    SNN_TRY(seg_classify(L.hoff, E0, maxlen, X.seg, ar, s, h->d_scal + SC_W2));
     BuildCheckJob job{L.hoff, L.hpins, h->d_scal};
-    SNN_TRY(seg_run(job, X.seg, E0, ar, s));
+    {
+        ProfScope prof(h, PS_BUILD);
+        SNN_TRY(seg_run(job, X.seg, E0, ar, s));
+    }
     if (V > 0) SNN_CUDA(cudaMemsetAsync(L.vinpins, 0, (size_t)V * sizeof(int32_t), s));
     if (E0 > 0) {
-        k_count_inpins<<<grid_for((int64_t)E0 * 32, 256), 256, 0, s>>>(L.hoff, L.hpins, E0, L.vinpins);
+        SNN_L k_count_inpins<<<grid_for((int64_t)E0 * 32, 256), 256, 0, s>>>(L.hoff, L.hpins, E0, L.vinpins);
         SNN_CUDA(cudaGetLastError());
     }
     if (V > 0) {
-        k_vertex_init<<<grid_for(V, 256), 256, 0, s>>>(L, h->prm.delta, h->prm.phi, h->d_scal);
+        SNN_L k_vertex_init<<<grid_for(V, 256), 256, 0, s>>>(L, h->prm.delta, h->prm.phi, h->d_scal);
         SNN_CUDA(cudaGetLastError());
     }
     SNN_TRY(build_incidence(h, L));
     SNN_TRY(read_scalars(h));
+    X.pair_terms = h->h_scal[SC_W2];
     h->scratch.reset();
     if (h->h_scal[SC_STATUS] & ST_INVALID)
         return Status{SNNMAP_ERR_INVALID, "repeated destination or source listed as a destination"};

@@ -29,6 +29,7 @@
 #include "internal.cuh"
 
 #include <algorithm>
+#include <memory>
 
 namespace snn {
 
@@ -395,10 +396,10 @@ static Status affinity(snnmap_hgraph* h, Level& L)
         attrs = true;
     }
     int grid = (int)std::min<int64_t>(ceil_div(V, AFF_WARPS), 152 * 3 * 8);
-    k_aff_warp<S><<<grid, AFF_WARPS * 32, aff_warp_smem<S>(), s>>>(
+    SNN_L k_aff_warp<S><<<grid, AFF_WARPS * 32, aff_warp_smem<S>(), s>>>(
         L, p.omega, p.delta, p.phi, h->cand, h->cscore, h->cov, heavy, h->d_scal);
     SNN_CUDA(cudaGetLastError());
-    k_aff_block<S><<<152, AFF_BTHREADS, aff_block_smem<S>(), s>>>(
+    SNN_L k_aff_block<S><<<152, AFF_BTHREADS, aff_block_smem<S>(), s>>>(
         L, p.omega, p.delta, p.phi, h->cand, h->cscore, h->cov, heavy, h->d_scal + SC_E, heavy2,
         h->d_scal + SC_F, nullptr, 0);
     SNN_CUDA(cudaGetLastError());
@@ -413,7 +414,7 @@ static Status affinity(snnmap_hgraph* h, Level& L)
         unsigned char* gtab;
         SNN_TRY(ar.alloc(&gtab, blocks * per));
         SNN_TRY(init_global_tables<S>(gtab, blocks, cap, s));
-        k_aff_block<S><<<blocks, AFF_BTHREADS, 0, s>>>(
+        SNN_L k_aff_block<S><<<blocks, AFF_BTHREADS, 0, s>>>(
             L, p.omega, p.delta, p.phi, h->cand, h->cscore, h->cov, heavy2, h->d_scal + SC_F,
             nullptr, nullptr, gtab, cap);
         SNN_CUDA(cudaGetLastError());
@@ -432,13 +433,17 @@ Status coarsen_level(snnmap_hgraph* h, int32_t* n_cand, int32_t* n_pairs)
     h->have_matching = false;
     SNN_TRY(zero_scalars(h));
     if (V == 0) return Status{};
-    if (h->wide) {
-        SNN_TRY(affinity<unsigned long long>(h, L));
-    } else {
-        SNN_TRY(affinity<uint32_t>(h, L));
+    {
+        ProfScope prof(h, PS_AFFINITY);
+        if (h->wide) {
+            SNN_TRY(affinity<unsigned long long>(h, L));
+        } else {
+            SNN_TRY(affinity<uint32_t>(h, L));
+        }
     }
     int g = grid_for(V, 256);
-    k_count_cand<<<g, 256, 0, s>>>(V, h->cand, h->d_scal);
+    std::unique_ptr<ProfScope> prof(new ProfScope(h, PS_MATCH));
+    SNN_L k_count_cand<<<g, 256, 0, s>>>(V, h->cand, h->d_scal);
     SNN_CUDA(cudaGetLastError());
     int64_t* bestsc;
     int32_t *bc, *link, *nxt, *nxt2;
@@ -449,11 +454,12 @@ Status coarsen_level(snnmap_hgraph* h, int32_t* n_cand, int32_t* n_pairs)
     SNN_TRY(ar.alloc(&par, V));
     SNN_TRY(fill_i64(bestsc, INT64_MIN, V, s));
     SNN_TRY(fill_i32(bc, 0x7fffffff, V, s));
-    k_child_best_score<<<g, 256, 0, s>>>(V, h->cand, h->cscore, bestsc);
-    k_child_best_id<<<g, 256, 0, s>>>(V, h->cand, h->cscore, bestsc, bc);
-    k_link<<<g, 256, 0, s>>>(V, h->cand, bc, link);
-    k_walk<<<g, 256, 0, s>>>(V, link, par, h->d_scal);
+    SNN_L k_child_best_score<<<g, 256, 0, s>>>(V, h->cand, h->cscore, bestsc);
+    SNN_L k_child_best_id<<<g, 256, 0, s>>>(V, h->cand, h->cscore, bestsc, bc);
+    SNN_L k_link<<<g, 256, 0, s>>>(V, h->cand, bc, link);
+    SNN_L k_walk<<<g, 256, 0, s>>>(V, link, par, h->d_scal);
     SNN_CUDA(cudaGetLastError());
+    prof.reset();
     SNN_TRY(read_scalars(h));
     *n_cand = (int32_t)h->h_scal[SC_A];
     int64_t unresolved = h->h_scal[SC_B];
@@ -463,23 +469,25 @@ Status coarsen_level(snnmap_hgraph* h, int32_t* n_cand, int32_t* n_pairs)
         SNN_TRY(ar.alloc(&nxt2, V));
         SNN_TRY(ar.alloc(&pj, V));
         SNN_TRY(ar.alloc(&pj2, V));
-        k_jump_init<<<g, 256, 0, s>>>(V, link, nxt, pj);
+        SNN_L k_jump_init<<<g, 256, 0, s>>>(V, link, nxt, pj);
         SNN_CUDA(cudaGetLastError());
         for (int it = 0; it < 40; it++) {
             SNN_TRY(zero_scalars(h));
-            k_jump<<<g, 256, 0, s>>>(V, nxt, pj, nxt2, pj2, h->d_scal);
+            SNN_L k_jump<<<g, 256, 0, s>>>(V, nxt, pj, nxt2, pj2, h->d_scal);
             SNN_CUDA(cudaGetLastError());
             std::swap(nxt, nxt2);
             std::swap(pj, pj2);
             SNN_TRY(read_scalars(h));
             if (h->h_scal[SC_B] == 0) break;
         }
-        k_jump_done<<<g, 256, 0, s>>>(V, pj, par);
+        SNN_L k_jump_done<<<g, 256, 0, s>>>(V, pj, par);
         SNN_CUDA(cudaGetLastError());
     }
     SNN_TRY(zero_scalars(h));
-    k_match_finish<<<g, 256, 0, s>>>(V, h->cand, bc, par, h->match, h->d_scal);
+    prof.reset(new ProfScope(h, PS_MATCH));
+    SNN_L k_match_finish<<<g, 256, 0, s>>>(V, h->cand, bc, par, h->match, h->d_scal);
     SNN_CUDA(cudaGetLastError());
+    prof.reset();
     SNN_TRY(read_scalars(h));
     *n_pairs = (int32_t)h->h_scal[SC_C];
     h->have_matching = true;

@@ -41,6 +41,12 @@ struct Status {
 
 constexpr unsigned FULL = 0xffffffffu;
 
+// Every kernel launch of the library goes through SNN_L, which counts it
+// (process-wide, reported by snnmap_launch_count).
+void note_launch();
+int64_t launch_count();
+#define SNN_L (void)::snn::note_launch(),
+
 __device__ __forceinline__ unsigned lanemask_lt()
 {
     unsigned m;

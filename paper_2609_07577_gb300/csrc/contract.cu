@@ -16,6 +16,8 @@
 // 5. Compaction into the next level's arrays, then its incidence lists.
 #include "internal.cuh"
 
+#include <memory>
+
 namespace snn {
 
 __global__ void k_rep_flags(int32_t V, const int32_t* __restrict__ match, int32_t* isrep)
@@ -229,6 +231,7 @@ Status contract_level(snnmap_hgraph* h)
     int32_t V = L.V, E = L.E;
     int g = grid_for(V, 256);
     SNN_TRY(zero_scalars(h));
+    std::unique_ptr<ProfScope> prof(new ProfScope(h, PS_CONTRACT));
 
     // 1-2. coarse ids and super-node state
     int32_t *isrep, *repidx;
@@ -239,10 +242,10 @@ Status contract_level(snnmap_hgraph* h)
     SNN_TRY(ar.alloc(&ns.inpins, V));
     SNN_TRY(ar.alloc(&ns.incnt, V));
     SNN_TRY(ar.alloc(&ns.inint, V));
-    k_rep_flags<<<g, 256, 0, s>>>(V, h->match, isrep);
+    SNN_L k_rep_flags<<<g, 256, 0, s>>>(V, h->match, isrep);
     SNN_CUDA(cudaGetLastError());
     SNN_TRY(scan_exclusive_i32(isrep, repidx, V, (int32_t*)(h->d_scal + SC_A), ar, s));
-    k_cid_state<<<g, 256, 0, s>>>(L, h->match, h->cand, h->cov, repidx, ns);
+    SNN_L k_cid_state<<<g, 256, 0, s>>>(L, h->match, h->cand, h->cov, repidx, ns);
     SNN_CUDA(cudaGetLastError());
 
     // 3. per-hyperedge remap, sort, unique
@@ -278,15 +281,15 @@ Status contract_level(snnmap_hgraph* h)
     int ge = grid_for(E, 256);
     int hibits = bits_for((uint64_t)V);
     if (E > 0) {
-        k_dedup_keys<<<ge, 256, 0, s>>>(E, tlen, L.hoff, tpins, thash, (uint64_t)V, keys, vals);
+        SNN_L k_dedup_keys<<<ge, 256, 0, s>>>(E, tlen, L.hoff, tpins, thash, (uint64_t)V, keys, vals);
         SNN_CUDA(cudaGetLastError());
         SNN_TRY(radix_sort_pairs(keys, vals, keys2, vals2, E, 32 + hibits, ar, s));
-        k_run_heads<<<ge, 256, 0, s>>>(E, keys, headpos);
+        SNN_L k_run_heads<<<ge, 256, 0, s>>>(E, keys, headpos);
         SNN_CUDA(cudaGetLastError());
     }
     SNN_TRY(scan_inclusive_max_i32(headpos, runstart, E, ar, s));
     if (E > 0) {
-        k_dedup_rep<<<ge, 256, 0, s>>>(E, keys, vals, runstart, L.hoff, tpins, tlen, tsd, rep, head);
+        SNN_L k_dedup_rep<<<ge, 256, 0, s>>>(E, keys, vals, runstart, L.hoff, tpins, tlen, tsd, rep, head);
         SNN_CUDA(cudaGetLastError());
     }
     SNN_TRY(scan_exclusive_i32(head, gidh, E, (int32_t*)(h->d_scal + SC_B), ar, s));
@@ -294,10 +297,11 @@ Status contract_level(snnmap_hgraph* h)
         SNN_CUDA(cudaMemsetAsync(tw, 0, (size_t)E * sizeof(int64_t), s));
         SNN_CUDA(cudaMemsetAsync(tk, 0, (size_t)E * sizeof(int32_t), s));
         SNN_CUDA(cudaMemsetAsync(newlen, 0, (size_t)E * sizeof(int64_t), s));
-        k_dedup_accum<<<ge, 256, 0, s>>>(E, vals, rep, gidh, tlen, L.hw, L.hk, tw, tk, newlen, gid);
+        SNN_L k_dedup_accum<<<ge, 256, 0, s>>>(E, vals, rep, gidh, tlen, L.hw, L.hk, tw, tk, newlen, gid);
         SNN_CUDA(cudaGetLastError());
     }
     SNN_TRY(scan_exclusive_i64(newlen, newoff, E, h->d_scal + SC_C, ar, s));
+    prof.reset();
     SNN_TRY(read_scalars(h));
     int32_t V2 = (int32_t)(h->h_scal[SC_A] & 0xffffffff);
     int32_t E2 = (int32_t)(h->h_scal[SC_B] & 0xffffffff);
@@ -311,6 +315,7 @@ Status contract_level(snnmap_hgraph* h)
     Level& Lp = h->levels[h->levels.size() - 2];
     SNN_TRY(level_alloc(h, N, NX, V2, E2, P2));
     N.maxlen = Lp.maxlen;
+    prof.reset(new ProfScope(h, PS_CONTRACT));
     if (V2 > 0) {
         SNN_CUDA(cudaMemcpyAsync(N.vsize, ns.size, (size_t)V2 * 4, cudaMemcpyDeviceToDevice, s));
         SNN_CUDA(cudaMemcpyAsync(N.vinpins, ns.inpins, (size_t)V2 * 4, cudaMemcpyDeviceToDevice, s));
@@ -318,16 +323,19 @@ Status contract_level(snnmap_hgraph* h)
         SNN_CUDA(cudaMemcpyAsync(N.vinint, ns.inint, (size_t)V2 * 4, cudaMemcpyDeviceToDevice, s));
     }
     if (E > 0) {
-        k_dedup_emit<<<grid_for((int64_t)E * 32, 256), 256, 0, s>>>(
+        SNN_L k_dedup_emit<<<grid_for((int64_t)E * 32, 256), 256, 0, s>>>(
             E, vals, rep, gid, Lp.hoff, tpins, tlen, tsd, tw, tk, newoff, N);
         SNN_CUDA(cudaGetLastError());
     }
-    k_set_off_end<<<1, 1, 0, s>>>(N.hoff, E2, P2);
+    SNN_L k_set_off_end<<<1, 1, 0, s>>>(N.hoff, E2, P2);
     SNN_CUDA(cudaGetLastError());
+    prof.reset();
     SNN_TRY(build_incidence(h, N));
-    SNN_TRY(seg_classify(N.hoff, E2, N.maxlen, NX.seg, ar, s));
+    SNN_CUDA(cudaMemsetAsync(h->d_scal + SC_W2, 0, sizeof(int64_t), s));
+    SNN_TRY(seg_classify(N.hoff, E2, N.maxlen, NX.seg, ar, s, h->d_scal + SC_W2));
     h->have_matching = false;
-    SNN_CUDA(cudaStreamSynchronize(s));
+    SNN_TRY(read_scalars(h));
+    NX.pair_terms = h->h_scal[SC_W2];
     ar.reset();
     return Status{};
 }

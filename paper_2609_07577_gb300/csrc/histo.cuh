@@ -172,7 +172,7 @@ __global__ void k_init_tables(unsigned char* g, int blocks, int64_t cap)
 template <typename S>
 inline Status init_global_tables(unsigned char* g, int blocks, int64_t cap, cudaStream_t s)
 {
-    k_init_tables<S><<<grid_for(blocks * cap, 256), 256, 0, s>>>(g, blocks, cap);
+    SNN_L k_init_tables<S><<<grid_for(blocks * cap, 256), 256, 0, s>>>(g, blocks, cap);
     SNN_CUDA(cudaGetLastError());
     return Status{};
 }

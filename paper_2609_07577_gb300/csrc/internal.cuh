@@ -12,12 +12,21 @@ namespace snn {
 enum Scalar : int {
     SC_STATUS = 0,   // int32 status bits live in the low word of this slot
     SC_A, SC_B, SC_C, SC_D, SC_E, SC_F, SC_G,
+    SC_W2 = 9,       // pair terms of the level being classified
     SC_COUNT = 16,
 };
 
 struct LevelExtra {
-    SegBuckets seg;     // hyperedge size buckets
+    SegBuckets seg;          // hyperedge size buckets
+    int64_t pair_terms = 0;  // sum of |e|(|e|-1)
 };
+
+// pipeline stages timed by the profiler
+enum ProfStage : int {
+    PS_BUILD, PS_AFFINITY, PS_MATCH, PS_CONTRACT, PS_INCIDENCE, PS_PINCOUNT, PS_GAINS,
+    PS_SORTMOVES, PS_REPLAY, PS_VALIDITY, PS_APPLY, PS_N
+};
+extern const char* const kStageNames[PS_N];
 
 }  // namespace snn
 
@@ -41,9 +50,31 @@ struct snnmap_hgraph {
     bool wide = false;           // some neighbour score may reach 2^32
     std::vector<snnmap_round_log> rlog;
     std::vector<snnmap_level_log> llog;
+    // profiler
+    bool prof_on = false;
+    struct Pend {
+        int stage;
+        cudaEvent_t a, b;
+    };
+    std::vector<Pend> prof_pend;
+    std::vector<cudaEvent_t> prof_pool;
+    double prof_ms[snn::PS_N] = {};
+    int64_t prof_calls[snn::PS_N] = {};
 };
 
 namespace snn {
+
+// Times the enclosed launches of one stage with a pair of events.
+struct ProfScope {
+    snnmap_hgraph* h;
+    int stage;
+    cudaEvent_t a = nullptr, b = nullptr;
+    ProfScope(snnmap_hgraph* h_, int stage_);
+    ~ProfScope();
+};
+// folds finished event pairs into the counters (call after a stream sync)
+void prof_collect(snnmap_hgraph* h);
+void prof_release(snnmap_hgraph* h);
 
 // scalars: copy the SC_COUNT slots device->host and synchronize the stream
 Status read_scalars(snnmap_hgraph* h);

@@ -5,9 +5,14 @@
 // stable scatter whose in-tile ranks come from warp match_any groups.
 #include "common.cuh"
 
+#include <atomic>
 #include <climits>
 
 namespace snn {
+
+static std::atomic<int64_t> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 // ---------------------------------------------------------------------------
 // Arena
@@ -98,7 +103,7 @@ __global__ void k_iota(int32_t* p, int64_t n)
 Status fill_i32(int32_t* p, int32_t v, int64_t n, cudaStream_t s)
 {
     if (n <= 0) return Status{};
-    k_fill<int32_t><<<grid_for(n, 256), 256, 0, s>>>(p, v, n);
+    SNN_L k_fill<int32_t><<<grid_for(n, 256), 256, 0, s>>>(p, v, n);
     SNN_CUDA(cudaGetLastError());
     return Status{};
 }
@@ -106,7 +111,7 @@ Status fill_i32(int32_t* p, int32_t v, int64_t n, cudaStream_t s)
 Status fill_i64(int64_t* p, int64_t v, int64_t n, cudaStream_t s)
 {
     if (n <= 0) return Status{};
-    k_fill<int64_t><<<grid_for(n, 256), 256, 0, s>>>(p, v, n);
+    SNN_L k_fill<int64_t><<<grid_for(n, 256), 256, 0, s>>>(p, v, n);
     SNN_CUDA(cudaGetLastError());
     return Status{};
 }
@@ -114,7 +119,7 @@ Status fill_i64(int64_t* p, int64_t v, int64_t n, cudaStream_t s)
 Status iota_i32(int32_t* p, int64_t n, cudaStream_t s)
 {
     if (n <= 0) return Status{};
-    k_iota<<<grid_for(n, 256), 256, 0, s>>>(p, n);
+    SNN_L k_iota<<<grid_for(n, 256), 256, 0, s>>>(p, n);
     SNN_CUDA(cudaGetLastError());
     return Status{};
 }
@@ -255,23 +260,23 @@ static Status scan_impl(const Tin* in, T* out, int64_t n, T* total, Arena& ar, c
 {
     if (n <= 0) {
         if (total) {
-            k_set_identity<T, Op><<<1, 1, 0, s>>>(total);
+            SNN_L k_set_identity<T, Op><<<1, 1, 0, s>>>(total);
             SNN_CUDA(cudaGetLastError());
         }
         return Status{};
     }
     int64_t nb = ceil_div(n, SC_TILE);
     if (nb == 1) {
-        k_scan_tile<Tin, T, Op, INCL><<<1, SC_THREADS, 0, s>>>(in, n, out, nullptr, total);
+        SNN_L k_scan_tile<Tin, T, Op, INCL><<<1, SC_THREADS, 0, s>>>(in, n, out, nullptr, total);
         SNN_CUDA(cudaGetLastError());
         return Status{};
     }
     T* bsum = nullptr;
     SNN_TRY(ar.alloc(&bsum, nb));
-    k_scan_reduce<Tin, T, Op><<<(unsigned)nb, SC_THREADS, 0, s>>>(in, n, bsum);
+    SNN_L k_scan_reduce<Tin, T, Op><<<(unsigned)nb, SC_THREADS, 0, s>>>(in, n, bsum);
     SNN_CUDA(cudaGetLastError());
     SNN_TRY((scan_impl<T, T, Op, false>(bsum, bsum, nb, nullptr, ar, s)));
-    k_scan_tile<Tin, T, Op, INCL><<<(unsigned)nb, SC_THREADS, 0, s>>>(in, n, out, bsum, total);
+    SNN_L k_scan_tile<Tin, T, Op, INCL><<<(unsigned)nb, SC_THREADS, 0, s>>>(in, n, out, bsum, total);
     SNN_CUDA(cudaGetLastError());
     return Status{};
 }
@@ -401,12 +406,12 @@ Status radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint
     uint32_t *vi = vals, *vo = vals_alt;
     for (int p = 0; p < passes; p++) {
         int shift = 8 * p;
-        k_rs_upsweep<<<nblk, RS_THREADS, 0, s>>>(ki, n, shift, counts, nblk);
+        SNN_L k_rs_upsweep<<<nblk, RS_THREADS, 0, s>>>(ki, n, shift, counts, nblk);
         SNN_CUDA(cudaGetLastError());
         SNN_TRY((scan_impl<uint32_t, uint32_t, OpSum<uint32_t>, false>(counts, counts,
                                                                       (int64_t)256 * nblk,
                                                                       nullptr, ar, s)));
-        k_rs_downsweep<<<nblk, RS_THREADS, 0, s>>>(ki, vi, ko, vo, n, shift, counts, nblk);
+        SNN_L k_rs_downsweep<<<nblk, RS_THREADS, 0, s>>>(ki, vi, ko, vo, n, shift, counts, nblk);
         SNN_CUDA(cudaGetLastError());
         uint64_t* tk = ki; ki = ko; ko = tk;
         uint32_t* tv = vi; vi = vo; vo = tv;

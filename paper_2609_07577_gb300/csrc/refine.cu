@@ -33,6 +33,7 @@
 
 #include <algorithm>
 #include <climits>
+#include <memory>
 
 namespace snn {
 
@@ -83,7 +84,7 @@ Status project(snnmap_hgraph* h, int32_t level, const int32_t* rho_coarse, int32
 {
     Level& L = h->levels[level];
     if (L.V > 0) {
-        k_project<<<grid_for(L.V, 256), 256, 0, h->stream>>>(L.V, L.cid, rho_coarse, rho_fine);
+        SNN_L k_project<<<grid_for(L.V, 256), 256, 0, h->stream>>>(L.V, L.cid, rho_coarse, rho_fine);
         SNN_CUDA(cudaGetLastError());
     }
     return Status{};
@@ -761,10 +762,10 @@ static Status gains(snnmap_hgraph* h, Level& L, const PinCounts& pc, const int32
         attrs = true;
     }
     int grid = (int)std::min<int64_t>(ceil_div(V, GAIN_WARPS), 152 * 3 * 8);
-    k_gain_warp<S><<<grid, GAIN_WARPS * 32, wsm, s>>>(L, pc, rho, ps, p.omega, p.delta, p.phi, pto,
+    SNN_L k_gain_warp<S><<<grid, GAIN_WARPS * 32, wsm, s>>>(L, pc, rho, ps, p.omega, p.delta, p.phi, pto,
                                                        pgain, heavy, slots);
     SNN_CUDA(cudaGetLastError());
-    k_gain_block<S><<<152, GAIN_BTHREADS, bsm, s>>>(L, pc, rho, ps, p.omega, p.delta, p.phi, pto,
+    SNN_L k_gain_block<S><<<152, GAIN_BTHREADS, bsm, s>>>(L, pc, rho, ps, p.omega, p.delta, p.phi, pto,
                                                      pgain, heavy, slots, heavy2, slots + 1,
                                                      nullptr, 0);
     SNN_CUDA(cudaGetLastError());
@@ -781,7 +782,7 @@ static Status gains(snnmap_hgraph* h, Level& L, const PinCounts& pc, const int32
         unsigned char* gtab;
         SNN_TRY(ar.alloc(&gtab, blocks * per));
         SNN_TRY(init_global_tables<S>(gtab, blocks, cap, s));
-        k_gain_block<S><<<blocks, GAIN_BTHREADS, 0, s>>>(L, pc, rho, ps, p.omega, p.delta, p.phi,
+        SNN_L k_gain_block<S><<<blocks, GAIN_BTHREADS, 0, s>>>(L, pc, rho, ps, p.omega, p.delta, p.phi,
                                                           pto, pgain, heavy2, slots + 1, nullptr,
                                                           nullptr, gtab, cap);
         SNN_CUDA(cudaGetLastError());
@@ -806,7 +807,7 @@ static Status pin_counts(snnmap_hgraph* h, Level& L, LevelExtra& X, int32_t K, c
     SNN_CUDA(cudaMemsetAsync(ps.inpins, 0, (size_t)K * 8, s));
     SNN_CUDA(cudaMemsetAsync(ps.pincnt, 0, (size_t)K * 8, s));
     if (L.V > 0) {
-        k_pstate_vertices<<<grid_for(L.V, 256), 256, 0, s>>>(L, rho, ps);
+        SNN_L k_pstate_vertices<<<grid_for(L.V, 256), 256, 0, s>>>(L, rho, ps);
         SNN_CUDA(cudaGetLastError());
     }
     PinCountJob job{L.hoff, L.hpins, L.hsd, L.hk, L.hw, rho, pc, ps.pincnt, h->d_scal};
@@ -844,14 +845,18 @@ static Status refine_round(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* 
     *applied = 0;
     *gain = 0;
     SNN_TRY(zero_scalars(h));
-    k_round_init<<<1, 1, 0, s>>>(h->d_scal);
+    SNN_L k_round_init<<<1, 1, 0, s>>>(h->d_scal);
     SNN_CUDA(cudaGetLastError());
 
     PinCounts pc;
     PState ps;
-    SNN_TRY(pin_counts(h, L, X, K, rho, pc, ps));
-    k_check_pstate<<<grid_for(K, 256), 256, 0, s>>>(K, ps, prm.omega, prm.delta, prm.phi, h->d_scal);
-    SNN_CUDA(cudaGetLastError());
+    {
+        ProfScope prof(h, PS_PINCOUNT);
+        SNN_TRY(pin_counts(h, L, X, K, rho, pc, ps));
+        SNN_L k_check_pstate<<<grid_for(K, 256), 256, 0, s>>>(K, ps, prm.omega, prm.delta, prm.phi, h->d_scal);
+        SNN_CUDA(cudaGetLastError());
+    }
+    std::unique_ptr<ProfScope> prof(new ProfScope(h, PS_GAINS));
 
     int32_t *pto, *flag, *pos;
     int64_t* pgain;
@@ -865,9 +870,10 @@ static Status refine_round(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* 
         SNN_TRY(gains<uint32_t>(h, L, pc, rho, ps, pto, pgain));
     }
     int gv = grid_for(V, 256);
-    k_prop_stats<<<gv, 256, 0, s>>>(L, pto, pgain, flag, h->d_scal);
+    SNN_L k_prop_stats<<<gv, 256, 0, s>>>(L, pto, pgain, flag, h->d_scal);
     SNN_CUDA(cudaGetLastError());
     SNN_TRY(scan_exclusive_i32(flag, pos, V, (int32_t*)(h->d_scal + RS_M), ar, s));
+    prof.reset();
     SNN_TRY(read_scalars(h));
     *cost = h->h_scal[RS_COST];
     if (h->h_scal[SC_STATUS] & ST_BADSTATE)
@@ -879,13 +885,14 @@ static Status refine_round(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* 
     if (M == 0) return Status{};
 
     // S8
+    prof.reset(new ProfScope(h, PS_SORTMOVES));
     uint64_t *keys, *keys2;
     uint32_t *vals, *vals2;
     SNN_TRY(ar.alloc(&keys, M));
     SNN_TRY(ar.alloc(&keys2, M));
     SNN_TRY(ar.alloc(&vals, M));
     SNN_TRY(ar.alloc(&vals2, M));
-    k_prop_keys<<<gv, 256, 0, s>>>(V, pto, pgain, pos, maxg, keys, vals);
+    SNN_L k_prop_keys<<<gv, 256, 0, s>>>(V, pto, pgain, pos, maxg, keys, vals);
     SNN_CUDA(cudaGetLastError());
     SNN_TRY(radix_sort_pairs(keys, vals, keys2, vals2, M, bits_for((uint64_t)maxg), ar, s));
     Moves mv;
@@ -893,10 +900,11 @@ static Status refine_round(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* 
     SNN_TRY(ar.alloc(&mv.from, M));
     SNN_TRY(ar.alloc(&mv.to, M));
     int gm = grid_for(M, 256);
-    k_moves<<<gm, 256, 0, s>>>(M, vals, rho, pto, mv, moveidx);
+    SNN_L k_moves<<<gm, 256, 0, s>>>(M, vals, rho, pto, mv, moveidx);
     SNN_CUDA(cudaGetLastError());
 
     // S9
+    prof.reset(new ProfScope(h, PS_REPLAY));
     int64_t *gp, *G;
     int32_t *dv, *nviol;
     SNN_TRY(ar.alloc(&gp, M));
@@ -913,7 +921,7 @@ static Status refine_round(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* 
     SNN_TRY(ar.alloc(&ev.dsize, ev.cap));
     SNN_TRY(ar.alloc(&ev.dinp, ev.cap));
     SNN_TRY(ar.alloc(&ev.dpc, ev.cap));
-    k_size_events<<<gm, 256, 0, s>>>(M, mv, L, ev);
+    SNN_L k_size_events<<<gm, 256, 0, s>>>(M, mv, L, ev);
     SNN_CUDA(cudaGetLastError());
     uint32_t* mvbuf;
     int32_t *hv, *hvc;
@@ -921,19 +929,21 @@ static Status refine_round(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* 
     SNN_TRY(ar.alloc(&hv, L.E));
     SNN_TRY(ar.alloc(&hvc, L.E));
     if (L.E > 0) {
-        k_replay_warp<<<grid_for((int64_t)L.E * 32, 256), 256, 0, s>>>(L, pc, moveidx, mv, mvbuf, gp,
+        SNN_L k_replay_warp<<<grid_for((int64_t)L.E * 32, 256), 256, 0, s>>>(L, pc, moveidx, mv, mvbuf, gp,
                                                                       ev, 2 * (int64_t)M, hv, hvc,
                                                                       h->d_scal);
         SNN_CUDA(cudaGetLastError());
-        k_replay_block<<<152 * 2, 256, 0, s>>>(L, pc, mv, mvbuf, gp, ev, 2 * (int64_t)M, hv, hvc,
+        SNN_L k_replay_block<<<152 * 2, 256, 0, s>>>(L, pc, mv, mvbuf, gp, ev, 2 * (int64_t)M, hv, hvc,
                                                h->d_scal);
         SNN_CUDA(cudaGetLastError());
     }
+    prof.reset();
     SNN_TRY(read_scalars(h));
     if (h->h_scal[SC_STATUS] & ST_CAPACITY) return Status{SNNMAP_ERR_CUDA, "event buffer overflow"};
     int64_t T = 2 * (int64_t)M + h->h_scal[RS_NEV];
 
     // S10
+    prof.reset(new ProfScope(h, PS_VALIDITY));
     uint64_t* ekey2;
     uint32_t* eidx2;
     SNN_TRY(ar.alloc(&ekey2, T));
@@ -945,19 +955,21 @@ static Status refine_round(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* 
     SNN_TRY(ar.alloc(&pend, K));
     SNN_CUDA(cudaMemsetAsync(pbeg, 0, (size_t)K * 4, s));
     SNN_CUDA(cudaMemsetAsync(pend, 0, (size_t)K * 4, s));
-    k_part_bounds<<<grid_for(T, 256), 256, 0, s>>>(T, ev.key, ev.ibits, pbeg, pend);
+    SNN_L k_part_bounds<<<grid_for(T, 256), 256, 0, s>>>(T, ev.key, ev.ibits, pbeg, pend);
     SNN_CUDA(cudaGetLastError());
-    k_part_validity<<<grid_for((int64_t)K * 32, 256), 256, 0, s>>>(K, pbeg, pend, ev, ps, prm.omega,
+    SNN_L k_part_validity<<<grid_for((int64_t)K * 32, 256), 256, 0, s>>>(K, pbeg, pend, ev, ps, prm.omega,
                                                                   prm.delta, prm.phi, dv);
     SNN_CUDA(cudaGetLastError());
 
     // S11
+    prof.reset(new ProfScope(h, PS_APPLY));
     SNN_TRY(scan_inclusive_i64(gp, G, M, ar, s));
     SNN_TRY(scan_inclusive_i32(dv, nviol, M, ar, s));
-    k_best1<<<gm, 256, 0, s>>>(M, G, nviol, h->d_scal);
-    k_best2<<<gm, 256, 0, s>>>(M, G, nviol, h->d_scal);
-    k_apply<<<gm, 256, 0, s>>>(M, mv, rho, moveidx, h->d_scal);
+    SNN_L k_best1<<<gm, 256, 0, s>>>(M, G, nviol, h->d_scal);
+    SNN_L k_best2<<<gm, 256, 0, s>>>(M, G, nviol, h->d_scal);
+    SNN_L k_apply<<<gm, 256, 0, s>>>(M, mv, rho, moveidx, h->d_scal);
     SNN_CUDA(cudaGetLastError());
+    prof.reset();
     SNN_TRY(read_scalars(h));
     int64_t best = h->h_scal[RS_BEST];
     int64_t istar = h->h_scal[RS_ISTAR];
@@ -982,7 +994,7 @@ Status check_rho(snnmap_hgraph* h, int32_t level, int32_t K, const int32_t* rho)
     Level& L = h->levels[level];
     SNN_TRY(zero_scalars(h));
     if (L.V > 0) {
-        k_check_rho<<<grid_for(L.V, 256), 256, 0, h->stream>>>(L.V, rho, K, h->d_scal);
+        SNN_L k_check_rho<<<grid_for(L.V, 256), 256, 0, h->stream>>>(L.V, rho, K, h->d_scal);
         SNN_CUDA(cudaGetLastError());
     }
     SNN_TRY(read_scalars(h));

@@ -166,8 +166,9 @@ __global__ void k_seg_big(Job job, const int32_t* __restrict__ lists,
 
 // Builds the bucket lists of a level (device-only; list holds E ids, meta 8
 // ints, both caller-allocated).
+// Also adds sum |e|(|e|-1) over the level's hyperedges to *w2 (device).
 Status seg_classify(const int64_t* hoff, int32_t E, int32_t maxlen, SegBuckets& b, Arena& ar,
-                    cudaStream_t s);
+                    cudaStream_t s, int64_t* w2);
 
 // Grid sizes for the four bucket kernels.
 inline int seg_grid_small(int32_t E) { return grid_for((int64_t)E * 32, 256, 152 * 16); }
@@ -177,9 +178,9 @@ template <class Job>
 Status seg_run(const Job& job, const SegBuckets& b, int32_t E, Arena& ar, cudaStream_t s)
 {
     if (E <= 0) return Status{};
-    k_seg_b0<Job><<<seg_grid_small(E), 256, 0, s>>>(job, b.list, b.meta);
+    SNN_L k_seg_b0<Job><<<seg_grid_small(E), 256, 0, s>>>(job, b.list, b.meta);
     SNN_CUDA(cudaGetLastError());
-    k_seg_b1<Job><<<seg_grid_small(E), 256, 0, s>>>(job, b.list, b.meta);
+    SNN_L k_seg_b1<Job><<<seg_grid_small(E), 256, 0, s>>>(job, b.list, b.meta);
     SNN_CUDA(cudaGetLastError());
     {
         static bool attr_set = false;
@@ -189,14 +190,14 @@ Status seg_run(const Job& job, const SegBuckets& b, int32_t E, Arena& ar, cudaSt
                                           (int)smem));
             attr_set = true;
         }
-        k_seg_big<Job><<<seg_grid_big(E), SEG_B2_THREADS, smem, s>>>(job, b.list, b.meta, 2,
+        SNN_L k_seg_big<Job><<<seg_grid_big(E), SEG_B2_THREADS, smem, s>>>(job, b.list, b.meta, 2,
                                                                       nullptr, 0);
         SNN_CUDA(cudaGetLastError());
     }
     if (b.b3_cap > 0) {
         uint32_t* g = nullptr;
         SNN_TRY(ar.alloc(&g, (int64_t)SEG_B3_BLOCKS * b.b3_cap));
-        k_seg_big<Job><<<SEG_B3_BLOCKS, SEG_B3_THREADS, 0, s>>>(job, b.list, b.meta, 3, g,
+        SNN_L k_seg_big<Job><<<SEG_B3_BLOCKS, SEG_B3_THREADS, 0, s>>>(job, b.list, b.meta, 3, g,
                                                                  b.b3_cap);
         SNN_CUDA(cudaGetLastError());
     }
