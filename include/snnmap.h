@@ -183,6 +183,16 @@ int snnmap_partition(snnmap_hgraph* h, void* stream, int32_t* d_rho_out, int64_t
                      snnmap_stats* stats);
 
 /*
+ * Connectivity of a partition of the level-0 neurons (Sec. 3, Eq.
+ * connectivity): sum over axons of omega(e) * (distinct partitions among its
+ * pins - 1). d_rho: int32[n_vertices] device, values in [0, n_parts)
+ * (SNNMAP_ERR_INVALID otherwise). Uses the same per-axon pin-count pass as
+ * refinement; temporaries come from the handle's scratch memory.
+ */
+int snnmap_connectivity(snnmap_hgraph* h, int32_t n_parts, const int32_t* d_rho, void* stream,
+                        int64_t* cost_out);
+
+/*
  * Convenience for callers holding host arrays: copies the SNN hypergraph
  * (same layout as snnmap_build_hgraph, host memory) to the device, runs
  * snnmap_partition and copies the partition back into h_rho_out

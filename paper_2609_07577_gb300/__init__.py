@@ -8,7 +8,7 @@ convenience layer that keeps inputs in torch device tensors.
 from ._native import (  # noqa: F401
     Params, Stats, SnnmapError, lib,
     snnmap_default_params, snnmap_build_hgraph, snnmap_coarsen_level, snnmap_contract,
-    snnmap_num_levels, snnmap_level_dims, snnmap_project, snnmap_refine, snnmap_partition,
+    snnmap_num_levels, snnmap_level_dims, snnmap_project, snnmap_refine, snnmap_partition, snnmap_connectivity,
     snnmap_partition_host, snnmap_level_copy, snnmap_last_matching, snnmap_level_cid,
     snnmap_round_logs, snnmap_level_logs, snnmap_device_bytes, snnmap_free, snnmap_last_error,
     snnmap_profile, snnmap_stage_times, snnmap_launch_count,

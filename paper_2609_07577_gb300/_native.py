@@ -64,6 +64,7 @@ _SIGS = {
     "snnmap_project": (C.c_int, [_vp, _i32, _vp, _vp, _vp]),
     "snnmap_refine": (C.c_int, [_vp, _i32, _i32, _vp, _vp, C.POINTER(_i64)]),
     "snnmap_partition": (C.c_int, [_vp, _vp, _vp, C.POINTER(_i64), C.POINTER(Stats)]),
+    "snnmap_connectivity": (C.c_int, [_vp, _i32, _vp, _vp, C.POINTER(_i64)]),
     "snnmap_partition_host": (C.c_int, [C.POINTER(Params), _i32, _i32, _vp, _vp, _vp, _vp,
                                         C.POINTER(_i64), C.POINTER(Stats), _vp]),
     "snnmap_level_copy": (C.c_int, [_vp, _i32] + [_vp] * 9 + [_vp]),
@@ -173,6 +174,12 @@ def snnmap_partition(h, d_rho_out, stream=None):
     st = Stats()
     check(lib().snnmap_partition(h, _stream(stream), _p(d_rho_out), C.byref(c), C.byref(st)))
     return c.value, st.as_dict()
+
+
+def snnmap_connectivity(h, n_parts, d_rho, stream=None):
+    c = C.c_int64()
+    check(lib().snnmap_connectivity(h, int(n_parts), _p(d_rho), _stream(stream), C.byref(c)))
+    return c.value
 
 
 def snnmap_partition_host(params, n_vertices, n_hedges, h_offsets, h_pins, h_w, h_rho_out,

@@ -248,6 +248,18 @@ int snnmap_refine(snnmap_hgraph* h, int32_t level, int32_t n_parts, int32_t* d_r
     return SNNMAP_OK;
 }
 
+int snnmap_connectivity(snnmap_hgraph* h, int32_t n_parts, const int32_t* d_rho, void* stream,
+                        int64_t* cost_out)
+{
+    g_err.clear();
+    if (!h || !h->levels.size() || !cost_out) return fail(SNNMAP_ERR_INVALID, "NULL argument");
+    if (n_parts < 1 || !is_device_ptr(d_rho)) return fail(SNNMAP_ERR_INVALID, "bad rho / n_parts");
+    bind(h, stream);
+    API_TRY(snn::check_rho(h, 0, n_parts, d_rho));
+    API_TRY(snn::level_cost(h, 0, n_parts, d_rho, cost_out));
+    return SNNMAP_OK;
+}
+
 int snnmap_partition(snnmap_hgraph* h, void* stream, int32_t* d_rho_out, int64_t* cost_out,
                      snnmap_stats* stats)
 {

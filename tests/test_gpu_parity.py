@@ -124,3 +124,25 @@ def test_empty_and_degenerate():
     rho, cost, st = partition(hg)
     assert cost == cost_o == 0 and np.array_equal(rho, rho_o)
     assert st["levels"] == st_o["levels"]
+
+
+def test_connectivity_entry_point():
+    """S12 as its own call: Conn of arbitrary partitions equals the oracle's."""
+    from paper_2609_07577_gb300 import HGraph, SnnmapError, snnmap_connectivity
+    import paper_2609_07577_gb300._native as N
+    rng = np.random.default_rng(5)
+    for name in ("cfg1s", "cfg3s"):
+        hg = snngen.by_name(name)
+        L = oracle.Level.from_hypergraph(hg)
+        G = HGraph.from_hypergraph(hg)
+        try:
+            for K in (1, 7, 300, hg.V):
+                rho = rng.integers(0, K, size=hg.V).astype(np.int32)
+                got = snnmap_connectivity(G.handle, K, torch.from_numpy(rho).cuda())
+                assert got == L.conn(rho), (name, K)
+            bad = torch.full((hg.V,), 5, dtype=torch.int32, device="cuda")
+            with pytest.raises(SnnmapError) as e:
+                snnmap_connectivity(G.handle, 5, bad)
+            assert e.value.code == N.ERR_INVALID
+        finally:
+            G.close()
