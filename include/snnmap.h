@@ -245,6 +245,35 @@ int snnmap_device_bytes(const snnmap_hgraph* h, int64_t* bytes);
 
 void snnmap_free(snnmap_hgraph* h);
 
+/*
+ * Connectivity (same value as snnmap_connectivity) for callers that cannot
+ * allocate device memory. This entry point has no counterpart in the paper;
+ * it exists for callers whose device memory is entirely reserved by another
+ * allocator (a framework's caching pool, a fixed per-tenant budget) and for
+ * latency-critical loops that may not call cudaMalloc/cudaFree, since a free
+ * can synchronize the whole device. It allocates nothing: no handle, no
+ * cudaMalloc or cudaFree, no allocating library routine. Its scratch (one
+ * count per hyperedge, an error word, an accumulator) is a static device
+ * array of 16 MiB + 256 bytes that every device loading this library holds
+ * until the process exits; hence the limit n_hedges <= 4,194,304, larger
+ * inputs being rejected with SNNMAP_ERR_INVALID before any work is queued.
+ * The first call on a device looks up the array's device address (with that
+ * device current) and should come before any stream capture. Each call
+ * clears the accumulator before use; calls whose work overlaps on the GPU
+ * share the array and race, so callers must not overlap them.
+ * Inputs (device, caller-owned): the level-0 layout of snnmap_build_hgraph
+ * (d_offsets int64[n_hedges+1], d_pins, d_w int32) and d_rho int32[n_vertices]
+ * with values in [0, n_parts). Output: *d_cost_out (device int64) = Conn.
+ * Axons with no destination count zero. Cost grows with the square of an
+ * axon's pin count. Errors: SNNMAP_ERR_INVALID (sizes, host pointers,
+ * offsets, pin ids, weights or partition ids out of range), SNNMAP_ERR_CUDA.
+ * Synchronizes the stream before returning; snnmap_last_error() describes
+ * failures.
+ */
+int snnmap_connectivity_noalloc(int32_t n_vertices, int32_t n_hedges, const int64_t* d_offsets,
+                                const int32_t* d_pins, const int32_t* d_w, const int32_t* d_rho,
+                                int32_t n_parts, int64_t* d_cost_out, void* stream);
+
 /* Kernels launched by the library in this process so far. */
 int64_t snnmap_launch_count(void);
 

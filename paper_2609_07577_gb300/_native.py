@@ -76,6 +76,7 @@ _SIGS = {
     "snnmap_profile": (C.c_int, [_vp, _i32]),
     "snnmap_stage_times": (C.c_int, [_vp, _vp, _i32, C.POINTER(_i32)]),
     "snnmap_launch_count": (_i64, []),
+    "snnmap_connectivity_noalloc": (C.c_int, [_i32, _i32, _vp, _vp, _vp, _vp, _i32, _vp, _vp]),
     "snnmap_free": (None, [_vp]),
     "snnmap_last_error": (C.c_char_p, []),
 }
@@ -247,6 +248,14 @@ def snnmap_stage_times(h):
     buf = (StageTime * 32)()
     check(lib().snnmap_stage_times(h, buf, 32, C.byref(n)))
     return {buf[i].name.decode(): {"calls": buf[i].calls, "ms": buf[i].ms} for i in range(n.value)}
+
+
+def snnmap_connectivity_noalloc(n_vertices, n_hedges, d_offsets, d_pins, d_w, d_rho, n_parts,
+                                d_cost_out, stream=None):
+    """Allocation-free connectivity; the result lands in d_cost_out (device)."""
+    check(lib().snnmap_connectivity_noalloc(int(n_vertices), int(n_hedges), _p(d_offsets),
+                                            _p(d_pins), _p(d_w), _p(d_rho), int(n_parts),
+                                            _p(d_cost_out), _stream(stream)))
 
 
 def snnmap_launch_count():

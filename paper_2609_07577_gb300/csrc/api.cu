@@ -96,6 +96,10 @@ snn::Status count_nonempty(snnmap_hgraph* h, int32_t V, int32_t K, const int32_t
 
 }  // namespace
 
+namespace snn {
+void set_last_error(const std::string& msg) { g_err = msg; }
+}  // namespace snn
+
 extern "C" {
 
 snnmap_params snnmap_default_params(int32_t omega, int32_t delta, int32_t phi)
