@@ -82,6 +82,8 @@ typedef struct {
     int32_t n_cand;      /* vertices with a valid candidate */
     int32_t n_pairs;     /* matched pairs */
     int64_t pair_terms;  /* sum over hyperedges of |e|(|e|-1): neighbour-histogram updates */
+    int32_t n_block;     /* vertices whose histogram needed a block-wide table */
+    int32_t n_global;    /* vertices whose histogram needed a table in global memory */
 } snnmap_level_log;
 
 /* Device time of one pipeline stage, summed over the calls since the last

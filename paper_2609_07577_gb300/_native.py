@@ -35,7 +35,8 @@ class RoundLog(C.Structure):
 
 class LevelLog(C.Structure):
     _fields_ = [("V", C.c_int32), ("E", C.c_int32), ("P", C.c_int64), ("n_cand", C.c_int32),
-                ("n_pairs", C.c_int32), ("pair_terms", C.c_int64)]
+                ("n_pairs", C.c_int32), ("pair_terms", C.c_int64), ("n_block", C.c_int32),
+                ("n_global", C.c_int32)]
 
 
 class StageTime(C.Structure):

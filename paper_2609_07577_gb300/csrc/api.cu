@@ -185,7 +185,8 @@ int snnmap_coarsen_level(snnmap_hgraph* h, void* stream, int32_t* n_cand_out, in
     h->scratch.reset();
     if (!st.ok()) return fail(st);
     const snn::Level& L = h->levels.back();
-    h->llog.push_back(snnmap_level_log{L.V, L.E, L.P, nc, np, h->extra.back().pair_terms});
+    h->llog.push_back(snnmap_level_log{L.V, L.E, L.P, nc, np, h->extra.back().pair_terms,
+                                            h->extra.back().n_block, h->extra.back().n_global});
     *n_cand_out = nc;
     *n_pairs_out = np;
     return SNNMAP_OK;
@@ -282,7 +283,8 @@ int snnmap_partition(snnmap_hgraph* h, void* stream, int32_t* d_rho_out, int64_t
         h->scratch.reset();
         if (!s1.ok()) return fail(s1);
         const snn::Level& L = h->levels.back();
-        h->llog.push_back(snnmap_level_log{L.V, L.E, L.P, nc, np, h->extra.back().pair_terms});
+        h->llog.push_back(snnmap_level_log{L.V, L.E, L.P, nc, np, h->extra.back().pair_terms,
+                                            h->extra.back().n_block, h->extra.back().n_global});
         if (nc == 0 || np == 0) break;
         API_TRY(snn::contract_level(h));
     }

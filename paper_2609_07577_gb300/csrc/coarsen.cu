@@ -33,21 +33,44 @@
 
 namespace snn {
 
-constexpr int AFF_WARPS = 8;
-constexpr int AFF_T = 512;                 // slots per warp table
-constexpr int AFF_LOAD = AFF_T * 3 / 4;    // distinct neighbours before a warp gives up
-constexpr int AFF_BT = 8192;               // slots of the block shared table
-constexpr int AFF_BLOAD = AFF_BT * 3 / 4;
-constexpr int AFF_BTHREADS = 256;
 constexpr int MATCH_WALK = 64;
 
-// neighbour terms of vertex n: pins of its incident hyperedges
-template <typename S>
-struct AffVis {
-    const Level& L;
-    int32_t n;
-    const Table<S>& t;
-    __device__ Seg<S> seg(int64_t i) const
+// Neighbour histogram policy: for vertex n, every pin m != n of every
+// incident hyperedge a adds omega(a) to m's score and, when n and m are both
+// destinations of a, k(a) to their shared inbound count. The best neighbour
+// keeping the merged super-node within Omega, Phi and Delta wins.
+template <typename S_>
+struct AffPol {
+    using S = S_;
+    struct Acc {
+        __device__ Acc() {}
+        __device__ void add(const Acc&) {}
+        __device__ void atomic_into(Acc*) const {}
+    };
+    static __device__ Acc warp_reduce(const Acc& a) { return a; }
+
+    Level L;
+    int32_t V;
+    int64_t keys;
+    int32_t omega, delta, phi;
+    int32_t* cand;
+    int64_t* cscore;
+    int32_t* cov;
+    const int32_t* vmin;   // smallest size and inbound pins over the level's vertices
+
+    // n cannot merge even with the smallest vertex: no candidate
+    __device__ bool skip(int32_t n) const
+    {
+        return (int64_t)L.vsize[n] + vmin[0] > omega || (int64_t)L.vinpins[n] + vmin[1] > phi;
+    }
+    __device__ int64_t vb(int32_t n) const { return L.voff[n]; }
+    __device__ int64_t ve(int32_t n) const { return L.voff[n + 1]; }
+    __device__ int64_t seg_len(int64_t i) const
+    {
+        int32_t a = (int32_t)((uint32_t)L.vinc[i] & ~SRC_BIT);
+        return L.hoff[a + 1] - L.hoff[a];
+    }
+    __device__ Seg<S> seg(int64_t i, Acc&) const
     {
         uint32_t inc = (uint32_t)L.vinc[i];
         int32_t a = (int32_t)(inc & ~SRC_BIT);
@@ -60,185 +83,37 @@ struct AffVis {
         g.k = (uint32_t)L.hk[a];
         return g;
     }
-    __device__ bool elem(const Seg<S>& g, int32_t off) const
+    template <class Tb>
+    __device__ bool elem(int32_t n, const Seg<S>& g, int32_t off, const Tb& t, Acc&) const
     {
         int32_t m = L.hpins[g.b + off];
         if (m == n) return true;
+        // a neighbour whose size or inbound pins alone break Omega or Phi
+        // with n can never be the candidate: leave it out of the table
+        if ((int64_t)L.vsize[n] + L.vsize[m] > omega || (int64_t)L.vinpins[n] + L.vinpins[m] > phi)
+            return true;
         int md = off != 0 || g.sd;   // pin 0 is the source
         return t.add(m, g.w, (g.nd && md) ? g.k : 0u);
     }
-};
-
-// Best valid neighbour among the table's used slots [u0, nused) taken every
-// `stride`; resets those slots. Per-thread result.
-template <typename S>
-__device__ void scan_table(const Level& L, int32_t n, const Table<S>& t, int32_t u0, int32_t nused,
-                           int32_t stride, int32_t omega, int32_t delta, int32_t phi,
-                           int64_t& bs, int32_t& bm, uint32_t& bo)
-{
-    int64_t sz = L.vsize[n], ip = L.vinpins[n], ic = L.vincnt[n];
-    for (int32_t u = u0; u < nused; u += stride) {
-        int32_t slot = t.used[u];
-        int32_t m = t.key[slot];
-        int64_t s = (int64_t)t.sc[slot];
-        uint32_t o = t.ov[slot];
-        t.key[slot] = -1;
-        t.sc[slot] = 0;
-        t.ov[slot] = 0;
-        bool valid = sz + L.vsize[m] <= omega && ip + L.vinpins[m] <= phi &&
-                     ic + L.vincnt[m] - (int64_t)o <= delta;
-        if (valid && better(s, m, bs, bm)) {
+    __device__ void consider(int32_t n, int32_t m, int64_t s, uint32_t o, const Acc&, int64_t& bs,
+                             int32_t& bk, uint32_t& bo) const
+    {
+        bool valid = (int64_t)L.vsize[n] + L.vsize[m] <= omega &&
+                     (int64_t)L.vinpins[n] + L.vinpins[m] <= phi &&
+                     (int64_t)L.vincnt[n] + L.vincnt[m] - (int64_t)o <= delta;
+        if (valid && better(s, m, bs, bk)) {
             bs = s;
-            bm = m;
+            bk = m;
             bo = o;
         }
     }
-}
-
-template <typename S>
-__global__ void __launch_bounds__(AFF_WARPS * 32)
-    k_aff_warp(Level L, int32_t omega, int32_t delta, int32_t phi, int32_t* cand, int64_t* cscore,
-               int32_t* cov, int32_t* heavy, int64_t* scal)
-{
-    extern __shared__ unsigned char smem_raw[];
-    __shared__ int32_t nfill[AFF_WARPS];
-    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    Table<S> t = carve_table<S>(smem_raw + (size_t)warp * table_bytes<S>(AFF_T), AFF_T, &nfill[warp]);
-    for (int i = lane; i < AFF_T; i += 32) {
-        t.key[i] = -1;
-        t.sc[i] = 0;
-        t.ov[i] = 0;
+    __device__ void write(int32_t n, int64_t bs, int32_t bk, uint32_t bo, const Acc&) const
+    {
+        cand[n] = bk;
+        cscore[n] = bk < 0 ? 0 : bs;
+        cov[n] = bk < 0 ? 0 : (int32_t)bo;
     }
-    int64_t gw = blockIdx.x * (int64_t)AFF_WARPS + warp;
-    int64_t nw = (int64_t)gridDim.x * AFF_WARPS;
-    for (int64_t n = gw; n < L.V; n += nw) {
-        if (lane == 0) nfill[warp] = 0;
-        __syncwarp();
-        AffVis<S> vis{L, (int32_t)n, t};
-        bool ok = warp_flat_visit<S>(vis, L.voff[n], L.voff[n + 1], 32, &nfill[warp], AFF_LOAD);
-        __syncwarp();
-        int32_t nused = nfill[warp];
-        if (!ok || nused > AFF_T) {
-            // reset the whole table and hand the vertex to the block tier
-            for (int i = lane; i < AFF_T; i += 32) {
-                t.key[i] = -1;
-                t.sc[i] = 0;
-                t.ov[i] = 0;
-            }
-            if (lane == 0) {
-                int32_t pos = atomicAdd((int*)&scal[SC_E], 1);
-                heavy[pos] = (int32_t)n;
-            }
-            __syncwarp();
-            continue;
-        }
-        int64_t bs = 0;
-        int32_t bm = -1;
-        uint32_t bo = 0;
-        scan_table<S>(L, (int32_t)n, t, lane, nused, 32, omega, delta, phi, bs, bm, bo);
-        warp_argmax(bs, bm, bo);
-        if (lane == 0) {
-            cand[n] = bm;
-            cscore[n] = bm < 0 ? 0 : bs;
-            cov[n] = bm < 0 ? 0 : (int32_t)bo;
-        }
-        __syncwarp();
-    }
-}
-
-// Block tier: one block per listed vertex. Shared table (gtab == nullptr) or
-// a per-block slice of a global table of `cap` slots (key -1 / zero sums on
-// entry; every vertex resets what it used). Vertices overflowing the shared
-// table are appended to `next`.
-template <typename S>
-__global__ void __launch_bounds__(AFF_BTHREADS)
-    k_aff_block(Level L, int32_t omega, int32_t delta, int32_t phi, int32_t* cand,
-                int64_t* cscore, int32_t* cov, const int32_t* list, const int64_t* count_slot,
-                int32_t* next, int64_t* next_slot, unsigned char* gtab, int64_t cap)
-{
-    extern __shared__ unsigned char smem_raw[];
-    __shared__ int32_t nfill;
-    __shared__ int sh_fail;
-    __shared__ int64_t rs[AFF_BTHREADS / 32];
-    __shared__ int32_t rm[AFF_BTHREADS / 32];
-    __shared__ uint32_t ro[AFF_BTHREADS / 32];
-    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nwarps = AFF_BTHREADS / 32;
-    int64_t tcap = gtab ? cap : AFF_BT;
-    int32_t limit = gtab ? (int32_t)(cap - 1) : AFF_BLOAD;
-    Table<S> t = carve_table<S>(gtab ? gtab + (size_t)blockIdx.x * table_bytes<S>(cap) : smem_raw,
-                                (int32_t)tcap, &nfill);
-    if (!gtab) {
-        for (int i = threadIdx.x; i < AFF_BT; i += AFF_BTHREADS) {
-            t.key[i] = -1;
-            t.sc[i] = 0;
-            t.ov[i] = 0;
-        }
-    }
-    int32_t cnt = (int32_t)*count_slot;
-    for (int32_t idx = blockIdx.x; idx < cnt; idx += gridDim.x) {
-        int32_t n = list[idx];
-        if (threadIdx.x == 0) {
-            nfill = 0;
-            sh_fail = 0;
-        }
-        __syncthreads();
-        AffVis<S> vis{L, n, t};
-        bool ok = warp_flat_visit<S>(vis, L.voff[n] + 32 * warp, L.voff[n + 1], 32 * nwarps,
-                                     &nfill, limit);
-        if (!ok) atomicOr(&sh_fail, 1);
-        __syncthreads();
-        int32_t nused = nfill;
-        if (sh_fail || nused > limit) {
-            for (int64_t i = threadIdx.x; i < tcap; i += AFF_BTHREADS) {
-                t.key[i] = -1;
-                t.sc[i] = 0;
-                t.ov[i] = 0;
-            }
-            if (threadIdx.x == 0 && next) {
-                int32_t pos = atomicAdd((int*)next_slot, 1);
-                next[pos] = n;
-            }
-            __syncthreads();
-            continue;
-        }
-        int64_t bs = 0;
-        int32_t bm = -1;
-        uint32_t bo = 0;
-        scan_table<S>(L, n, t, threadIdx.x, nused, AFF_BTHREADS, omega, delta, phi, bs, bm, bo);
-        warp_argmax(bs, bm, bo);
-        if (lane == 0) {
-            rs[warp] = bs;
-            rm[warp] = bm;
-            ro[warp] = bo;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            for (int w = 1; w < nwarps; w++)
-                if (better(rs[w], rm[w], bs, bm)) {
-                    bs = rs[w];
-                    bm = rm[w];
-                    bo = ro[w];
-                }
-            cand[n] = bm;
-            cscore[n] = bm < 0 ? 0 : bs;
-            cov[n] = bm < 0 ? 0 : (int32_t)bo;
-        }
-        __syncthreads();
-    }
-}
-
-template <typename S>
-constexpr size_t aff_warp_smem()
-{
-    return (size_t)AFF_WARPS * table_bytes<S>(AFF_T);
-}
-
-template <typename S>
-constexpr size_t aff_block_smem()
-{
-    return table_bytes<S>(AFF_BT);
-}
+};
 
 // ---------------------------------------------------------------------------
 // matching
@@ -377,48 +252,52 @@ __global__ void k_match_finish(int32_t V, const int32_t* __restrict__ cand,
 
 // ---------------------------------------------------------------------------
 
+__global__ void k_level_min(Level L, int32_t* vmin)
+{
+    int32_t ms = 0x7fffffff, mi = 0x7fffffff;
+    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < L.V;
+         n += (int64_t)gridDim.x * blockDim.x) {
+        ms = min(ms, L.vsize[n]);
+        mi = min(mi, L.vinpins[n]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ms = min(ms, __shfl_xor_sync(FULL, ms, o));
+        mi = min(mi, __shfl_xor_sync(FULL, mi, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(&vmin[0], ms);
+        atomicMin(&vmin[1], mi);
+    }
+}
+
 template <typename S>
 static Status affinity(snnmap_hgraph* h, Level& L)
 {
-    cudaStream_t s = h->stream;
-    Arena& ar = h->scratch;
-    const snnmap_params& p = h->prm;
-    int32_t V = L.V;
-    int32_t *heavy, *heavy2;
-    SNN_TRY(ar.alloc(&heavy, V));
-    SNN_TRY(ar.alloc(&heavy2, V));
-    static bool attrs = false;
-    if (!attrs) {
-        SNN_CUDA(cudaFuncSetAttribute(k_aff_warp<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)aff_warp_smem<S>()));
-        SNN_CUDA(cudaFuncSetAttribute(k_aff_block<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)aff_block_smem<S>()));
-        attrs = true;
-    }
-    int grid = (int)std::min<int64_t>(ceil_div(V, AFF_WARPS), 152 * 3 * 8);
-    SNN_L k_aff_warp<S><<<grid, AFF_WARPS * 32, aff_warp_smem<S>(), s>>>(
-        L, p.omega, p.delta, p.phi, h->cand, h->cscore, h->cov, heavy, h->d_scal);
+    int32_t* vmin;
+    SNN_TRY(h->scratch.alloc(&vmin, 2));
+    SNN_TRY(fill_i32(vmin, 0x7fffffff, 2, h->stream));
+    SNN_L k_level_min<<<grid_for(L.V, 256), 256, 0, h->stream>>>(L, vmin);
     SNN_CUDA(cudaGetLastError());
-    SNN_L k_aff_block<S><<<152, AFF_BTHREADS, aff_block_smem<S>(), s>>>(
-        L, p.omega, p.delta, p.phi, h->cand, h->cscore, h->cov, heavy, h->d_scal + SC_E, heavy2,
-        h->d_scal + SC_F, nullptr, 0);
-    SNN_CUDA(cudaGetLastError());
-    SNN_TRY(read_scalars(h));
-    int64_t n2 = h->h_scal[SC_F];
-    if (n2 > 0) {
-        int64_t cap = 1024;
-        while (cap < 2 * (int64_t)V) cap <<= 1;
-        int64_t per = (int64_t)table_bytes<S>(cap);
-        int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(16, ((int64_t)1 << 30) / per));
-        if (blocks > n2) blocks = (int)n2;
-        unsigned char* gtab;
-        SNN_TRY(ar.alloc(&gtab, blocks * per));
-        SNN_TRY(init_global_tables<S>(gtab, blocks, cap, s));
-        SNN_L k_aff_block<S><<<blocks, AFF_BTHREADS, 0, s>>>(
-            L, p.omega, p.delta, p.phi, h->cand, h->cscore, h->cov, heavy2, h->d_scal + SC_F,
-            nullptr, nullptr, gtab, cap);
-        SNN_CUDA(cudaGetLastError());
-    }
+    AffPol<S> pol;
+    pol.vmin = vmin;
+    pol.L = L;
+    pol.V = L.V;
+    pol.keys = L.V;
+    pol.omega = h->prm.omega;
+    pol.delta = h->prm.delta;
+    pol.phi = h->prm.phi;
+    pol.cand = h->cand;
+    pol.cscore = h->cscore;
+    pol.cov = h->cov;
+    int64_t* cnt;
+    SNN_TRY(h->scratch.alloc(&cnt, HT_NTIER));
+    SNN_TRY(run_histogram(pol, h->scratch, h->stream, cnt, h->h_scal + 14, h->d_scal));
+    int64_t hc[HT_NTIER] = {0, 0, 0, 0};
+    SNN_CUDA(cudaMemcpyAsync(hc, cnt, HT_NTIER * sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream));
+    SNN_CUDA(cudaStreamSynchronize(h->stream));
+    h->extra.back().n_block = (int32_t)(hc[HT_TIER_BLOCK] + hc[HT_TIER_BIG]);
+    h->extra.back().n_global = (int32_t)hc[HT_TIER_SPLIT];
     return Status{};
 }
 

@@ -1,8 +1,43 @@
-// Open-addressing integer histograms keyed by a vertex or partition id, used
-// per vertex by the neighbour histogram (coarsening) and the partition
-// connection histogram (refinement gains).
+// Per-vertex integer histograms keyed by a vertex id (coarsening: score and
+// shared inbound count per neighbour) or a partition id (refinement:
+// connection weight and inbound overlap per adjacent partition), followed by
+// an argmax over the keys. Sums are integer atomics, so results do not
+// depend on the order of updates.
+//
+// Vertices are first binned by their work (total length of the segments
+// their incidences contribute), which bounds their number of distinct keys:
+//   warp tier   work <= 3/4 of a 512-slot table: one warp, shared memory;
+//               cannot overflow.
+//   block tier  work <= 2^16: one 256-thread block, 2048-slot shared table;
+//               a vertex with more than 1536 distinct keys is handed on.
+//   big tier    work <= 2^22 or hand-overs: one 512-thread block per SM with
+//               a 16384-slot shared table; overflow is handed on.
+//   split tier  the rest: the incidences are cut into items of about 16384
+//               elements processed by warps all over the GPU, all adding into
+//               one global-memory table per vertex sized to twice its bound
+//               of distinct keys (so it cannot overflow); one block per
+//               vertex then reduces the table.
+// Every tier visits a chunk of 32 incidences at a time with their segments
+// flattened into one range, so all 32 lanes load consecutive elements even
+// when segments are short.
+//
+// A Policy supplies:
+//   typedef S (score type), struct Acc (per-thread sums, with add(Acc) and
+//   __device__ Acc reduce over a warp)
+//   int32_t V (vertices), key space bound `keys`
+//   __device__ bool skip(n)                         n needs no histogram (result
+//                                                   written by write(n, 0, -1, 0, Acc()))
+//   __device__ int64_t seg_len(int64_t i)           segment length of incidence i
+//   __device__ int64_t vb(n), ve(n)                 incidence range of vertex n
+//   __device__ Seg<S> seg(int64_t i, Acc&)          segment of incidence i
+//   __device__ bool elem(n, const Seg<S>&, off, const Table<S>&, Acc&)
+//   __device__ void consider(n, key, int64 sc, uint32 ov, const Acc& total,
+//                            int64_t& best, int32_t& bkey, uint32_t& bov)
+//   __device__ void write(n, best, bkey, bov, const Acc& total)
 #pragma once
 #include "common.cuh"
+
+#include <algorithm>
 
 namespace snn {
 
@@ -14,32 +49,31 @@ __device__ __forceinline__ bool better(int64_t s1, int32_t m1, int64_t s2, int32
     return s1 > s2 || (s1 == s2 && m1 < m2);
 }
 
-// Table slots: key (-1 empty), summed weight, summed shared-inbound count;
-// `used` lists occupied slots in insertion order.
+// Open-addressing slots: key (-1 empty), summed weight, summed overlap.
 template <typename S>
 struct Table {
     int32_t* key;
     S* sc;
     uint32_t* ov;
-    int32_t* used;
-    int32_t* nfill;
-    uint32_t mask;   // capacity - 1
+    uint32_t mask;     // capacity - 1
+    uint32_t probes;   // probe limit of add()
 
-    // returns false if the table is full
+    // returns false if m finds no slot within the probe limit (tables that
+    // must never fail use the full capacity as the limit)
     __device__ __forceinline__ bool add(int32_t m, S w, uint32_t o) const
     {
+        return try_add(m, w, o, probes);
+    }
+
+    // returns false if m has no slot within the first max_probes probed
+    __device__ __forceinline__ bool try_add(int32_t m, S w, uint32_t o, uint32_t max_probes) const
+    {
         uint32_t slot = hash32((uint32_t)m) & mask;
-        for (uint32_t probe = 0; probe <= mask; probe++) {
+        for (uint32_t probe = 0; probe < max_probes; probe++) {
             int32_t k = *(volatile int32_t*)&key[slot];
             if (k == -1) {
                 int32_t prev = atomicCAS(&key[slot], -1, m);
-                if (prev == -1) {
-                    int32_t u = atomicAdd(nfill, 1);
-                    if ((uint32_t)u <= mask) used[u] = (int32_t)slot;
-                    k = m;
-                } else {
-                    k = prev;
-                }
+                k = prev == -1 ? m : prev;
             }
             if (k == m) {
                 atomicAdd(&sc[slot], w);
@@ -52,9 +86,27 @@ struct Table {
     }
 };
 
-// One incidence's segment: elements [b, b+len) of some per-hyperedge array,
+template <typename S>
+__host__ __device__ constexpr size_t slot_bytes()
+{
+    return 2 * sizeof(int32_t) + sizeof(S);
+}
+
+template <typename S>
+__device__ __forceinline__ Table<S> carve_table(unsigned char* base, int64_t cap)
+{
+    Table<S> t;
+    t.key = (int32_t*)base;
+    t.sc = (S*)(base + (size_t)cap * sizeof(int32_t));
+    t.ov = (uint32_t*)(base + (size_t)cap * (sizeof(int32_t) + sizeof(S)));
+    t.mask = (uint32_t)(cap - 1);
+    t.probes = (uint32_t)cap;
+    return t;
+}
+
+// One incidence's segment: elements [b, b+len) of a per-hyperedge array,
 // with the hyperedge's weight w, multiplicity k, whether the visiting vertex
-// is a destination (nd), and the hyperedge's selfdst flag (sd).
+// is one of its destinations (nd) and its selfdst flag (sd).
 template <typename S>
 struct Seg {
     int64_t b;
@@ -64,22 +116,18 @@ struct Seg {
     int nd, sd;
 };
 
-// Visits, with one warp, the elements of the segments of incidences
-// [i0, ve) of a vertex, 32 incidences at a time taken every `stride`. The
-// segments of a chunk are flattened into one range so that all 32 lanes
-// work on consecutive elements. V::seg(i) gives incidence i's segment;
-// V::elem(seg, off) handles element `off` of it and returns false if the
-// table is full. Returns false as soon as an element fails or the table
-// holds more than `limit` keys (checked once per chunk).
-template <typename S, class Vis>
-__device__ bool warp_flat_visit(Vis& vis, int64_t i0, int64_t ve, int64_t stride,
-                                const int32_t* nfill, int32_t limit)
+// One warp visits incidences [i0, ve) of vertex n, 32 at a time every
+// `stride`, flattening their segments. Returns false if an insert failed.
+template <typename S, class Pol, class Tb>
+__device__ bool warp_visit(const Pol& pol, int32_t n, int64_t i0, int64_t ve, int64_t stride,
+                           const Tb& t, typename Pol::Acc& acc)
 {
     int lane = threadIdx.x & 31;
+    bool ok = true;
     for (int64_t ib = i0; ib < ve; ib += stride) {
         int64_t i = ib + lane;
         Seg<S> sg{0, 0, 0, 0, 0, 0};
-        if (i < ve) sg = vis.seg(i);
+        if (i < ve) sg = pol.seg(i, acc);
         int32_t pre = sg.len;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -88,7 +136,6 @@ __device__ bool warp_flat_visit(Vis& vis, int64_t i0, int64_t ve, int64_t stride
         }
         int32_t total = __shfl_sync(FULL, pre, 31);
         pre -= sg.len;
-        bool ok = true;
         for (int32_t vbase = 0; vbase < total; vbase += 32) {
             int32_t v = vbase + lane;
             int32_t lo = 0;
@@ -98,22 +145,47 @@ __device__ bool warp_flat_visit(Vis& vis, int64_t i0, int64_t ve, int64_t stride
                 int32_t pc = __shfl_sync(FULL, pre, c & 31);
                 if (c < 32 && pc <= v) lo = c;
             }
-            Seg<S> t;
-            t.b = __shfl_sync(FULL, sg.b, lo);
-            t.len = __shfl_sync(FULL, sg.len, lo);
-            t.w = __shfl_sync(FULL, sg.w, lo);
-            t.k = __shfl_sync(FULL, sg.k, lo);
-            t.nd = __shfl_sync(FULL, sg.nd, lo);
-            t.sd = __shfl_sync(FULL, sg.sd, lo);
+            Seg<S> g;
+            g.b = __shfl_sync(FULL, sg.b, lo);
+            g.len = __shfl_sync(FULL, sg.len, lo);
+            g.w = __shfl_sync(FULL, sg.w, lo);
+            g.k = __shfl_sync(FULL, sg.k, lo);
+            g.nd = __shfl_sync(FULL, sg.nd, lo);
+            g.sd = __shfl_sync(FULL, sg.sd, lo);
             int32_t pt = __shfl_sync(FULL, pre, lo);
-            if (v < total) {
-                if (!vis.elem(t, v - pt)) ok = false;
-            }
+            if (v < total && !pol.elem(n, g, v - pt, t, acc)) ok = false;
         }
-        __syncwarp();
-        if (!__all_sync(FULL, ok) || *(volatile const int32_t*)nfill > limit) return false;
     }
-    return true;
+    return __all_sync(FULL, ok);
+}
+
+template <typename S>
+__device__ __forceinline__ void clear_slots(const Table<S>& t, int64_t from, int64_t to,
+                                            int64_t stride)
+{
+    for (int64_t i = from; i < to; i += stride) {
+        t.key[i] = -1;
+        t.sc[i] = 0;
+        t.ov[i] = 0;
+    }
+}
+
+// best over slots [from, to) by `stride`, resetting them
+template <typename S, class Pol>
+__device__ void scan_slots(const Pol& pol, int32_t n, const Table<S>& t, int64_t from, int64_t to,
+                           int64_t stride, const typename Pol::Acc& tot, int64_t& bs, int32_t& bk,
+                           uint32_t& bo)
+{
+    for (int64_t i = from; i < to; i += stride) {
+        int32_t k = t.key[i];
+        if (k < 0) continue;
+        int64_t s = (int64_t)t.sc[i];
+        uint32_t o = t.ov[i];
+        t.key[i] = -1;
+        t.sc[i] = 0;
+        t.ov[i] = 0;
+        pol.consider(n, k, s, o, tot, bs, bk, bo);
+    }
 }
 
 __device__ __forceinline__ void warp_argmax(int64_t& bs, int32_t& bm, uint32_t& bo)
@@ -131,48 +203,553 @@ __device__ __forceinline__ void warp_argmax(int64_t& bs, int32_t& bm, uint32_t& 
     }
 }
 
-// table carving: a warp slice or a block table from raw memory
+constexpr int HT_WARPS = 8;
+constexpr int HT_WCAP = 512;            // warp table slots
+constexpr int HT_WLOAD = HT_WCAP * 3 / 4;
+constexpr int64_t HT_WWORK = 8192;      // most elements one warp takes alone
+constexpr int HT_BTHREADS = 256;
+constexpr int HT_BCAP = 2048;           // block table slots
+constexpr int64_t HT_BWORK = 1 << 16;
+constexpr int HT_GTHREADS = 512;        // big-block tier
+constexpr int64_t HT_GWORK = 1 << 22;
+constexpr int64_t HT_CHUNK = 1024;      // incidences per split-tier work item
+enum : int { HT_TIER_WARP = 0, HT_TIER_BLOCK = 1, HT_TIER_BIG = 2, HT_TIER_SPLIT = 3, HT_NTIER = 4 };
+
 template <typename S>
-__device__ __forceinline__ Table<S> carve_table(unsigned char* base, int32_t cap, int32_t* nfill)
+__host__ __device__ constexpr int big_cap()
 {
-    Table<S> t;
-    t.key = (int32_t*)base;
-    t.sc = (S*)(base + (size_t)cap * sizeof(int32_t));
-    t.ov = (uint32_t*)(base + (size_t)cap * (sizeof(int32_t) + sizeof(S)));
-    t.used = (int32_t*)(base + (size_t)cap * (2 * sizeof(int32_t) + sizeof(S)));
-    t.nfill = nfill;
-    t.mask = (uint32_t)(cap - 1);
-    return t;
+    return sizeof(S) == 4 ? 16384 : 8192;
 }
 
-template <typename S>
-__host__ __device__ constexpr size_t table_bytes(int64_t cap)
+__host__ __device__ inline int64_t pow2_ceil(int64_t x)
 {
-    return (size_t)cap * (3 * sizeof(int32_t) + sizeof(S));
+    int64_t p = 1;
+    while (p < x) p <<= 1;
+    return p;
 }
 
-}  // namespace snn
-
-namespace snn {
-
-template <typename S>
-__global__ void k_init_tables(unsigned char* g, int blocks, int64_t cap)
+// work[n] = total segment length over n's incidences (one warp per vertex),
+// or -1 when the policy decides n without a histogram
+template <class Pol>
+__global__ void __launch_bounds__(256) k_ht_work(Pol pol, int64_t* work)
 {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < blocks * cap;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        int64_t b = i / cap, j = i - b * cap;
-        Table<S> t = carve_table<S>(g + (size_t)b * table_bytes<S>(cap), (int32_t)cap, nullptr);
-        t.key[j] = -1;
-        t.sc[j] = 0;
-        t.ov[j] = 0;
+    int lane = threadIdx.x & 31;
+    int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t n = gw; n < pol.V; n += nw) {
+        if (pol.skip((int32_t)n)) {
+            if (lane == 0) work[n] = -1;
+            continue;
+        }
+        int64_t w = 0;
+        for (int64_t i = pol.vb((int32_t)n) + lane; i < pol.ve((int32_t)n); i += 32) w += pol.seg_len(i);
+        w = warp_sum(w);
+        if (lane == 0) work[n] = w;
     }
 }
 
-// global-memory tables for the block tier: key -1, sums 0
-template <typename S>
-inline Status init_global_tables(unsigned char* g, int blocks, int64_t cap, cudaStream_t s)
+// lists: tier t's vertices at lists + t*V; cnt[t] their number; the split
+// tier also records each vertex's table capacity
+template <class Pol>
+__device__ __forceinline__ void ht_push(const Pol& pol, int tier, int32_t n, int64_t work,
+                                        int32_t* lists, int64_t* cnt, int64_t* scap)
 {
-    SNN_L k_init_tables<S><<<grid_for(blocks * cap, 256), 256, 0, s>>>(g, blocks, cap);
+    int64_t p = (int64_t)atomicAdd((unsigned long long*)&cnt[tier], 1ull);
+    lists[(int64_t)tier * pol.V + p] = n;
+    if (tier == HT_TIER_SPLIT) {
+        int64_t bound = work < pol.keys ? work : pol.keys;
+        scap[p] = pow2_ceil(2 * (bound > 16 ? bound : 16));
+    }
+}
+
+template <class Pol>
+__global__ void __launch_bounds__(256)
+    k_ht_classify(Pol pol, const int64_t* __restrict__ workv, int32_t* lists, int64_t* cnt,
+                  int64_t* scap)
+{
+    int lane = threadIdx.x & 31;
+    unsigned lt = lanemask_lt();
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < pol.V;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        int64_t n = base + threadIdx.x;
+        int tier = -1;
+        int64_t work = 0;
+        if (n < pol.V) {
+            work = workv[n];
+            if (work < 0) {
+                pol.write((int32_t)n, 0, -1, 0, typename Pol::Acc());
+            } else {
+                int64_t bound = work < pol.keys ? work : pol.keys;
+                if (bound <= HT_WLOAD) tier = work <= HT_WWORK ? HT_TIER_WARP : HT_TIER_SPLIT;
+                else if (work <= HT_BWORK) tier = HT_TIER_BLOCK;
+                else if (work <= HT_GWORK) tier = HT_TIER_BIG;
+                else tier = HT_TIER_SPLIT;
+            }
+        }
+        for (int t = 0; t < HT_NTIER; t++) {
+            unsigned m = __ballot_sync(FULL, tier == t);
+            if (!m) continue;
+            int leader = __ffs(m) - 1;
+            int64_t pos = 0;
+            if (lane == leader) pos = (int64_t)atomicAdd((unsigned long long*)&cnt[t], (unsigned long long)__popc(m));
+            pos = __shfl_sync(FULL, pos, leader);
+            if (tier == t) {
+                int64_t p = pos + __popc(m & lt);
+                lists[(int64_t)t * pol.V + p] = (int32_t)n;
+                if (t == HT_TIER_SPLIT) {
+                    int64_t bound = work < pol.keys ? work : pol.keys;
+                    scap[p] = pow2_ceil(2 * (bound > 16 ? bound : 16));
+                }
+            }
+        }
+    }
+}
+
+template <class Pol>
+__global__ void __launch_bounds__(HT_WARPS * 32)
+    k_ht_warp(Pol pol, const int32_t* __restrict__ lists, const int64_t* __restrict__ cnt,
+              const int64_t* __restrict__ workv)
+{
+    using S = typename Pol::S;
+    using Acc = typename Pol::Acc;
+    extern __shared__ __align__(16) unsigned char ht_dyn[];
+    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int32_t* list = lists + (int64_t)HT_TIER_WARP * pol.V;
+    int64_t nl = cnt[HT_TIER_WARP];
+    int64_t gw = blockIdx.x * (int64_t)HT_WARPS + warp, nw = (int64_t)gridDim.x * HT_WARPS;
+    Table<S> full = carve_table<S>(ht_dyn + (size_t)warp * HT_WCAP * slot_bytes<S>(), HT_WCAP);
+    clear_slots(full, lane, HT_WCAP, 32);
+    __syncwarp();
+    for (int64_t idx = gw; idx < nl; idx += nw) {
+        int32_t n = list[idx];
+        int64_t vb = pol.vb(n), ve = pol.ve(n);
+        Acc acc;
+        int64_t work = workv[n];
+        int64_t bound = work < pol.keys ? work : pol.keys;
+        int64_t cap = pow2_ceil(2 * (bound > 8 ? bound : 8));
+        if (cap > HT_WCAP) cap = HT_WCAP;
+        Table<S> t = full;
+        t.mask = (uint32_t)(cap - 1);
+        warp_visit<S>(pol, n, vb, ve, 32, t, acc);
+        __syncwarp();
+        Acc tot = Pol::warp_reduce(acc);
+        int64_t bs = 0;
+        int32_t bk = -1;
+        uint32_t bo = 0;
+        scan_slots<S>(pol, n, t, lane, cap, 32, tot, bs, bk, bo);
+        warp_argmax(bs, bk, bo);
+        if (lane == 0) pol.write(n, bs, bk, bo, tot);
+        __syncwarp();
+    }
+}
+
+// Block-wide visit of incidences [vb, ve): tiles of blockDim incidences, one
+// per thread, segment lengths scanned across the block, then every thread
+// takes elements v = tid, tid + blockDim, ... of the tile's flattened range
+// and finds its segment by binary search in shared memory.
+template <typename S, class Pol, int T>
+__device__ bool block_visit(const Pol& pol, int32_t n, int64_t vb, int64_t ve, const Table<S>& t,
+                            typename Pol::Acc& acc, Seg<S>* sseg, int32_t* spre, int32_t* swarp,
+                            int* sfail)
+{
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = T / 32;
+    bool ok = true;
+    for (int64_t tile = vb; tile < ve; tile += T) {
+        int64_t i = tile + threadIdx.x;
+        Seg<S> sg{0, 0, 0, 0, 0, 0};
+        if (i < ve) sg = pol.seg(i, acc);
+        int32_t inc = sg.len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int32_t t2 = __shfl_up_sync(FULL, inc, o);
+            if (lane >= o) inc += t2;
+        }
+        if (lane == 31) swarp[warp] = inc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int32_t run = 0;
+            for (int w = 0; w < nw; w++) {
+                int32_t c = swarp[w];
+                swarp[w] = run;
+                run += c;
+            }
+            swarp[nw] = run;
+        }
+        __syncthreads();
+        spre[threadIdx.x] = swarp[warp] + inc - sg.len;
+        sseg[threadIdx.x] = sg;
+        int32_t total = swarp[nw];
+        __syncthreads();
+        for (int32_t v = threadIdx.x; v < total; v += T) {
+            int32_t lo = 0, hi = T - 1;
+            while (lo < hi) {
+                int32_t mid = (lo + hi + 1) >> 1;
+                if (spre[mid] <= v) lo = mid;
+                else hi = mid - 1;
+            }
+            if (!pol.elem(n, sseg[lo], v - spre[lo], t, acc)) {
+                ok = false;
+                break;
+            }
+        }
+        if (!ok) *sfail = 1;
+        __syncthreads();
+        if (*sfail) break;
+    }
+    return *sfail == 0;
+}
+
+// Block (T threads) per vertex with a CAP-slot shared table; vertices whose
+// keys do not fit are pushed to tier `next`.
+template <class Pol, int T, int CAP, int TIER, int NEXT>
+__global__ void __launch_bounds__(T)
+    k_ht_block(Pol pol, int32_t* lists, int64_t* cnt, int64_t* scap, const int64_t* __restrict__ workv)
+{
+    using S = typename Pol::S;
+    using Acc = typename Pol::Acc;
+    extern __shared__ __align__(16) unsigned char ht_dyn[];
+    __shared__ __align__(16) unsigned char sseg_raw[sizeof(Seg<S>) * T];
+    __shared__ int32_t spre[T];
+    __shared__ int32_t swarp[T / 32 + 1];
+    __shared__ int sfail;
+    __shared__ __align__(16) unsigned char wacc_raw[sizeof(Acc) * (T / 32)];
+    __shared__ int64_t rs[T / 32];
+    __shared__ int32_t rk[T / 32];
+    __shared__ uint32_t ro[T / 32];
+    Seg<S>* sseg = (Seg<S>*)sseg_raw;
+    Acc* wacc = (Acc*)wacc_raw;
+    const int nwarps = T / 32;
+    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    Table<S> t = carve_table<S>(ht_dyn, CAP);
+    t.probes = 64;   // a vertex that clusters the table this much moves on
+    clear_slots(t, threadIdx.x, CAP, T);
+    const int32_t* list = lists + (int64_t)TIER * pol.V;
+    int64_t nl = cnt[TIER];
+    for (int64_t idx = blockIdx.x; idx < nl; idx += gridDim.x) {
+        int32_t n = list[idx];
+        if (threadIdx.x == 0) sfail = 0;
+        __syncthreads();
+        int64_t vb = pol.vb(n), ve = pol.ve(n);
+        Acc acc;
+        bool ok = block_visit<S, Pol, T>(pol, n, vb, ve, t, acc, sseg, spre, swarp, &sfail);
+        Acc wa = Pol::warp_reduce(acc);
+        if (lane == 0) wacc[warp] = wa;
+        __syncthreads();
+        if (!ok) {
+            clear_slots(t, threadIdx.x, CAP, T);
+            if (threadIdx.x == 0) ht_push(pol, NEXT, n, workv[n], lists, cnt, scap);
+            __syncthreads();
+            continue;
+        }
+        Acc tot = wacc[0];
+        for (int w = 1; w < nwarps; w++) tot.add(wacc[w]);
+        int64_t bs = 0;
+        int32_t bk = -1;
+        uint32_t bo = 0;
+        scan_slots<S>(pol, n, t, threadIdx.x, CAP, T, tot, bs, bk, bo);
+        warp_argmax(bs, bk, bo);
+        if (lane == 0) {
+            rs[warp] = bs;
+            rk[warp] = bk;
+            ro[warp] = bo;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int w = 1; w < nwarps; w++)
+                if (better(rs[w], rk[w], bs, bk)) {
+                    bs = rs[w];
+                    bk = rk[w];
+                    bo = ro[w];
+                }
+            pol.write(n, bs, bk, bo, tot);
+        }
+        __syncthreads();
+    }
+}
+
+// Split tier. The incidences of the split vertices are laid out flat
+// (vertex j owns flat positions [od[j], od[j+1])) and cut into work items of
+// about HT_ITEM elements: an item starts at a vertex's first incidence or
+// where the running element count crosses a multiple of HT_ITEM. Each item
+// is visited by one warp adding straight into the vertex's global table.
+constexpr int64_t HT_ITEM = 16384;
+
+__device__ __forceinline__ int64_t find_owner(const int64_t* od, int64_t ns, int64_t f)
+{
+    int64_t lo = 0, hi = ns - 1;
+    while (lo < hi) {
+        int64_t mid = (lo + hi + 1) >> 1;
+        if (od[mid] <= f) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <class Pol>
+__global__ void k_ht_split_deg(Pol pol, const int32_t* __restrict__ slist, int64_t ns, int64_t* deg)
+{
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < ns;
+         j += (int64_t)gridDim.x * blockDim.x)
+        deg[j] = pol.ve(slist[j]) - pol.vb(slist[j]);
+}
+
+template <class Pol>
+__global__ void k_ht_split_len(Pol pol, const int32_t* __restrict__ slist, int64_t ns,
+                               const int64_t* __restrict__ od, int64_t D, int64_t* len)
+{
+    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < D;
+         f += (int64_t)gridDim.x * blockDim.x) {
+        int64_t j = find_owner(od, ns, f);
+        len[f] = pol.seg_len(pol.vb(slist[j]) + (f - od[j]));
+    }
+}
+
+static __global__ void k_ht_split_starts(int64_t ns, const int64_t* __restrict__ od, int64_t D,
+                                  const int64_t* __restrict__ x, const int64_t* __restrict__ len,
+                                  int32_t* start)
+{
+    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < D;
+         f += (int64_t)gridDim.x * blockDim.x) {
+        int64_t j = find_owner(od, ns, f);
+        int64_t base = x[od[j]];
+        int s = 0;
+        if (f == od[j]) s = 1;
+        else {
+            int64_t b0 = (x[f - 1] - base) / HT_ITEM, b1 = (x[f] - base) / HT_ITEM;
+            s = b1 != b0;
+        }
+        start[f] = s;
+    }
+}
+
+static __global__ void k_ht_split_items(int64_t D, const int32_t* __restrict__ start,
+                                 const int32_t* __restrict__ pos, int64_t* item_f0)
+{
+    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < D;
+         f += (int64_t)gridDim.x * blockDim.x)
+        if (start[f]) item_f0[pos[f]] = f;
+}
+
+// adds the used slots of a warp-private table into the global table g and
+// clears them
+template <typename S>
+__device__ bool flush_private(const Table<S>& p, int64_t cap, const Table<S>& g)
+{
+    int lane = threadIdx.x & 31;
+    bool ok = true;
+    for (int64_t i = lane; i < cap; i += 32) {
+        int32_t k = p.key[i];
+        if (k < 0) continue;
+        if (!g.add(k, p.sc[i], p.ov[i])) ok = false;
+        p.key[i] = -1;
+        p.sc[i] = 0;
+        p.ov[i] = 0;
+    }
+    __syncwarp();
+    return __all_sync(FULL, ok);
+}
+
+// Items of vertices with few possible keys (table capacity <= HT_WCAP) are
+// counted in a warp-private shared table first and flushed once per item,
+// so many warps working for one vertex do not all hit the same few global
+// slots; other items add straight into the global table.
+template <class Pol>
+__global__ void __launch_bounds__(HT_WARPS * 32)
+    k_ht_split_visit(Pol pol, const int32_t* __restrict__ slist, int64_t ns,
+                     const int64_t* __restrict__ od, int64_t D,
+                     const int64_t* __restrict__ item_f0, int64_t nitems,
+                     const int64_t* __restrict__ toff, const int64_t* __restrict__ scap,
+                     unsigned char* pool, typename Pol::Acc* gacc, int64_t* status)
+{
+    using S = typename Pol::S;
+    using Acc = typename Pol::Acc;
+    extern __shared__ __align__(16) unsigned char ht_dyn[];
+    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    Table<S> priv = carve_table<S>(ht_dyn + (size_t)warp * HT_WCAP * slot_bytes<S>(), HT_WCAP);
+    clear_slots(priv, lane, HT_WCAP, 32);
+    __syncwarp();
+    int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t it = gw; it < nitems; it += nw) {
+        int64_t f0 = item_f0[it];
+        int64_t f1 = it + 1 < nitems ? item_f0[it + 1] : D;
+        int64_t j = find_owner(od, ns, f0);
+        if (f1 > od[j + 1]) f1 = od[j + 1];
+        int32_t n = slist[j];
+        int64_t vb = pol.vb(n) + (f0 - od[j]);
+        int64_t ve = pol.vb(n) + (f1 - od[j]);
+        Table<S> g = carve_table<S>(pool + toff[j] * slot_bytes<S>(), scap[j]);
+        Acc acc;
+        bool ok;
+        if (scap[j] <= HT_WCAP) {
+            Table<S> p = priv;
+            p.mask = (uint32_t)(scap[j] - 1);
+            p.probes = (uint32_t)scap[j];
+            ok = warp_visit<S>(pol, n, vb, ve, 32, p, acc);
+            ok = flush_private(p, scap[j], g) && ok;
+        } else {
+            ok = warp_visit<S>(pol, n, vb, ve, 32, g, acc);
+        }
+        if (!ok && lane == 0) atomicOr((int*)status, ST_CAPACITY);
+        Acc wa = Pol::warp_reduce(acc);
+        if (lane == 0) wa.atomic_into(&gacc[j]);
+    }
+}
+
+template <class Pol>
+__global__ void __launch_bounds__(1024)
+    k_ht_split_scan(Pol pol, const int32_t* __restrict__ slist, int64_t ns,
+                    const int64_t* __restrict__ toff, const int64_t* __restrict__ scap,
+                    unsigned char* pool, const typename Pol::Acc* gacc)
+{
+    using S = typename Pol::S;
+    __shared__ int64_t rs[32];
+    __shared__ int32_t rk[32];
+    __shared__ uint32_t ro[32];
+    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int nwarps = blockDim.x >> 5;
+    for (int64_t j = blockIdx.x; j < ns; j += gridDim.x) {
+        int32_t n = slist[j];
+        Table<S> t = carve_table<S>(pool + toff[j] * slot_bytes<S>(), scap[j]);
+        typename Pol::Acc tot = gacc[j];
+        int64_t bs = 0;
+        int32_t bk = -1;
+        uint32_t bo = 0;
+        scan_slots<S>(pol, n, t, threadIdx.x, scap[j], blockDim.x, tot, bs, bk, bo);
+        warp_argmax(bs, bk, bo);
+        if (lane == 0) {
+            rs[warp] = bs;
+            rk[warp] = bk;
+            ro[warp] = bo;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int w = 1; w < nwarps; w++)
+                if (better(rs[w], rk[w], bs, bk)) {
+                    bs = rs[w];
+                    bk = rk[w];
+                    bo = ro[w];
+                }
+            pol.write(n, bs, bk, bo, tot);
+        }
+        __syncthreads();
+    }
+}
+
+template <typename S>
+__global__ void k_ht_pool_clear(unsigned char* pool, const int64_t* __restrict__ toff,
+                                const int64_t* __restrict__ scap, int64_t ns)
+{
+    for (int64_t j = blockIdx.x; j < ns; j += gridDim.x) {
+        Table<S> t = carve_table<S>(pool + toff[j] * slot_bytes<S>(), scap[j]);
+        clear_slots(t, threadIdx.x, scap[j], blockDim.x);
+    }
+}
+
+template <typename K>
+inline Status set_smem(K kernel, size_t bytes)
+{
+    if (bytes > 48 * 1024)
+        SNN_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    return Status{};
+}
+
+// Host driver: work, classification and the warp, block and big-block tiers
+// run without host synchronization; the split tier follows reads of its
+// sizes. d_cnt: >= HT_NTIER device int64; h_cnt: a pinned host int64[>=2];
+// status: device word.
+template <class Pol>
+Status run_histogram(const Pol& pol, Arena& ar, cudaStream_t s, int64_t* d_cnt, int64_t* h_cnt,
+                     int64_t* status)
+{
+    using S = typename Pol::S;
+    int32_t V = pol.V;
+    if (V <= 0) return Status{};
+    int32_t* lists;
+    int64_t *scap, *workv;
+    SNN_TRY(ar.alloc(&lists, (int64_t)HT_NTIER * V));
+    SNN_TRY(ar.alloc(&scap, V));
+    SNN_TRY(ar.alloc(&workv, V));
+    SNN_CUDA(cudaMemsetAsync(d_cnt, 0, HT_NTIER * sizeof(int64_t), s));
+    SNN_L k_ht_work<Pol><<<grid_for((int64_t)V * 32, 256), 256, 0, s>>>(pol, workv);
+    SNN_CUDA(cudaGetLastError());
+    SNN_L k_ht_classify<Pol><<<grid_for(V, 256), 256, 0, s>>>(pol, workv, lists, d_cnt, scap);
+    SNN_CUDA(cudaGetLastError());
+    static bool attrs = false;
+    size_t wsm = (size_t)HT_WARPS * HT_WCAP * slot_bytes<S>();
+    size_t bsm = (size_t)HT_BCAP * slot_bytes<S>();
+    size_t gsm = (size_t)big_cap<S>() * slot_bytes<S>();
+    auto kb = k_ht_block<Pol, HT_BTHREADS, HT_BCAP, HT_TIER_BLOCK, HT_TIER_BIG>;
+    auto kg = k_ht_block<Pol, HT_GTHREADS, big_cap<S>(), HT_TIER_BIG, HT_TIER_SPLIT>;
+    if (!attrs) {
+        SNN_TRY(set_smem(k_ht_warp<Pol>, wsm));
+        SNN_TRY(set_smem(kb, bsm));
+        SNN_TRY(set_smem(kg, gsm));
+        attrs = true;
+    }
+    SNN_L k_ht_warp<Pol><<<(int)std::min<int64_t>(ceil_div(V, HT_WARPS), 152 * 8), HT_WARPS * 32, wsm,
+                           s>>>(pol, lists, d_cnt, workv);
+    SNN_CUDA(cudaGetLastError());
+    SNN_L kb<<<(int)std::min<int64_t>(V, 152 * 8), HT_BTHREADS, bsm, s>>>(pol, lists, d_cnt, scap, workv);
+    SNN_CUDA(cudaGetLastError());
+    SNN_L kg<<<152, HT_GTHREADS, gsm, s>>>(pol, lists, d_cnt, scap, workv);
+    SNN_CUDA(cudaGetLastError());
+    SNN_CUDA(cudaMemcpyAsync(h_cnt, d_cnt + HT_TIER_SPLIT, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    SNN_CUDA(cudaStreamSynchronize(s));
+    int64_t ns = h_cnt[0];
+    if (ns == 0) return Status{};
+    const int32_t* sl = lists + (int64_t)HT_TIER_SPLIT * V;
+    int64_t *toff, *deg, *od, *tot;
+    SNN_TRY(ar.alloc(&toff, ns + 1));
+    SNN_TRY(ar.alloc(&deg, ns));
+    SNN_TRY(ar.alloc(&od, ns + 1));
+    SNN_TRY(ar.alloc(&tot, 4));
+    SNN_CUDA(cudaMemsetAsync(tot, 0, 4 * sizeof(int64_t), s));
+    SNN_TRY(scan_exclusive_i64(scap, toff, ns, tot, ar, s));
+    SNN_L k_ht_split_deg<Pol><<<grid_for(ns, 256), 256, 0, s>>>(pol, sl, ns, deg);
+    SNN_CUDA(cudaGetLastError());
+    SNN_TRY(scan_exclusive_i64(deg, od, ns, od + ns, ar, s));
+    SNN_CUDA(cudaMemcpyAsync(h_cnt, tot, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    SNN_CUDA(cudaMemcpyAsync(h_cnt + 1, od + ns, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    SNN_CUDA(cudaStreamSynchronize(s));
+    int64_t slots = h_cnt[0], D = h_cnt[1];
+    int64_t *len, *x, *item_f0;
+    int32_t *start, *pos;
+    SNN_TRY(ar.alloc(&len, D));
+    SNN_TRY(ar.alloc(&x, D));
+    SNN_TRY(ar.alloc(&start, D));
+    SNN_TRY(ar.alloc(&pos, D));
+    SNN_TRY(ar.alloc(&item_f0, D));
+    SNN_L k_ht_split_len<Pol><<<grid_for(D, 256), 256, 0, s>>>(pol, sl, ns, od, D, len);
+    SNN_CUDA(cudaGetLastError());
+    SNN_TRY(scan_exclusive_i64(len, x, D, nullptr, ar, s));
+    SNN_L k_ht_split_starts<<<grid_for(D, 256), 256, 0, s>>>(ns, od, D, x, len, start);
+    SNN_CUDA(cudaGetLastError());
+    SNN_TRY(scan_exclusive_i32(start, pos, D, (int32_t*)(tot + 1), ar, s));
+    SNN_L k_ht_split_items<<<grid_for(D, 256), 256, 0, s>>>(D, start, pos, item_f0);
+    SNN_CUDA(cudaGetLastError());
+    SNN_CUDA(cudaMemcpyAsync(h_cnt, tot + 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    SNN_CUDA(cudaStreamSynchronize(s));
+    int64_t items = h_cnt[0];
+    unsigned char* pool;
+    typename Pol::Acc* gacc;
+    SNN_TRY(ar.alloc(&pool, slots * (int64_t)slot_bytes<S>()));
+    SNN_TRY(ar.alloc(&gacc, ns));
+    SNN_CUDA(cudaMemsetAsync(gacc, 0, (size_t)ns * sizeof(typename Pol::Acc), s));
+    SNN_L k_ht_pool_clear<S><<<(int)std::min<int64_t>(ns, 152 * 8), 256, 0, s>>>(pool, toff, scap, ns);
+    SNN_CUDA(cudaGetLastError());
+    static bool vattr = false;
+    if (!vattr) {
+        SNN_TRY(set_smem(k_ht_split_visit<Pol>, wsm));
+        vattr = true;
+    }
+    SNN_L k_ht_split_visit<Pol><<<(int)std::min<int64_t>(ceil_div(items, HT_WARPS), 152 * 8),
+                                  HT_WARPS * 32, wsm, s>>>(pol, sl, ns, od, D, item_f0, items, toff,
+                                                           scap, pool, gacc, status);
+    SNN_CUDA(cudaGetLastError());
+    SNN_L k_ht_split_scan<Pol><<<(int)std::min<int64_t>(ns, 152 * 4), 1024, 0, s>>>(pol, sl, ns, toff,
+                                                                                    scap, pool, gacc);
     SNN_CUDA(cudaGetLastError());
     return Status{};
 }

@@ -19,6 +19,8 @@ enum Scalar : int {
 struct LevelExtra {
     SegBuckets seg;          // hyperedge size buckets
     int64_t pair_terms = 0;  // sum of |e|(|e|-1)
+    int32_t n_block = 0;     // last histogram: vertices on the block tier
+    int32_t n_global = 0;    //                 and on the global-memory tier
 };
 
 // pipeline stages timed by the profiler

@@ -48,12 +48,6 @@ enum : int {
     RS_DEG = 8,        // incidences of proposing vertices
 };
 
-constexpr int GAIN_WARPS = 8;
-constexpr int GAIN_T = 512;
-constexpr int GAIN_LOAD = GAIN_T * 3 / 4;
-constexpr int GAIN_BT = 8192;
-constexpr int GAIN_BLOAD = GAIN_BT * 3 / 4;
-constexpr int GAIN_BTHREADS = 256;
 constexpr int REPLAY_WARP_MAX = 32;
 
 struct PinCounts {
@@ -189,16 +183,51 @@ __global__ void k_check_pstate(int32_t K, PState ps, int32_t omega, int32_t delt
 }
 
 // ---------------------------------------------------------------------------
-// S7
+// S7: partition connection histogram per vertex
 
-template <typename S>
-struct GainVis {
-    const Level& L;
-    const PinCounts& pc;
-    int32_t home;
-    const Table<S>& t;
-    int64_t W = 0, save = 0;
-    __device__ Seg<S> seg(int64_t i)
+template <typename S_>
+struct GainPol {
+    using S = S_;
+    struct Acc {
+        int64_t W, save;   // summed omega of incident hyperedges; of those n is the last pin of
+        __device__ Acc() : W(0), save(0) {}
+        __device__ void add(const Acc& o)
+        {
+            W += o.W;
+            save += o.save;
+        }
+        __device__ void atomic_into(Acc* g) const
+        {
+            if (W) atomicAdd((unsigned long long*)&g->W, (unsigned long long)W);
+            if (save) atomicAdd((unsigned long long*)&g->save, (unsigned long long)save);
+        }
+    };
+    static __device__ Acc warp_reduce(const Acc& a)
+    {
+        Acc r;
+        r.W = warp_sum(a.W);
+        r.save = warp_sum(a.save);
+        return r;
+    }
+
+    Level L;
+    PinCounts pc;
+    PState ps;
+    const int32_t* rho;
+    int32_t V;
+    int64_t keys;
+    int32_t omega, delta, phi;
+    int32_t* pto;
+    int64_t* pgain;
+
+    __device__ bool skip(int32_t) const { return false; }
+    __device__ int64_t vb(int32_t n) const { return L.voff[n]; }
+    __device__ int64_t ve(int32_t n) const { return L.voff[n + 1]; }
+    __device__ int64_t seg_len(int64_t i) const
+    {
+        return pc.lam[(int32_t)((uint32_t)L.vinc[i] & ~SRC_BIT)];
+    }
+    __device__ Seg<S> seg(int64_t i, Acc& acc) const
     {
         uint32_t inc = (uint32_t)L.vinc[i];
         int32_t a = (int32_t)(inc & ~SRC_BIT);
@@ -209,182 +238,45 @@ struct GainVis {
         g.len = pc.lam[a];
         g.w = (S)L.hw[a];
         g.k = (uint32_t)L.hk[a];
-        W += L.hw[a];
+        acc.W += L.hw[a];
         return g;
     }
-    __device__ bool elem(const Seg<S>& g, int32_t off)
+    template <class Tb>
+    __device__ bool elem(int32_t n, const Seg<S>& g, int32_t off, const Tb& t, Acc& acc) const
     {
         int64_t e = g.b + off;
         int32_t p = pc.p[e];
-        if (p == home) {
-            if (pc.cnt[e] == 1) save += (int64_t)g.w;
+        if (p == rho[n]) {
+            if (pc.cnt[e] == 1) acc.save += (int64_t)g.w;
             return true;
         }
+        // a partition that cannot take n by size or inbound pins is never
+        // the chosen move: leave it out of the table
+        if (ps.size[p] + L.vsize[n] > omega || ps.inpins[p] + L.vinpins[n] > phi) return true;
         return t.add(p, g.w, (g.nd && pc.dcnt[e] > 0) ? g.k : 0u);
     }
-};
-
-template <typename S>
-__device__ void scan_gain(const Table<S>& t, int32_t u0, int32_t nused, int32_t stride,
-                          int64_t base, int64_t sz, int64_t ip, int64_t ic, const PState& ps,
-                          int32_t omega, int32_t delta, int32_t phi, int64_t& bs, int32_t& bm)
-{
-    for (int32_t u = u0; u < nused; u += stride) {
-        int32_t slot = t.used[u];
-        int32_t p = t.key[slot];
-        int64_t conn = (int64_t)t.sc[slot];
-        uint32_t o = t.ov[slot];
-        t.key[slot] = -1;
-        t.sc[slot] = 0;
-        t.ov[slot] = 0;
-        int64_t gain = base + conn;
-        bool feas = ps.size[p] + sz <= omega && ps.inpins[p] + ip <= phi &&
-                    ps.pincnt[p] + ic - (int64_t)o <= delta;
-        if (feas && better(gain, p, bs, bm)) {
+    // gain = save - loss with loss = W - conn(p); feasible if p stays within
+    // Omega, Phi, and Delta on its inbound set grown by n's axons not yet
+    // inbound to p
+    __device__ void consider(int32_t n, int32_t p, int64_t conn, uint32_t o, const Acc& tot,
+                             int64_t& bs, int32_t& bk, uint32_t& bo) const
+    {
+        int64_t gain = tot.save - tot.W + conn;
+        bool feas = ps.size[p] + L.vsize[n] <= omega && ps.inpins[p] + L.vinpins[n] <= phi &&
+                    ps.pincnt[p] + L.vincnt[n] - (int64_t)o <= delta;
+        if (feas && better(gain, p, bs, bk)) {
             bs = gain;
-            bm = p;
+            bk = p;
+            bo = o;
         }
     }
-}
-
-template <typename S>
-__global__ void __launch_bounds__(GAIN_WARPS * 32)
-    k_gain_warp(Level L, PinCounts pc, const int32_t* __restrict__ rho, PState ps, int32_t omega,
-                int32_t delta, int32_t phi, int32_t* pto, int64_t* pgain, int32_t* heavy,
-                int64_t* heavy_slot)
-{
-    extern __shared__ unsigned char smem_raw[];
-    __shared__ int32_t nfill[GAIN_WARPS];
-    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    Table<S> t = carve_table<S>(smem_raw + (size_t)warp * table_bytes<S>(GAIN_T), GAIN_T, &nfill[warp]);
-    for (int i = lane; i < GAIN_T; i += 32) {
-        t.key[i] = -1;
-        t.sc[i] = 0;
-        t.ov[i] = 0;
+    __device__ void write(int32_t n, int64_t bs, int32_t bk, uint32_t, const Acc&) const
+    {
+        bool prop = bk >= 0 && bs > 0;
+        pto[n] = prop ? bk : -1;
+        pgain[n] = prop ? bs : 0;
     }
-    int64_t gw = blockIdx.x * (int64_t)GAIN_WARPS + warp;
-    int64_t nw = (int64_t)gridDim.x * GAIN_WARPS;
-    for (int64_t n = gw; n < L.V; n += nw) {
-        if (lane == 0) nfill[warp] = 0;
-        __syncwarp();
-        GainVis<S> vis{L, pc, rho[n], t};
-        bool ok = warp_flat_visit<S>(vis, L.voff[n], L.voff[n + 1], 32, &nfill[warp], GAIN_LOAD);
-        __syncwarp();
-        int32_t nused = nfill[warp];
-        if (!ok || nused > GAIN_T) {
-            for (int i = lane; i < GAIN_T; i += 32) {
-                t.key[i] = -1;
-                t.sc[i] = 0;
-                t.ov[i] = 0;
-            }
-            if (lane == 0) {
-                int32_t pos = atomicAdd((int*)heavy_slot, 1);
-                heavy[pos] = (int32_t)n;
-            }
-            __syncwarp();
-            continue;
-        }
-        int64_t W = warp_sum(vis.W), save = warp_sum(vis.save);
-        int64_t bs = 0;
-        int32_t bm = -1;
-        scan_gain<S>(t, lane, nused, 32, save - W, L.vsize[n], L.vinpins[n], L.vincnt[n], ps, omega,
-                     delta, phi, bs, bm);
-        uint32_t dummy = 0;
-        warp_argmax(bs, bm, dummy);
-        if (lane == 0) {
-            bool prop = bm >= 0 && bs > 0;
-            pto[n] = prop ? bm : -1;
-            pgain[n] = prop ? bs : 0;
-        }
-        __syncwarp();
-    }
-}
-
-template <typename S>
-__global__ void __launch_bounds__(GAIN_BTHREADS)
-    k_gain_block(Level L, PinCounts pc, const int32_t* __restrict__ rho, PState ps, int32_t omega,
-                 int32_t delta, int32_t phi, int32_t* pto, int64_t* pgain, const int32_t* list,
-                 const int64_t* count_slot, int32_t* next, int64_t* next_slot, unsigned char* gtab,
-                 int64_t cap)
-{
-    extern __shared__ unsigned char smem_raw[];
-    __shared__ int32_t nfill;
-    __shared__ int sh_fail;
-    __shared__ unsigned long long sW, sSave;
-    __shared__ int64_t rs[GAIN_BTHREADS / 32];
-    __shared__ int32_t rm[GAIN_BTHREADS / 32];
-    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nwarps = GAIN_BTHREADS / 32;
-    int64_t tcap = gtab ? cap : GAIN_BT;
-    int32_t limit = gtab ? (int32_t)(cap - 1) : GAIN_BLOAD;
-    Table<S> t = carve_table<S>(gtab ? gtab + (size_t)blockIdx.x * table_bytes<S>(cap) : smem_raw,
-                                (int32_t)tcap, &nfill);
-    if (!gtab) {
-        for (int i = threadIdx.x; i < GAIN_BT; i += GAIN_BTHREADS) {
-            t.key[i] = -1;
-            t.sc[i] = 0;
-            t.ov[i] = 0;
-        }
-    }
-    int32_t cnt = (int32_t)*count_slot;
-    for (int32_t idx = blockIdx.x; idx < cnt; idx += gridDim.x) {
-        int32_t n = list[idx];
-        if (threadIdx.x == 0) {
-            nfill = 0;
-            sh_fail = 0;
-            sW = 0;
-            sSave = 0;
-        }
-        __syncthreads();
-        GainVis<S> vis{L, pc, rho[n], t};
-        bool ok = warp_flat_visit<S>(vis, L.voff[n] + 32 * warp, L.voff[n + 1], 32 * nwarps,
-                                     &nfill, limit);
-        if (!ok) atomicOr(&sh_fail, 1);
-        int64_t w = warp_sum(vis.W), sv = warp_sum(vis.save);
-        if (lane == 0) {
-            atomicAdd(&sW, (unsigned long long)w);
-            atomicAdd(&sSave, (unsigned long long)sv);
-        }
-        __syncthreads();
-        int32_t nused = nfill;
-        if (sh_fail || nused > limit) {
-            for (int64_t i = threadIdx.x; i < tcap; i += GAIN_BTHREADS) {
-                t.key[i] = -1;
-                t.sc[i] = 0;
-                t.ov[i] = 0;
-            }
-            if (threadIdx.x == 0 && next) {
-                int32_t pos = atomicAdd((int*)next_slot, 1);
-                next[pos] = n;
-            }
-            __syncthreads();
-            continue;
-        }
-        int64_t base = (int64_t)sSave - (int64_t)sW;
-        int64_t bs = 0;
-        int32_t bm = -1;
-        scan_gain<S>(t, threadIdx.x, nused, GAIN_BTHREADS, base, L.vsize[n], L.vinpins[n],
-                     L.vincnt[n], ps, omega, delta, phi, bs, bm);
-        uint32_t dummy = 0;
-        warp_argmax(bs, bm, dummy);
-        if (lane == 0) {
-            rs[warp] = bs;
-            rm[warp] = bm;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            for (int w2 = 1; w2 < nwarps; w2++)
-                if (better(rs[w2], rm[w2], bs, bm)) {
-                    bs = rs[w2];
-                    bm = rm[w2];
-                }
-            bool prop = bm >= 0 && bs > 0;
-            pto[n] = prop ? bm : -1;
-            pgain[n] = prop ? bs : 0;
-        }
-        __syncthreads();
-    }
-}
+};
 
 // ---------------------------------------------------------------------------
 // S8
@@ -742,52 +634,23 @@ __global__ void k_round_init(int64_t* scal) { scal[RS_ISTAR] = INT64_MAX; }
 
 template <typename S>
 static Status gains(snnmap_hgraph* h, Level& L, const PinCounts& pc, const int32_t* rho,
-                    const PState& ps, int32_t* pto, int64_t* pgain)
+                    const PState& ps, int32_t K, int32_t* pto, int64_t* pgain)
 {
-    cudaStream_t s = h->stream;
-    Arena& ar = h->scratch;
-    const snnmap_params& p = h->prm;
-    int32_t V = L.V;
-    int32_t *heavy, *heavy2;
-    int64_t* slots;
-    SNN_TRY(ar.alloc(&heavy, V));
-    SNN_TRY(ar.alloc(&heavy2, V));
-    SNN_TRY(ar.alloc(&slots, 2));
-    SNN_CUDA(cudaMemsetAsync(slots, 0, 2 * sizeof(int64_t), s));
-    static bool attrs = false;
-    size_t wsm = (size_t)GAIN_WARPS * table_bytes<S>(GAIN_T), bsm = table_bytes<S>(GAIN_BT);
-    if (!attrs) {
-        SNN_CUDA(cudaFuncSetAttribute(k_gain_warp<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsm));
-        SNN_CUDA(cudaFuncSetAttribute(k_gain_block<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm));
-        attrs = true;
-    }
-    int grid = (int)std::min<int64_t>(ceil_div(V, GAIN_WARPS), 152 * 3 * 8);
-    SNN_L k_gain_warp<S><<<grid, GAIN_WARPS * 32, wsm, s>>>(L, pc, rho, ps, p.omega, p.delta, p.phi, pto,
-                                                       pgain, heavy, slots);
-    SNN_CUDA(cudaGetLastError());
-    SNN_L k_gain_block<S><<<152, GAIN_BTHREADS, bsm, s>>>(L, pc, rho, ps, p.omega, p.delta, p.phi, pto,
-                                                     pgain, heavy, slots, heavy2, slots + 1,
-                                                     nullptr, 0);
-    SNN_CUDA(cudaGetLastError());
-    int64_t n2 = 0;
-    SNN_CUDA(cudaMemcpyAsync(&n2, slots + 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    SNN_CUDA(cudaStreamSynchronize(s));
-    if (n2 > 0) {
-        int64_t K = h->levels.back().V;
-        int64_t cap = 1024;
-        while (cap < 2 * K) cap <<= 1;
-        int64_t per = (int64_t)table_bytes<S>(cap);
-        int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(16, ((int64_t)1 << 30) / per));
-        if (blocks > n2) blocks = (int)n2;
-        unsigned char* gtab;
-        SNN_TRY(ar.alloc(&gtab, blocks * per));
-        SNN_TRY(init_global_tables<S>(gtab, blocks, cap, s));
-        SNN_L k_gain_block<S><<<blocks, GAIN_BTHREADS, 0, s>>>(L, pc, rho, ps, p.omega, p.delta, p.phi,
-                                                          pto, pgain, heavy2, slots + 1, nullptr,
-                                                          nullptr, gtab, cap);
-        SNN_CUDA(cudaGetLastError());
-    }
-    return Status{};
+    GainPol<S> pol;
+    pol.L = L;
+    pol.pc = pc;
+    pol.ps = ps;
+    pol.rho = rho;
+    pol.V = L.V;
+    pol.keys = K;
+    pol.omega = h->prm.omega;
+    pol.delta = h->prm.delta;
+    pol.phi = h->prm.phi;
+    pol.pto = pto;
+    pol.pgain = pgain;
+    int64_t* cnt;
+    SNN_TRY(h->scratch.alloc(&cnt, HT_NTIER));
+    return run_histogram(pol, h->scratch, h->stream, cnt, h->h_scal + 14, h->d_scal);
 }
 
 // pin counts + partition state + Conn for rho
@@ -865,9 +728,9 @@ static Status refine_round(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* 
     SNN_TRY(ar.alloc(&flag, V));
     SNN_TRY(ar.alloc(&pos, V));
     if (h->wide) {
-        SNN_TRY(gains<unsigned long long>(h, L, pc, rho, ps, pto, pgain));
+        SNN_TRY(gains<unsigned long long>(h, L, pc, rho, ps, K, pto, pgain));
     } else {
-        SNN_TRY(gains<uint32_t>(h, L, pc, rho, ps, pto, pgain));
+        SNN_TRY(gains<uint32_t>(h, L, pc, rho, ps, K, pto, pgain));
     }
     int gv = grid_for(V, 256);
     SNN_L k_prop_stats<<<gv, 256, 0, s>>>(L, pto, pgain, flag, h->d_scal);
