@@ -48,6 +48,9 @@ CONFIGS = {
              "receptive window + 4 random pins", snngen.cfg2),
     "cfg3": ("Recurrent power-law SNN, 2^23 neurons, Pareto(2.1) fan-out on [8,16384]",
              snngen.cfg3),
+    # quarter-width conv workload (profiling captures: inputs still larger than L2)
+    "cfg2q": ("Conv-like layered SNN, 8 layers of 64x64x8 (262,144 neurons)",
+              lambda: snngen.by_name("cfg2q")),
 }
 
 
@@ -60,6 +63,8 @@ def parse():
     ap.add_argument("--config", default="cfg2", choices=sorted(CONFIGS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-clocks", action="store_true",
+                    help="do not sample nvidia-smi (for runs under a profiler)")
     return ap.parse_args()
 
 
@@ -245,7 +250,7 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    sampler = ClockSampler(gpu_uuid(torch, local))
+    sampler = None if args.no_clocks else ClockSampler(gpu_uuid(torch, local))
     time.sleep(0.3)
     barrier()
     l0 = P.snnmap_launch_count()
@@ -261,7 +266,8 @@ def run_ours(args):
     e1.record(stream)
     barrier()
     launches = P.snnmap_launch_count() - l0
-    clocks = sampler.stop()
+    clocks = sampler.stop() if sampler else {"sm_mhz": None, "sm_max_mhz": None,
+                                             "reasons": ["not sampled"]}
     ms = e0.elapsed_time(e1) / args.steps
     if world > 1:
         t = torch.tensor([ms], device=dev)
@@ -304,22 +310,24 @@ def run_ours(args):
     pair_terms = sum(g["pair_terms"] for g in levels)
 
     # end to end through the host-buffer entry point (pinned host memory)
-    h_off = torch.from_numpy(hg.off).pin_memory()
-    h_pins = torch.from_numpy(hg.pins).pin_memory()
-    h_w = torch.from_numpy(hg.w).pin_memory()
-    h_rho = torch.empty(hg.V, dtype=torch.int32).pin_memory()
-    P.snnmap_partition_host(params, hg.V, hg.E, h_off, h_pins, h_w, h_rho, stream)
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
-        c2, _ = P.snnmap_partition_host(params, hg.V, hg.E, h_off, h_pins, h_w, h_rho, stream)
-    barrier()
-    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
-    assert c2 == cost, (c2, cost)
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = None
+    if args.e2e_steps > 0:
+        h_off = torch.from_numpy(hg.off).pin_memory()
+        h_pins = torch.from_numpy(hg.pins).pin_memory()
+        h_w = torch.from_numpy(hg.w).pin_memory()
+        h_rho = torch.empty(hg.V, dtype=torch.int32).pin_memory()
+        P.snnmap_partition_host(params, hg.V, hg.E, h_off, h_pins, h_w, h_rho, stream)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            c2, _ = P.snnmap_partition_host(params, hg.V, hg.E, h_off, h_pins, h_w, h_rho, stream)
+        barrier()
+        e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+        assert c2 == cost, (c2, cost)
+        if world > 1:
+            t = torch.tensor([e2e_s], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
 
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -342,9 +350,10 @@ def run_ours(args):
             "stage_ms_per_step": {k: round(v["ms"], 3) for k, v in per_step.items()},
             "roofline": roof,
             "cpu_baseline": cb,
-            "e2e": {"value": world * hg.P / e2e_s, "unit": UNIT,
-                    "h2d_bytes_per_step": 8 * (hg.E + 1) + 4 * hg.P + 4 * hg.E,
-                    "d2h_bytes_per_step": 4 * hg.V, "s_per_step": e2e_s},
+            "e2e": None if e2e_s is None else {
+                "value": world * hg.P / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": 8 * (hg.E + 1) + 4 * hg.P + 4 * hg.E,
+                "d2h_bytes_per_step": 4 * hg.V, "s_per_step": e2e_s},
             "gpu_launches": launches,
             "clocks": clocks,
         }

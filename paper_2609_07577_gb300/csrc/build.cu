@@ -102,7 +102,7 @@ Status level_alloc(snnmap_hgraph* h, Level& L, LevelExtra& X, int32_t V, int32_t
     c.add(&L.vinint, V);
     c.add(&L.cid, V);
     c.add(&X.seg.list, E);
-    c.add(&X.seg.meta, 8);
+    c.add(&X.seg.meta, 2 * SEG_NB);
     void* p = nullptr;
     SNN_CUDA(cudaMallocAsync(&p, c.total, h->stream));
     c.assign(p);
@@ -122,50 +122,54 @@ void level_free(snnmap_hgraph* h, Level& L)
 
 __device__ __forceinline__ int seg_bucket(int64_t len)
 {
-    return len <= 32 ? 0 : (len <= SEG_B1_CAP ? 1 : (len <= SEG_B2_CAP ? 2 : 3));
+    return len <= SEG_T_CAP ? SEG_BT
+         : len <= 32 ? SEG_BB0 : (len <= SEG_B1_CAP ? SEG_BB1 : (len <= SEG_B2_CAP ? SEG_BB2 : SEG_BB3));
 }
 
+// bucket flags packed two per int64 (pa: T, B0; pb: B1, B2; pc: B3)
 __global__ void k_seg_flags(const int64_t* __restrict__ hoff, int32_t E, int64_t* pa, int64_t* pb,
-                            int64_t* w2)
+                            int64_t* pc, int64_t* w2)
 {
     int64_t acc = 0;
     for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < E;
          a += (int64_t)gridDim.x * blockDim.x) {
         int64_t len = hoff[a + 1] - hoff[a];
         int b = seg_bucket(len);
-        pa[a] = (int64_t)(b == 0) | ((int64_t)(b == 1) << 32);
-        pb[a] = (int64_t)(b == 2) | ((int64_t)(b == 3) << 32);
+        pa[a] = (int64_t)(b == SEG_BT) | ((int64_t)(b == SEG_BB0) << 32);
+        pb[a] = (int64_t)(b == SEG_BB1) | ((int64_t)(b == SEG_BB2) << 32);
+        pc[a] = (int64_t)(b == SEG_BB3);
         acc += len * (len - 1);
     }
     acc = warp_sum(acc);
     if ((threadIdx.x & 31) == 0 && acc) atomicAdd((unsigned long long*)w2, (unsigned long long)acc);
 }
 
-__global__ void k_seg_meta(const int64_t* ta, const int64_t* tb, int32_t* meta)
+__global__ void k_seg_meta(const int64_t* tot, int32_t* meta)
 {
-    int32_t c0 = (int32_t)(*ta & 0xffffffff), c1 = (int32_t)(*ta >> 32);
-    int32_t c2 = (int32_t)(*tb & 0xffffffff), c3 = (int32_t)(*tb >> 32);
-    meta[0] = 0;
-    meta[1] = c0;
-    meta[2] = c0 + c1;
-    meta[3] = c0 + c1 + c2;
-    meta[4] = c0;
-    meta[5] = c1;
-    meta[6] = c2;
-    meta[7] = c3;
+    int32_t c[SEG_NB] = {(int32_t)(tot[0] & 0xffffffff), (int32_t)(tot[0] >> 32),
+                         (int32_t)(tot[1] & 0xffffffff), (int32_t)(tot[1] >> 32),
+                         (int32_t)(tot[2] & 0xffffffff)};
+    int32_t run = 0;
+    for (int b = 0; b < SEG_NB; b++) {
+        meta[b] = run;
+        meta[SEG_NB + b] = c[b];
+        run += c[b];
+    }
 }
 
 __global__ void k_seg_scatter(const int64_t* __restrict__ hoff, int32_t E,
                               const int64_t* __restrict__ pa, const int64_t* __restrict__ pb,
-                              const int32_t* __restrict__ meta, int32_t* list)
+                              const int64_t* __restrict__ pc, const int32_t* __restrict__ meta,
+                              int32_t* list)
 {
     for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < E;
          a += (int64_t)gridDim.x * blockDim.x) {
         int b = seg_bucket(hoff[a + 1] - hoff[a]);
-        int64_t pos = b == 0 ? (pa[a] & 0xffffffff)
-                    : b == 1 ? (pa[a] >> 32)
-                    : b == 2 ? (pb[a] & 0xffffffff)
-                             : (pb[a] >> 32);
+        int64_t pos = b == SEG_BT ? (pa[a] & 0xffffffff)
+                    : b == SEG_BB0 ? (pa[a] >> 32)
+                    : b == SEG_BB1 ? (pb[a] & 0xffffffff)
+                    : b == SEG_BB2 ? (pb[a] >> 32)
+                                   : (pc[a] & 0xffffffff);
         list[meta[b] + pos] = (int32_t)a;
     }
 }
@@ -173,10 +177,11 @@ __global__ void k_seg_scatter(const int64_t* __restrict__ hoff, int32_t E,
 Status seg_classify(const int64_t* hoff, int32_t E, int32_t maxlen, SegBuckets& b, Arena& ar,
                     cudaStream_t s, int64_t* w2)
 {
-    int64_t *pa, *pb, *tot;
+    int64_t *pa, *pb, *pc, *tot;
     SNN_TRY(ar.alloc(&pa, E));
     SNN_TRY(ar.alloc(&pb, E));
-    SNN_TRY(ar.alloc(&tot, 2));
+    SNN_TRY(ar.alloc(&pc, E));
+    SNN_TRY(ar.alloc(&tot, 3));
     b.b3_cap = 0;
     if (maxlen > SEG_B2_CAP) {
         int64_t c = SEG_B2_CAP;
@@ -184,15 +189,16 @@ Status seg_classify(const int64_t* hoff, int32_t E, int32_t maxlen, SegBuckets& 
         b.b3_cap = c;
     }
     if (E > 0) {
-        SNN_L k_seg_flags<<<grid_for(E, 256), 256, 0, s>>>(hoff, E, pa, pb, w2);
+        SNN_L k_seg_flags<<<grid_for(E, 256), 256, 0, s>>>(hoff, E, pa, pb, pc, w2);
         SNN_CUDA(cudaGetLastError());
     }
     SNN_TRY(scan_exclusive_i64(pa, pa, E, tot, ar, s));
     SNN_TRY(scan_exclusive_i64(pb, pb, E, tot + 1, ar, s));
-    SNN_L k_seg_meta<<<1, 1, 0, s>>>(tot, tot + 1, b.meta);
+    SNN_TRY(scan_exclusive_i64(pc, pc, E, tot + 2, ar, s));
+    SNN_L k_seg_meta<<<1, 1, 0, s>>>(tot, b.meta);
     SNN_CUDA(cudaGetLastError());
     if (E > 0) {
-        SNN_L k_seg_scatter<<<grid_for(E, 256), 256, 0, s>>>(hoff, E, pa, pb, b.meta, b.list);
+        SNN_L k_seg_scatter<<<grid_for(E, 256), 256, 0, s>>>(hoff, E, pa, pb, pc, b.meta, b.list);
         SNN_CUDA(cudaGetLastError());
     }
     return Status{};
@@ -343,6 +349,17 @@ struct BuildCheckJob {
             }
         }
         if (__any_sync(FULL, bad) && lane == 0) atomicOr((int*)&scal[SC_STATUS], ST_INVALID);
+    }
+    __device__ void finish_thread(int32_t a, const uint32_t* s, int n) const
+    {
+        int64_t base = hoff[a];
+        uint32_t src = (uint32_t)pins[base];
+        int bad = 0;
+        for (int i = 0; i < n; i++) {
+            if ((i > 0 && s[i - 1] == s[i]) || s[i] == src) bad = 1;
+            pins[base + 1 + i] = (int32_t)s[i];
+        }
+        if (bad) atomicOr((int*)&scal[SC_STATUS], ST_INVALID);
     }
 };
 

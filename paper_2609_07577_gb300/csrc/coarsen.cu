@@ -42,6 +42,7 @@ constexpr int MATCH_WALK = 64;
 template <typename S_>
 struct AffPol {
     using S = S_;
+    static constexpr bool kOptimistic = false;
     struct Acc {
         __device__ Acc() {}
         __device__ void add(const Acc&) {}
@@ -292,7 +293,7 @@ static Status affinity(snnmap_hgraph* h, Level& L)
     pol.cov = h->cov;
     int64_t* cnt;
     SNN_TRY(h->scratch.alloc(&cnt, HT_NTIER));
-    SNN_TRY(run_histogram(pol, h->scratch, h->stream, cnt, h->h_scal + 14, h->d_scal));
+    SNN_TRY(run_histogram(pol, h->scratch, h->stream, cnt, h->h_scal + 12, h->d_scal));
     int64_t hc[HT_NTIER] = {0, 0, 0, 0};
     SNN_CUDA(cudaMemcpyAsync(hc, cnt, HT_NTIER * sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream));
     SNN_CUDA(cudaStreamSynchronize(h->stream));

@@ -115,6 +115,33 @@ struct ContractJob {
             }
         }
     }
+    __device__ void finish_thread(int32_t a, const uint32_t* s, int n) const
+    {
+        int64_t base = hoff[a];
+        uint32_t sp = (uint32_t)cid[hpins[base]];
+        int cnt = 0, sd = hsd[a];
+        uint64_t hsum = 0;
+        for (int i = 0; i < n; i++) {
+            uint32_t v = s[i];
+            if (i > 0 && s[i - 1] == v) continue;
+            if (v == sp) {
+                sd = 1;
+                continue;
+            }
+            tpins[base + 1 + cnt++] = (int32_t)v;
+            hsum += mix64(v);
+        }
+        tpins[base] = (int32_t)sp;
+        if (cnt == 0) {
+            tlen[a] = 0;
+            if (sd) atomicAdd(&inint_next[sp], hk[a]);
+        } else {
+            tlen[a] = 1 + cnt;
+            tsd[a] = (uint8_t)sd;
+            uint64_t hh = hsum + mix64(0x5bd1e995ull + (uint64_t)sd) + mix64((uint64_t)cnt << 1);
+            thash[a] = (uint32_t)(hh ^ (hh >> 32));
+        }
+    }
 };
 
 __global__ void k_dedup_keys(int32_t E, const int32_t* __restrict__ tlen,

@@ -25,6 +25,8 @@
 //   typedef S (score type), struct Acc (per-thread sums, with add(Acc) and
 //   __device__ Acc reduce over a warp)
 //   int32_t V (vertices), key space bound `keys`
+//   static constexpr bool kOptimistic               try the warp tier even when the
+//                                                   bound exceeds its table (few keys expected)
 //   __device__ bool skip(n)                         n needs no histogram (result
 //                                                   written by write(n, 0, -1, 0, Acc()))
 //   __device__ int64_t seg_len(int64_t i)           segment length of incidence i
@@ -281,6 +283,7 @@ __global__ void __launch_bounds__(256)
             } else {
                 int64_t bound = work < pol.keys ? work : pol.keys;
                 if (bound <= HT_WLOAD) tier = work <= HT_WWORK ? HT_TIER_WARP : HT_TIER_SPLIT;
+                else if (Pol::kOptimistic && work <= HT_WWORK) tier = HT_TIER_WARP;
                 else if (work <= HT_BWORK) tier = HT_TIER_BLOCK;
                 else if (work <= HT_GWORK) tier = HT_TIER_BIG;
                 else tier = HT_TIER_SPLIT;
@@ -307,8 +310,8 @@ __global__ void __launch_bounds__(256)
 
 template <class Pol>
 __global__ void __launch_bounds__(HT_WARPS * 32)
-    k_ht_warp(Pol pol, const int32_t* __restrict__ lists, const int64_t* __restrict__ cnt,
-              const int64_t* __restrict__ workv)
+    k_ht_warp(Pol pol, int32_t* lists, int64_t* cnt, const int64_t* __restrict__ workv,
+              int64_t* scap)
 {
     using S = typename Pol::S;
     using Acc = typename Pol::Acc;
@@ -330,8 +333,18 @@ __global__ void __launch_bounds__(HT_WARPS * 32)
         if (cap > HT_WCAP) cap = HT_WCAP;
         Table<S> t = full;
         t.mask = (uint32_t)(cap - 1);
-        warp_visit<S>(pol, n, vb, ve, 32, t, acc);
+        // a vertex whose bound fits the table cannot overflow it; others
+        // (policies that expect few keys) try it and move on if it fills
+        bool sure = bound <= HT_WLOAD;
+        t.probes = sure ? (uint32_t)cap : 32u;
+        bool ok = warp_visit<S>(pol, n, vb, ve, 32, t, acc);
         __syncwarp();
+        if (!ok) {
+            clear_slots(t, lane, cap, 32);
+            if (lane == 0) ht_push(pol, HT_TIER_BLOCK, n, work, lists, cnt, scap);
+            __syncwarp();
+            continue;
+        }
         Acc tot = Pol::warp_reduce(acc);
         int64_t bs = 0;
         int32_t bk = -1;
@@ -470,10 +483,9 @@ __global__ void __launch_bounds__(T)
 
 // Split tier. The incidences of the split vertices are laid out flat
 // (vertex j owns flat positions [od[j], od[j+1])) and cut into work items of
-// about HT_ITEM elements: an item starts at a vertex's first incidence or
-// where the running element count crosses a multiple of HT_ITEM. Each item
-// is visited by one warp adding straight into the vertex's global table.
-constexpr int64_t HT_ITEM = 16384;
+// about `item` elements: an item starts at a vertex's first incidence or
+// where the running element count crosses a multiple of `item`. The item
+// size is chosen so that the items outnumber the resident warps.
 
 __device__ __forceinline__ int64_t find_owner(const int64_t* od, int64_t ns, int64_t f)
 {
@@ -487,11 +499,17 @@ __device__ __forceinline__ int64_t find_owner(const int64_t* od, int64_t ns, int
 }
 
 template <class Pol>
-__global__ void k_ht_split_deg(Pol pol, const int32_t* __restrict__ slist, int64_t ns, int64_t* deg)
+__global__ void k_ht_split_deg(Pol pol, const int32_t* __restrict__ slist, int64_t ns, int64_t* deg,
+                               const int64_t* __restrict__ workv, int64_t* total_work)
 {
+    int64_t w = 0;
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < ns;
-         j += (int64_t)gridDim.x * blockDim.x)
+         j += (int64_t)gridDim.x * blockDim.x) {
         deg[j] = pol.ve(slist[j]) - pol.vb(slist[j]);
+        w += workv[slist[j]];
+    }
+    w = warp_sum(w);
+    if ((threadIdx.x & 31) == 0 && w) atomicAdd((unsigned long long*)total_work, (unsigned long long)w);
 }
 
 template <class Pol>
@@ -507,7 +525,7 @@ __global__ void k_ht_split_len(Pol pol, const int32_t* __restrict__ slist, int64
 
 static __global__ void k_ht_split_starts(int64_t ns, const int64_t* __restrict__ od, int64_t D,
                                   const int64_t* __restrict__ x, const int64_t* __restrict__ len,
-                                  int32_t* start)
+                                  int32_t* start, int64_t item)
 {
     for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < D;
          f += (int64_t)gridDim.x * blockDim.x) {
@@ -516,7 +534,7 @@ static __global__ void k_ht_split_starts(int64_t ns, const int64_t* __restrict__
         int s = 0;
         if (f == od[j]) s = 1;
         else {
-            int64_t b0 = (x[f - 1] - base) / HT_ITEM, b1 = (x[f] - base) / HT_ITEM;
+            int64_t b0 = (x[f - 1] - base) / item, b1 = (x[f] - base) / item;
             s = b1 != b0;
         }
         start[f] = s;
@@ -689,7 +707,7 @@ Status run_histogram(const Pol& pol, Arena& ar, cudaStream_t s, int64_t* d_cnt, 
         attrs = true;
     }
     SNN_L k_ht_warp<Pol><<<(int)std::min<int64_t>(ceil_div(V, HT_WARPS), 152 * 8), HT_WARPS * 32, wsm,
-                           s>>>(pol, lists, d_cnt, workv);
+                           s>>>(pol, lists, d_cnt, workv, scap);
     SNN_CUDA(cudaGetLastError());
     SNN_L kb<<<(int)std::min<int64_t>(V, 152 * 8), HT_BTHREADS, bsm, s>>>(pol, lists, d_cnt, scap, workv);
     SNN_CUDA(cudaGetLastError());
@@ -707,13 +725,16 @@ Status run_histogram(const Pol& pol, Arena& ar, cudaStream_t s, int64_t* d_cnt, 
     SNN_TRY(ar.alloc(&tot, 4));
     SNN_CUDA(cudaMemsetAsync(tot, 0, 4 * sizeof(int64_t), s));
     SNN_TRY(scan_exclusive_i64(scap, toff, ns, tot, ar, s));
-    SNN_L k_ht_split_deg<Pol><<<grid_for(ns, 256), 256, 0, s>>>(pol, sl, ns, deg);
+    SNN_L k_ht_split_deg<Pol><<<grid_for(ns, 256), 256, 0, s>>>(pol, sl, ns, deg, workv, tot + 2);
     SNN_CUDA(cudaGetLastError());
     SNN_TRY(scan_exclusive_i64(deg, od, ns, od + ns, ar, s));
     SNN_CUDA(cudaMemcpyAsync(h_cnt, tot, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     SNN_CUDA(cudaMemcpyAsync(h_cnt + 1, od + ns, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    SNN_CUDA(cudaMemcpyAsync(h_cnt + 2, tot + 2, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     SNN_CUDA(cudaStreamSynchronize(s));
     int64_t slots = h_cnt[0], D = h_cnt[1];
+    int64_t item = pow2_ceil(h_cnt[2] / (152 * 64 * 2) + 1);
+    item = item < 1024 ? 1024 : (item > 16384 ? 16384 : item);
     int64_t *len, *x, *item_f0;
     int32_t *start, *pos;
     SNN_TRY(ar.alloc(&len, D));
@@ -724,7 +745,7 @@ Status run_histogram(const Pol& pol, Arena& ar, cudaStream_t s, int64_t* d_cnt, 
     SNN_L k_ht_split_len<Pol><<<grid_for(D, 256), 256, 0, s>>>(pol, sl, ns, od, D, len);
     SNN_CUDA(cudaGetLastError());
     SNN_TRY(scan_exclusive_i64(len, x, D, nullptr, ar, s));
-    SNN_L k_ht_split_starts<<<grid_for(D, 256), 256, 0, s>>>(ns, od, D, x, len, start);
+    SNN_L k_ht_split_starts<<<grid_for(D, 256), 256, 0, s>>>(ns, od, D, x, len, start, item);
     SNN_CUDA(cudaGetLastError());
     SNN_TRY(scan_exclusive_i32(start, pos, D, (int32_t*)(tot + 1), ar, s));
     SNN_L k_ht_split_items<<<grid_for(D, 256), 256, 0, s>>>(D, start, pos, item_f0);

@@ -153,6 +153,34 @@ struct PinCountJob {
             if (R > 1) atomicAdd((unsigned long long*)&scal[RS_COST], (unsigned long long)(hw[a] * (R - 1)));
         }
     }
+    __device__ void finish_thread(int32_t a, const uint32_t* s, int n) const
+    {
+        int64_t base = hoff[a];
+        int R = 0, c = 0, d = 0;
+        for (int i = 0; i < n; i++) {
+            uint32_t p = s[i] >> 1;
+            if (i > 0 && p != (s[i - 1] >> 1)) {
+                pc.p[base + R] = (int32_t)(s[i - 1] >> 1);
+                pc.cnt[base + R] = c;
+                pc.dcnt[base + R] = d;
+                if (d > 0) atomicAdd((unsigned long long*)&pincnt[s[i - 1] >> 1], (unsigned long long)hk[a]);
+                R++;
+                c = 0;
+                d = 0;
+            }
+            c++;
+            d += (int)(s[i] & 1);
+        }
+        if (n > 0) {
+            pc.p[base + R] = (int32_t)(s[n - 1] >> 1);
+            pc.cnt[base + R] = c;
+            pc.dcnt[base + R] = d;
+            if (d > 0) atomicAdd((unsigned long long*)&pincnt[s[n - 1] >> 1], (unsigned long long)hk[a]);
+            R++;
+        }
+        pc.lam[a] = R;
+        if (R > 1) atomicAdd((unsigned long long*)&scal[RS_COST], (unsigned long long)(hw[a] * (R - 1)));
+    }
 };
 
 __global__ void k_pstate_vertices(Level L, const int32_t* __restrict__ rho, PState ps)
@@ -188,6 +216,8 @@ __global__ void k_check_pstate(int32_t K, PState ps, int32_t omega, int32_t delt
 template <typename S_>
 struct GainPol {
     using S = S_;
+    // a vertex meets few partitions even when its bound is large
+    static constexpr bool kOptimistic = true;
     struct Acc {
         int64_t W, save;   // summed omega of incident hyperedges; of those n is the last pin of
         __device__ Acc() : W(0), save(0) {}
@@ -650,7 +680,7 @@ static Status gains(snnmap_hgraph* h, Level& L, const PinCounts& pc, const int32
     pol.pgain = pgain;
     int64_t* cnt;
     SNN_TRY(h->scratch.alloc(&cnt, HT_NTIER));
-    return run_histogram(pol, h->scratch, h->stream, cnt, h->h_scal + 14, h->d_scal);
+    return run_histogram(pol, h->scratch, h->stream, cnt, h->h_scal + 12, h->d_scal);
 }
 
 // pin counts + partition state + Conn for rho

@@ -1,6 +1,7 @@
 // Segmented sort of small uint32 key lists, one list per hyperedge, followed
 // by a per-hyperedge epilogue. Hyperedges are split into size buckets once
 // per level (by pin count L):
+//   T:  L <= 16      one thread, keys in a local array (insertion sort)
 //   B0: L <= 32      one warp, keys in registers (shuffle bitonic network)
 //   B1: L <= 256     one warp, keys in a per-warp shared-memory slice
 //   B2: L <= 16384   one block of 512 threads, keys in dynamic shared memory
@@ -14,11 +15,14 @@
 //   __device__ uint32_t load(int32_t a, int i)   key i (0 <= i < len)
 //   __device__ void finish(int32_t a, const uint32_t* s, int n)
 //        run by one full warp on the n sorted keys s[0..n)
+//   __device__ void finish_thread(int32_t a, const uint32_t* s, int n)
+//        the same, run by a single thread
 #pragma once
 #include "common.cuh"
 
 namespace snn {
 
+constexpr int SEG_T_CAP = 16;
 constexpr int SEG_B1_CAP = 256;
 constexpr int SEG_B2_CAP = 16384;
 constexpr int SEG_B2_THREADS = 512;
@@ -27,7 +31,8 @@ constexpr int SEG_B3_BLOCKS = 16;
 constexpr uint32_t KEY_PAD = 0xffffffffu;
 
 // Per-level bucket lists of hyperedge ids: one array of E ids holding the
-// four buckets back to back; meta (device int32[8]) = start[4], count[4].
+// buckets (T, B0, B1, B2, B3) back to back; meta (device int32[10]) =
+// start[5], count[5].
 struct SegBuckets {
     int32_t* list = nullptr;
     int32_t* meta = nullptr;
@@ -101,14 +106,39 @@ __device__ __forceinline__ void block_bitonic(uint32_t* s, int N)
     }
 }
 
+enum : int { SEG_BT = 0, SEG_BB0 = 1, SEG_BB1 = 2, SEG_BB2 = 3, SEG_BB3 = 4, SEG_NB = 5 };
+
+template <class Job>
+__global__ void __launch_bounds__(256) k_seg_t(Job job, const int32_t* __restrict__ lists,
+                                               const int32_t* __restrict__ meta)
+{
+    const int32_t* list = lists + meta[SEG_BT];
+    int n = meta[SEG_NB + SEG_BT];
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+        int32_t a = list[idx];
+        int L = job.len(a);
+        uint32_t k[SEG_T_CAP];
+        for (int i = 0; i < L; i++) {
+            uint32_t v = job.load(a, i);
+            int j = i;
+            while (j > 0 && k[j - 1] > v) {
+                k[j] = k[j - 1];
+                j--;
+            }
+            k[j] = v;
+        }
+        job.finish_thread(a, k, L);
+    }
+}
+
 template <class Job>
 __global__ void __launch_bounds__(256) k_seg_b0(Job job, const int32_t* __restrict__ lists,
                                                 const int32_t* __restrict__ meta)
 {
     __shared__ uint32_t buf[8][32];
     int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int32_t* list = lists + meta[0];
-    int n = meta[4];
+    const int32_t* list = lists + meta[SEG_BB0];
+    int n = meta[SEG_NB + SEG_BB0];
     for (int idx = blockIdx.x * 8 + warp; idx < n; idx += gridDim.x * 8) {
         int32_t a = list[idx];
         int L = job.len(a);
@@ -127,8 +157,8 @@ __global__ void __launch_bounds__(256) k_seg_b1(Job job, const int32_t* __restri
 {
     __shared__ uint32_t buf[8][SEG_B1_CAP];
     int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int32_t* list = lists + meta[1];
-    int n = meta[5];
+    const int32_t* list = lists + meta[SEG_BB1];
+    int n = meta[SEG_NB + SEG_BB1];
     uint32_t* s = buf[warp];
     for (int idx = blockIdx.x * 8 + warp; idx < n; idx += gridDim.x * 8) {
         int32_t a = list[idx];
@@ -151,7 +181,7 @@ __global__ void k_seg_big(Job job, const int32_t* __restrict__ lists,
     extern __shared__ uint32_t sbuf[];
     uint32_t* s = gscratch ? gscratch + (int64_t)blockIdx.x * cap : sbuf;
     const int32_t* list = lists + meta[bucket];
-    int n = meta[4 + bucket];
+    int n = meta[SEG_NB + bucket];
     for (int idx = blockIdx.x; idx < n; idx += gridDim.x) {
         int32_t a = list[idx];
         int L = job.len(a);
@@ -178,6 +208,8 @@ template <class Job>
 Status seg_run(const Job& job, const SegBuckets& b, int32_t E, Arena& ar, cudaStream_t s)
 {
     if (E <= 0) return Status{};
+    SNN_L k_seg_t<Job><<<grid_for(E, 256, 152 * 16), 256, 0, s>>>(job, b.list, b.meta);
+    SNN_CUDA(cudaGetLastError());
     SNN_L k_seg_b0<Job><<<seg_grid_small(E), 256, 0, s>>>(job, b.list, b.meta);
     SNN_CUDA(cudaGetLastError());
     SNN_L k_seg_b1<Job><<<seg_grid_small(E), 256, 0, s>>>(job, b.list, b.meta);
@@ -190,15 +222,15 @@ Status seg_run(const Job& job, const SegBuckets& b, int32_t E, Arena& ar, cudaSt
                                           (int)smem));
             attr_set = true;
         }
-        SNN_L k_seg_big<Job><<<seg_grid_big(E), SEG_B2_THREADS, smem, s>>>(job, b.list, b.meta, 2,
-                                                                      nullptr, 0);
+        SNN_L k_seg_big<Job><<<seg_grid_big(E), SEG_B2_THREADS, smem, s>>>(job, b.list, b.meta,
+                                                                            SEG_BB2, nullptr, 0);
         SNN_CUDA(cudaGetLastError());
     }
     if (b.b3_cap > 0) {
         uint32_t* g = nullptr;
         SNN_TRY(ar.alloc(&g, (int64_t)SEG_B3_BLOCKS * b.b3_cap));
-        SNN_L k_seg_big<Job><<<SEG_B3_BLOCKS, SEG_B3_THREADS, 0, s>>>(job, b.list, b.meta, 3, g,
-                                                                 b.b3_cap);
+        SNN_L k_seg_big<Job><<<SEG_B3_BLOCKS, SEG_B3_THREADS, 0, s>>>(job, b.list, b.meta, SEG_BB3,
+                                                                       g, b.b3_cap);
         SNN_CUDA(cudaGetLastError());
     }
     return Status{};

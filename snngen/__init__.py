@@ -311,6 +311,8 @@ def by_name(name: str) -> Hypergraph:
                               name="cfg2s"),
         "cfg2m": lambda: conv(8, 32, 8, 4, seed=12, omega=1024, delta=4096, phi=16384,
                               name="cfg2m"),
+        "cfg2q": lambda: conv(8, 64, 8, 4, seed=13, omega=1024, delta=4096, phi=16384,
+                              name="cfg2q"),
         "cfg3s": lambda: powerlaw(1 << 14, 4096, 8, 2048, 2.1, 0.7, seed=21,
                                   omega=512, delta=2048, phi=8192, name="cfg3s"),
         "cfg3m": lambda: powerlaw(1 << 17, 65536, 8, 16384, 2.1, 0.7, seed=22,
