@@ -242,6 +242,16 @@ int snnmap_profile(snnmap_hgraph* h, int32_t on);
 /* Copies up to cap stage records; *n receives the number of stages. */
 int snnmap_stage_times(snnmap_hgraph* h, snnmap_stage_time* out, int32_t cap, int32_t* n);
 
+/*
+ * Memory of the hierarchy. Level 0 and the coarsest level always stay in
+ * memory; the others keep only their sizes and cid map once their arrays
+ * would exceed `bytes` (0: 40% of the device's memory, the default), and are
+ * rebuilt exactly from the nearest level below that is still in memory when
+ * a later call needs them (refinement, inspection). Results do not depend on
+ * the budget.
+ */
+int snnmap_set_level_budget(snnmap_hgraph* h, int64_t bytes);
+
 /* Bytes of device memory the handle currently holds. */
 int snnmap_device_bytes(const snnmap_hgraph* h, int64_t* bytes);
 

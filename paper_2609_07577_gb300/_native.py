@@ -77,6 +77,7 @@ _SIGS = {
     "snnmap_profile": (C.c_int, [_vp, _i32]),
     "snnmap_stage_times": (C.c_int, [_vp, _vp, _i32, C.POINTER(_i32)]),
     "snnmap_launch_count": (_i64, []),
+    "snnmap_set_level_budget": (C.c_int, [_vp, _i64]),
     "snnmap_connectivity_noalloc": (C.c_int, [_i32, _i32, _vp, _vp, _vp, _vp, _i32, _vp, _vp]),
     "snnmap_free": (None, [_vp]),
     "snnmap_last_error": (C.c_char_p, []),
@@ -257,6 +258,10 @@ def snnmap_connectivity_noalloc(n_vertices, n_hedges, d_offsets, d_pins, d_w, d_
     check(lib().snnmap_connectivity_noalloc(int(n_vertices), int(n_hedges), _p(d_offsets),
                                             _p(d_pins), _p(d_w), _p(d_rho), int(n_parts),
                                             _p(d_cost_out), _stream(stream)))
+
+
+def snnmap_set_level_budget(h, nbytes):
+    check(lib().snnmap_set_level_budget(h, int(nbytes)))
 
 
 def snnmap_launch_count():

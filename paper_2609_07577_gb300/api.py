@@ -116,6 +116,9 @@ class HGraph:
     def level_logs(self):
         return N.snnmap_level_logs(self._h)
 
+    def set_level_budget(self, nbytes):
+        N.snnmap_set_level_budget(self._h, nbytes)
+
     def profile(self, on=True):
         N.snnmap_profile(self._h, on)
 

@@ -155,6 +155,11 @@ int snnmap_build_hgraph(const snnmap_params* params, int32_t n_vertices, int32_t
     h->extra.reserve((size_t)params->max_levels + 2);
     int32_t cap = n_vertices > 0 ? n_vertices : 1;
     h->cap_v = cap;
+    {
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) h->level_budget = (int64_t)(tot * 2 / 5);
+        else h->level_budget = (int64_t)1 << 34;
+    }
     cudaError_t e = cudaMallocHost(&h->h_scal, snn::SC_COUNT * sizeof(int64_t));
     if (e == cudaSuccess) e = cudaMallocAsync(&h->d_scal, snn::SC_COUNT * sizeof(int64_t), h->stream);
     if (e == cudaSuccess) e = cudaMallocAsync(&h->cand, (size_t)cap * 4, h->stream);
@@ -198,6 +203,7 @@ int snnmap_contract(snnmap_hgraph* h, void* stream, int32_t* V_out, int32_t* E_o
     if (!h) return fail(SNNMAP_ERR_INVALID, "NULL handle");
     bind(h, stream);
     API_TRY(snn::contract_level(h));
+    snn::thin_levels(h);
     const snn::Level& N = h->levels.back();
     if (V_out) *V_out = N.V;
     if (E_out) *E_out = N.E;
@@ -247,6 +253,7 @@ int snnmap_refine(snnmap_hgraph* h, int32_t level, int32_t n_parts, int32_t* d_r
     if (n_parts < 1 || !is_device_ptr(d_rho)) return fail(SNNMAP_ERR_INVALID, "bad rho / n_parts");
     bind(h, stream);
     int64_t c = 0;
+    API_TRY(snn::ensure_resident(h, level));
     API_TRY(snn::check_rho(h, level, n_parts, d_rho));
     API_TRY(snn::refine_level(h, level, n_parts, d_rho, &c, nullptr));
     if (cost_out) *cost_out = c;
@@ -273,6 +280,7 @@ int snnmap_partition(snnmap_hgraph* h, void* stream, int32_t* d_rho_out, int64_t
     if (!is_device_ptr(d_rho_out)) return fail(SNNMAP_ERR_INVALID, "d_rho_out must be device memory");
     bind(h, stream);
     drop_levels_above(h, 1);
+    h->keep_stride = 1;
     h->rlog.clear();
     h->llog.clear();
     snnmap_stats st{};
@@ -287,6 +295,7 @@ int snnmap_partition(snnmap_hgraph* h, void* stream, int32_t* d_rho_out, int64_t
                                             h->extra.back().n_block, h->extra.back().n_global});
         if (nc == 0 || np == 0) break;
         API_TRY(snn::contract_level(h));
+        snn::thin_levels(h);
     }
     int32_t nl = (int32_t)h->levels.size();
     int32_t V0 = h->levels[0].V;
@@ -305,6 +314,11 @@ int snnmap_partition(snnmap_hgraph* h, void* stream, int32_t* d_rho_out, int64_t
     int64_t cost = 0;
     for (int32_t l = nl - 1; s2.ok() && l >= 0; l--) {
         if (l < nl - 1) {
+            // a level rebuilt for its refinement is released again
+            if (l + 1 < nl - 1 && (l + 1) % h->keep_stride != 0)
+                snn::level_release(h, h->levels[l + 1]);
+            s2 = snn::ensure_resident(h, l);
+            if (!s2.ok()) break;
             s2 = snn::project(h, l, cur, oth);
             if (!s2.ok()) break;
             std::swap(cur, oth);
@@ -379,6 +393,9 @@ int snnmap_level_copy(const snnmap_hgraph* h, int32_t level, int64_t* d_off, int
     g_err.clear();
     if (!h || level < 0 || level >= (int32_t)h->levels.size())
         return fail(SNNMAP_ERR_INVALID, "no such level");
+    snnmap_hgraph* hm = const_cast<snnmap_hgraph*>(h);
+    bind(hm, stream);
+    API_TRY(snn::ensure_resident(hm, level));
     const snn::Level& L = h->levels[level];
     cudaStream_t s = (cudaStream_t)stream;
     struct Item {
@@ -491,8 +508,21 @@ int snnmap_device_bytes(const snnmap_hgraph* h, int64_t* bytes)
 {
     if (!h || !bytes) return fail(SNNMAP_ERR_INVALID, "NULL argument");
     int64_t t = (int64_t)h->scratch.held() + (int64_t)h->cap_v * 20;
-    for (auto& L : h->levels) t += (int64_t)L.bytes;
+    for (auto& L : h->levels) t += (int64_t)L.bytes + 4 * (int64_t)L.V;
     *bytes = t;
+    return SNNMAP_OK;
+}
+
+int snnmap_set_level_budget(snnmap_hgraph* h, int64_t bytes)
+{
+    if (!h || bytes < 0) return fail(SNNMAP_ERR_INVALID, "bad arguments");
+    if (bytes == 0) {
+        size_t fr = 0, tot = 0;
+        bytes = cudaMemGetInfo(&fr, &tot) == cudaSuccess ? (int64_t)(tot * 2 / 5) : ((int64_t)1 << 34);
+    }
+    h->level_budget = bytes;
+    h->keep_stride = 1;
+    snn::thin_levels(h);
     return SNNMAP_OK;
 }
 

@@ -100,7 +100,6 @@ Status level_alloc(snnmap_hgraph* h, Level& L, LevelExtra& X, int32_t V, int32_t
     c.add(&L.vinpins, V);
     c.add(&L.vincnt, V);
     c.add(&L.vinint, V);
-    c.add(&L.cid, V);
     c.add(&X.seg.list, E);
     c.add(&X.seg.meta, 2 * SEG_NB);
     void* p = nullptr;
@@ -108,13 +107,30 @@ Status level_alloc(snnmap_hgraph* h, Level& L, LevelExtra& X, int32_t V, int32_t
     c.assign(p);
     L.block = p;
     L.bytes = c.total;
+    if (!L.cid) SNN_CUDA(cudaMallocAsync((void**)&L.cid, (size_t)(V > 0 ? V : 1) * 4, h->stream));
+    L.resident = true;
     return Status{};
 }
 
 void level_free(snnmap_hgraph* h, Level& L)
 {
     if (L.block) cudaFreeAsync(L.block, h->stream);
+    if (L.cid) cudaFreeAsync(L.cid, h->stream);
     L = Level{};
+}
+
+void level_release(snnmap_hgraph* h, Level& L)
+{
+    if (!L.resident) return;
+    if (L.block) cudaFreeAsync(L.block, h->stream);
+    int32_t* cid = L.cid;
+    Level k;
+    k.V = L.V;
+    k.E = L.E;
+    k.P = L.P;
+    k.maxlen = L.maxlen;
+    k.cid = cid;
+    L = k;
 }
 
 // ---------------------------------------------------------------------------

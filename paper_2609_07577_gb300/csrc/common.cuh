@@ -113,10 +113,11 @@ struct Level {
     int32_t* vinpins = nullptr;
     int32_t* vincnt = nullptr;
     int32_t* vinint = nullptr;
-    int32_t* cid = nullptr;      // map to the next level (after contraction)
+    int32_t* cid = nullptr;      // map to the next level (own allocation, always kept)
     int32_t maxlen = 0;          // longest hyperedge
-    void* block = nullptr;       // single allocation holding everything above
+    void* block = nullptr;       // single allocation holding every array but cid
     size_t bytes = 0;
+    bool resident = false;       // arrays in memory (else only sizes and cid)
 };
 
 constexpr uint32_t SRC_BIT = 0x80000000u;

@@ -3,8 +3,11 @@
 //
 // 1. Coarse ids: a vertex represents its pair if it is unmatched or the
 //    lower id of the pair; cid = rank of the representative (exclusive scan).
-// 2. Super-node state: size, inbound pins and internal axons add up; the
-//    merged inbound set has in_count(n) + in_count(m) - shared(n, m).
+// 2. Super-node state: size, inbound pins and internal axons add up over the
+//    members; the size of the merged inbound set (the paper's
+//    in_count(n) + in_count(m) - shared(n, m)) is recomputed from the coarse
+//    level as internal axons + the k of every coarse hyperedge the
+//    super-node is a destination of, which the two share.
 // 3. Per hyperedge (segmented sort): s' = cid(source), destinations mapped
 //    through cid, sorted, made unique; s' among them sets selfdst and is
 //    removed. A hyperedge left with no destination is dropped and its
@@ -14,6 +17,11 @@
 //    together, an exact comparison of the contents decides, and the first
 //    of each equal group becomes the coarse hyperedge; omega and k add up.
 // 5. Compaction into the next level's arrays, then its incidence lists.
+//
+// The same routine (build_coarse) materializes any level l from a resident
+// level j < l through the composed map cid_{l-1} o ... o cid_j: the image of
+// an axon does not depend on the order of the merges, so a level whose
+// arrays were released to save memory is rebuilt exactly.
 #include "internal.cuh"
 
 #include <memory>
@@ -30,33 +38,51 @@ __global__ void k_rep_flags(int32_t V, const int32_t* __restrict__ match, int32_
 }
 
 struct NextState {
-    int32_t *size, *inpins, *incnt, *inint;
+    int32_t *size, *inpins, *inint;
 };
 
-__global__ void k_cid_state(Level L, const int32_t* __restrict__ match,
-                            const int32_t* __restrict__ cand, const int32_t* __restrict__ cov,
-                            const int32_t* __restrict__ repidx, NextState ns)
+__global__ void k_cid_map(int32_t V, const int32_t* __restrict__ match,
+                          const int32_t* __restrict__ repidx, int32_t* cid)
 {
-    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < L.V;
+    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < V;
          n += (int64_t)gridDim.x * blockDim.x) {
         int32_t m = match[n];
-        if (!(m < 0 || (int32_t)n < m)) continue;
-        int32_t c = repidx[n];
-        L.cid[n] = c;
-        if (m < 0) {
-            ns.size[c] = L.vsize[n];
-            ns.inpins[c] = L.vinpins[n];
-            ns.incnt[c] = L.vincnt[n];
-            ns.inint[c] = L.vinint[n];
-        } else {
-            L.cid[m] = c;
-            int32_t ov = cand[n] == m ? cov[n] : cov[m];
-            ns.size[c] = L.vsize[n] + L.vsize[m];
-            ns.inpins[c] = L.vinpins[n] + L.vinpins[m];
-            ns.incnt[c] = L.vincnt[n] + L.vincnt[m] - ov;
-            ns.inint[c] = L.vinint[n] + L.vinint[m];
-        }
+        cid[n] = repidx[(m < 0 || (int32_t)n < m) ? (int32_t)n : m];
     }
+}
+
+// member sums per coarse vertex
+__global__ void k_sum_state(Level S, const int32_t* __restrict__ map, NextState ns)
+{
+    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < S.V;
+         n += (int64_t)gridDim.x * blockDim.x) {
+        int32_t u = map[n];
+        atomicAdd(&ns.size[u], S.vsize[n]);
+        atomicAdd(&ns.inpins[u], S.vinpins[n]);
+        if (S.vinint[n]) atomicAdd(&ns.inint[u], S.vinint[n]);
+    }
+}
+
+// in_count += k(a) for every destination of every hyperedge a (vincnt must
+// hold the internal counts on entry)
+__global__ void k_in_count(Level N)
+{
+    int lane = threadIdx.x & 31;
+    int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t a = gw; a < N.E; a += nw) {
+        int64_t b = N.hoff[a], e = N.hoff[a + 1];
+        int32_t k = N.hk[a];
+        for (int64_t j = b + 1 + lane; j < e; j += 32) atomicAdd(&N.vincnt[N.hpins[j]], k);
+        if (lane == 0 && N.hsd[a]) atomicAdd(&N.vincnt[N.hpins[b]], k);
+    }
+}
+
+__global__ void k_compose(int64_t n, int32_t* c, const int32_t* __restrict__ next)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        c[i] = next[c[i]];
 }
 
 // Remaps one hyperedge's destinations through cid; output at the same
@@ -248,34 +274,34 @@ __global__ void k_dedup_emit(int32_t E, const uint32_t* __restrict__ vals,
 
 __global__ void k_set_off_end(int64_t* hoff, int32_t E, int64_t P) { hoff[E] = P; }
 
-Status contract_level(snnmap_hgraph* h)
+// Materializes levels[dst] from the resident levels[src] through `map`
+// (int32[V(src)] into the new level's ids); *d_V2 (device) is its vertex
+// count. If levels[dst] already records sizes (a released level being
+// rebuilt), the rebuilt sizes must match them.
+Status build_coarse(snnmap_hgraph* h, int32_t src, const int32_t* map, const int64_t* d_V2,
+                    int32_t dst)
 {
-    if (!h->have_matching || h->last_pairs <= 0) return Status{SNNMAP_ERR_STATE, "no matching to contract"};
     cudaStream_t s = h->stream;
     Arena& ar = h->scratch;
-    Level& L = h->levels.back();
-    LevelExtra& X = h->extra.back();
+    Level& L = h->levels[src];
+    LevelExtra& X = h->extra[src];
     int32_t V = L.V, E = L.E;
-    int g = grid_for(V, 256);
     SNN_TRY(zero_scalars(h));
     std::unique_ptr<ProfScope> prof(new ProfScope(h, PS_CONTRACT));
-
-    // 1-2. coarse ids and super-node state
-    int32_t *isrep, *repidx;
     NextState ns;
-    SNN_TRY(ar.alloc(&isrep, V));
-    SNN_TRY(ar.alloc(&repidx, V));
     SNN_TRY(ar.alloc(&ns.size, V));
     SNN_TRY(ar.alloc(&ns.inpins, V));
-    SNN_TRY(ar.alloc(&ns.incnt, V));
     SNN_TRY(ar.alloc(&ns.inint, V));
-    SNN_L k_rep_flags<<<g, 256, 0, s>>>(V, h->match, isrep);
-    SNN_CUDA(cudaGetLastError());
-    SNN_TRY(scan_exclusive_i32(isrep, repidx, V, (int32_t*)(h->d_scal + SC_A), ar, s));
-    SNN_L k_cid_state<<<g, 256, 0, s>>>(L, h->match, h->cand, h->cov, repidx, ns);
-    SNN_CUDA(cudaGetLastError());
+    if (V > 0) {
+        SNN_CUDA(cudaMemsetAsync(ns.size, 0, (size_t)V * 4, s));
+        SNN_CUDA(cudaMemsetAsync(ns.inpins, 0, (size_t)V * 4, s));
+        SNN_CUDA(cudaMemsetAsync(ns.inint, 0, (size_t)V * 4, s));
+        SNN_L k_sum_state<<<grid_for(V, 256), 256, 0, s>>>(L, map, ns);
+        SNN_CUDA(cudaGetLastError());
+    }
+    SNN_CUDA(cudaMemcpyAsync(h->d_scal + SC_A, d_V2, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
 
-    // 3. per-hyperedge remap, sort, unique
+    // per-hyperedge remap, sort, unique
     int32_t *tpins, *tlen;
     uint8_t* tsd;
     uint32_t* thash;
@@ -283,10 +309,10 @@ Status contract_level(snnmap_hgraph* h)
     SNN_TRY(ar.alloc(&tlen, E));
     SNN_TRY(ar.alloc(&tsd, E));
     SNN_TRY(ar.alloc(&thash, E));
-    ContractJob job{L.hoff, L.hpins, L.hsd, L.hk, L.cid, tpins, tlen, tsd, thash, ns.inint};
+    ContractJob job{L.hoff, L.hpins, L.hsd, L.hk, map, tpins, tlen, tsd, thash, ns.inint};
     SNN_TRY(seg_run(job, X.seg, E, ar, s));
 
-    // 4. duplicate hyperedges
+    // duplicate hyperedges
     uint64_t *keys, *keys2;
     uint32_t *vals, *vals2;
     int32_t *headpos, *runstart, *rep, *head, *gidh, *gid, *tk;
@@ -330,41 +356,119 @@ Status contract_level(snnmap_hgraph* h)
     SNN_TRY(scan_exclusive_i64(newlen, newoff, E, h->d_scal + SC_C, ar, s));
     prof.reset();
     SNN_TRY(read_scalars(h));
-    int32_t V2 = (int32_t)(h->h_scal[SC_A] & 0xffffffff);
+    int32_t V2 = (int32_t)h->h_scal[SC_A];
     int32_t E2 = (int32_t)(h->h_scal[SC_B] & 0xffffffff);
     int64_t P2 = h->h_scal[SC_C];
 
-    // 5. next level
-    h->levels.emplace_back();
-    h->extra.emplace_back();
-    Level& N = h->levels.back();
-    LevelExtra& NX = h->extra.back();
-    Level& Lp = h->levels[h->levels.size() - 2];
+    Level& N = h->levels[dst];
+    LevelExtra& NX = h->extra[dst];
+    if (N.E != 0 || N.P != 0 || N.V != 0) {
+        if (N.V != V2 || N.E != E2 || N.P != P2)
+            return Status{SNNMAP_ERR_CUDA, "rebuilt level differs from the released one"};
+    }
     SNN_TRY(level_alloc(h, N, NX, V2, E2, P2));
-    N.maxlen = Lp.maxlen;
+    N.maxlen = L.maxlen;
     prof.reset(new ProfScope(h, PS_CONTRACT));
     if (V2 > 0) {
         SNN_CUDA(cudaMemcpyAsync(N.vsize, ns.size, (size_t)V2 * 4, cudaMemcpyDeviceToDevice, s));
         SNN_CUDA(cudaMemcpyAsync(N.vinpins, ns.inpins, (size_t)V2 * 4, cudaMemcpyDeviceToDevice, s));
-        SNN_CUDA(cudaMemcpyAsync(N.vincnt, ns.incnt, (size_t)V2 * 4, cudaMemcpyDeviceToDevice, s));
         SNN_CUDA(cudaMemcpyAsync(N.vinint, ns.inint, (size_t)V2 * 4, cudaMemcpyDeviceToDevice, s));
+        SNN_CUDA(cudaMemcpyAsync(N.vincnt, ns.inint, (size_t)V2 * 4, cudaMemcpyDeviceToDevice, s));
     }
     if (E > 0) {
         SNN_L k_dedup_emit<<<grid_for((int64_t)E * 32, 256), 256, 0, s>>>(
-            E, vals, rep, gid, Lp.hoff, tpins, tlen, tsd, tw, tk, newoff, N);
+            E, vals, rep, gid, L.hoff, tpins, tlen, tsd, tw, tk, newoff, N);
         SNN_CUDA(cudaGetLastError());
     }
     SNN_L k_set_off_end<<<1, 1, 0, s>>>(N.hoff, E2, P2);
     SNN_CUDA(cudaGetLastError());
+    if (E2 > 0) {
+        SNN_L k_in_count<<<grid_for((int64_t)E2 * 32, 256), 256, 0, s>>>(N);
+        SNN_CUDA(cudaGetLastError());
+    }
     prof.reset();
     SNN_TRY(build_incidence(h, N));
     SNN_CUDA(cudaMemsetAsync(h->d_scal + SC_W2, 0, sizeof(int64_t), s));
     SNN_TRY(seg_classify(N.hoff, E2, N.maxlen, NX.seg, ar, s, h->d_scal + SC_W2));
-    h->have_matching = false;
     SNN_TRY(read_scalars(h));
     NX.pair_terms = h->h_scal[SC_W2];
     ar.reset();
     return Status{};
+}
+
+Status contract_level(snnmap_hgraph* h)
+{
+    if (!h->have_matching || h->last_pairs <= 0) return Status{SNNMAP_ERR_STATE, "no matching to contract"};
+    cudaStream_t s = h->stream;
+    Arena& ar = h->scratch;
+    int32_t src = (int32_t)h->levels.size() - 1;
+    Level& L = h->levels[src];
+    int32_t V = L.V;
+    int32_t *isrep, *repidx;
+    int64_t* d_V2;
+    SNN_TRY(ar.alloc(&isrep, V));
+    SNN_TRY(ar.alloc(&repidx, V));
+    SNN_TRY(ar.alloc(&d_V2, 1));
+    SNN_CUDA(cudaMemsetAsync(d_V2, 0, sizeof(int64_t), s));
+    {
+        ProfScope prof(h, PS_CONTRACT);
+        SNN_L k_rep_flags<<<grid_for(V, 256), 256, 0, s>>>(V, h->match, isrep);
+        SNN_CUDA(cudaGetLastError());
+        SNN_TRY(scan_exclusive_i32(isrep, repidx, V, (int32_t*)d_V2, ar, s));
+        SNN_L k_cid_map<<<grid_for(V, 256), 256, 0, s>>>(V, h->match, repidx, L.cid);
+        SNN_CUDA(cudaGetLastError());
+    }
+    h->levels.emplace_back();
+    h->extra.emplace_back();
+    SNN_TRY(build_coarse(h, src, h->levels[src].cid, d_V2, src + 1));
+    h->have_matching = false;
+    return Status{};
+}
+
+// Intermediate levels (neither level 0 nor the coarsest) stay resident when
+// their index is a multiple of keep_stride; the stride doubles while their
+// bytes exceed the budget. Released levels keep their sizes and cid map.
+void thin_levels(snnmap_hgraph* h)
+{
+    int32_t top = (int32_t)h->levels.size() - 1;
+    auto held = [&]() {
+        int64_t b = 0;
+        for (int32_t i = 1; i < top; i++)
+            if (h->levels[i].resident) b += (int64_t)h->levels[i].bytes;
+        return b;
+    };
+    for (;;) {
+        for (int32_t i = 1; i < top; i++)
+            if (h->levels[i].resident && i % h->keep_stride != 0) level_release(h, h->levels[i]);
+        if (held() <= h->level_budget || h->keep_stride >= (1 << 30)) break;
+        h->keep_stride *= 2;
+    }
+}
+
+// The level's arrays back in memory: rebuilt from the nearest resident level
+// below through the composed cid maps.
+Status ensure_resident(snnmap_hgraph* h, int32_t l)
+{
+    if (h->levels[l].resident) return Status{};
+    int32_t j = l - 1;
+    while (j > 0 && !h->levels[j].resident) j--;
+    cudaStream_t s = h->stream;
+    Arena& ar = h->scratch;
+    const Level& S = h->levels[j];
+    int32_t* c;
+    int64_t* d_V2;
+    SNN_TRY(ar.alloc(&c, S.V));
+    SNN_TRY(ar.alloc(&d_V2, 1));
+    if (S.V > 0)
+        SNN_CUDA(cudaMemcpyAsync(c, S.cid, (size_t)S.V * 4, cudaMemcpyDeviceToDevice, s));
+    for (int32_t m = j + 1; m < l; m++) {
+        SNN_L k_compose<<<grid_for(S.V, 256), 256, 0, s>>>(S.V, c, h->levels[m].cid);
+        SNN_CUDA(cudaGetLastError());
+    }
+    int64_t v2 = h->levels[l].V;
+    SNN_CUDA(cudaMemcpyAsync(d_V2, &v2, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    SNN_CUDA(cudaStreamSynchronize(s));
+    return build_coarse(h, j, c, d_V2, l);
 }
 
 }  // namespace snn

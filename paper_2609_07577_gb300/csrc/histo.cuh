@@ -498,15 +498,23 @@ __device__ __forceinline__ int64_t find_owner(const int64_t* od, int64_t ns, int
     return lo;
 }
 
+// degree, table capacity (twice the key bound, at most twice `limit` when
+// limit > 0) and total work of the split vertices
 template <class Pol>
 __global__ void k_ht_split_deg(Pol pol, const int32_t* __restrict__ slist, int64_t ns, int64_t* deg,
-                               const int64_t* __restrict__ workv, int64_t* total_work)
+                               const int64_t* __restrict__ workv, int64_t* total_work,
+                               int64_t* scap, int64_t limit)
 {
     int64_t w = 0;
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < ns;
          j += (int64_t)gridDim.x * blockDim.x) {
-        deg[j] = pol.ve(slist[j]) - pol.vb(slist[j]);
-        w += workv[slist[j]];
+        int32_t n = slist[j];
+        deg[j] = pol.ve(n) - pol.vb(n);
+        int64_t work = workv[n];
+        w += work;
+        int64_t bound = work < pol.keys ? work : pol.keys;
+        if (limit > 0 && bound > limit) bound = limit;
+        scap[j] = pow2_ceil(2 * (bound > 16 ? bound : 16));
     }
     w = warp_sum(w);
     if ((threadIdx.x & 31) == 0 && w) atomicAdd((unsigned long long*)total_work, (unsigned long long)w);
@@ -578,7 +586,7 @@ __global__ void __launch_bounds__(HT_WARPS * 32)
                      const int64_t* __restrict__ od, int64_t D,
                      const int64_t* __restrict__ item_f0, int64_t nitems,
                      const int64_t* __restrict__ toff, const int64_t* __restrict__ scap,
-                     unsigned char* pool, typename Pol::Acc* gacc, int64_t* status)
+                     unsigned char* pool, typename Pol::Acc* gacc, int32_t* ovf, uint32_t probes)
 {
     using S = typename Pol::S;
     using Acc = typename Pol::Acc;
@@ -598,6 +606,7 @@ __global__ void __launch_bounds__(HT_WARPS * 32)
         int64_t vb = pol.vb(n) + (f0 - od[j]);
         int64_t ve = pol.vb(n) + (f1 - od[j]);
         Table<S> g = carve_table<S>(pool + toff[j] * slot_bytes<S>(), scap[j]);
+        if (probes) g.probes = probes;
         Acc acc;
         bool ok;
         if (scap[j] <= HT_WCAP) {
@@ -609,7 +618,7 @@ __global__ void __launch_bounds__(HT_WARPS * 32)
         } else {
             ok = warp_visit<S>(pol, n, vb, ve, 32, g, acc);
         }
-        if (!ok && lane == 0) atomicOr((int*)status, ST_CAPACITY);
+        if (!ok && lane == 0) ovf[j] = 1;
         Acc wa = Pol::warp_reduce(acc);
         if (lane == 0) wa.atomic_into(&gacc[j]);
     }
@@ -619,7 +628,8 @@ template <class Pol>
 __global__ void __launch_bounds__(1024)
     k_ht_split_scan(Pol pol, const int32_t* __restrict__ slist, int64_t ns,
                     const int64_t* __restrict__ toff, const int64_t* __restrict__ scap,
-                    unsigned char* pool, const typename Pol::Acc* gacc)
+                    unsigned char* pool, const typename Pol::Acc* gacc,
+                    const int32_t* __restrict__ ovf)
 {
     using S = typename Pol::S;
     __shared__ int64_t rs[32];
@@ -628,6 +638,7 @@ __global__ void __launch_bounds__(1024)
     int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int nwarps = blockDim.x >> 5;
     for (int64_t j = blockIdx.x; j < ns; j += gridDim.x) {
+        if (ovf[j]) continue;   // redone with a larger table
         int32_t n = slist[j];
         Table<S> t = carve_table<S>(pool + toff[j] * slot_bytes<S>(), scap[j]);
         typename Pol::Acc tot = gacc[j];
@@ -655,6 +666,14 @@ __global__ void __launch_bounds__(1024)
     }
 }
 
+static __global__ void k_ht_collect_ovf(const int32_t* __restrict__ slist, int64_t ns,
+                                        const int32_t* __restrict__ ovf, int32_t* out, int64_t* cnt)
+{
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < ns;
+         j += (int64_t)gridDim.x * blockDim.x)
+        if (ovf[j]) out[atomicAdd((unsigned long long*)cnt, 1ull)] = slist[j];
+}
+
 template <typename S>
 __global__ void k_ht_pool_clear(unsigned char* pool, const int64_t* __restrict__ toff,
                                 const int64_t* __restrict__ scap, int64_t ns)
@@ -673,9 +692,91 @@ inline Status set_smem(K kernel, size_t bytes)
     return Status{};
 }
 
+constexpr int64_t HT_SPLIT_CAP = 1 << 16;
+
+// Split tier for the vertices slist[0..ns). limit > 0 caps the tables and
+// collects the vertices that overflowed into `again` (count in h_cnt[0]);
+// limit == 0 sizes every table to its exact bound, which cannot overflow.
+template <class Pol>
+Status run_split(const Pol& pol, Arena& ar, cudaStream_t s, const int32_t* sl, int64_t ns,
+                 const int64_t* workv, int64_t limit, int32_t* again, int64_t* nagain,
+                 int64_t* h_cnt)
+{
+    using S = typename Pol::S;
+    int64_t *toff, *deg, *od, *tot, *scap;
+    int32_t* ovf;
+    SNN_TRY(ar.alloc(&toff, ns + 1));
+    SNN_TRY(ar.alloc(&deg, ns));
+    SNN_TRY(ar.alloc(&od, ns + 1));
+    SNN_TRY(ar.alloc(&tot, 4));
+    SNN_TRY(ar.alloc(&scap, ns));
+    SNN_TRY(ar.alloc(&ovf, ns));
+    SNN_CUDA(cudaMemsetAsync(tot, 0, 4 * sizeof(int64_t), s));
+    SNN_CUDA(cudaMemsetAsync(ovf, 0, (size_t)ns * sizeof(int32_t), s));
+    SNN_L k_ht_split_deg<Pol><<<grid_for(ns, 256), 256, 0, s>>>(pol, sl, ns, deg, workv, tot + 2, scap,
+                                                              limit);
+    SNN_CUDA(cudaGetLastError());
+    SNN_TRY(scan_exclusive_i64(scap, toff, ns, tot, ar, s));
+    SNN_TRY(scan_exclusive_i64(deg, od, ns, od + ns, ar, s));
+    SNN_CUDA(cudaMemcpyAsync(h_cnt, tot, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    SNN_CUDA(cudaMemcpyAsync(h_cnt + 1, od + ns, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    SNN_CUDA(cudaMemcpyAsync(h_cnt + 2, tot + 2, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    SNN_CUDA(cudaStreamSynchronize(s));
+    int64_t slots = h_cnt[0], D = h_cnt[1];
+    int64_t item = pow2_ceil(h_cnt[2] / (152 * 64 * 2) + 1);
+    item = item < 1024 ? 1024 : (item > 16384 ? 16384 : item);
+    int64_t *len, *x, *item_f0;
+    int32_t *start, *pos;
+    SNN_TRY(ar.alloc(&len, D));
+    SNN_TRY(ar.alloc(&x, D));
+    SNN_TRY(ar.alloc(&start, D));
+    SNN_TRY(ar.alloc(&pos, D));
+    SNN_TRY(ar.alloc(&item_f0, D));
+    SNN_L k_ht_split_len<Pol><<<grid_for(D, 256), 256, 0, s>>>(pol, sl, ns, od, D, len);
+    SNN_CUDA(cudaGetLastError());
+    SNN_TRY(scan_exclusive_i64(len, x, D, nullptr, ar, s));
+    SNN_L k_ht_split_starts<<<grid_for(D, 256), 256, 0, s>>>(ns, od, D, x, len, start, item);
+    SNN_CUDA(cudaGetLastError());
+    SNN_TRY(scan_exclusive_i32(start, pos, D, (int32_t*)(tot + 1), ar, s));
+    SNN_L k_ht_split_items<<<grid_for(D, 256), 256, 0, s>>>(D, start, pos, item_f0);
+    SNN_CUDA(cudaGetLastError());
+    SNN_CUDA(cudaMemcpyAsync(h_cnt, tot + 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    SNN_CUDA(cudaStreamSynchronize(s));
+    int64_t items = h_cnt[0];
+    unsigned char* pool;
+    typename Pol::Acc* gacc;
+    SNN_TRY(ar.alloc(&pool, slots * (int64_t)slot_bytes<S>()));
+    SNN_TRY(ar.alloc(&gacc, ns));
+    SNN_CUDA(cudaMemsetAsync(gacc, 0, (size_t)ns * sizeof(typename Pol::Acc), s));
+    SNN_L k_ht_pool_clear<S><<<(int)std::min<int64_t>(ns, 152 * 8), 256, 0, s>>>(pool, toff, scap, ns);
+    SNN_CUDA(cudaGetLastError());
+    static bool vattr = false;
+    size_t wsm = (size_t)HT_WARPS * HT_WCAP * slot_bytes<S>();
+    if (!vattr) {
+        SNN_TRY(set_smem(k_ht_split_visit<Pol>, wsm));
+        vattr = true;
+    }
+    SNN_L k_ht_split_visit<Pol><<<(int)std::min<int64_t>(ceil_div(items, HT_WARPS), 152 * 8),
+                                  HT_WARPS * 32, wsm, s>>>(pol, sl, ns, od, D, item_f0, items, toff,
+                                                           scap, pool, gacc, ovf,
+                                                           limit > 0 ? 256u : 0u);
+    SNN_CUDA(cudaGetLastError());
+    SNN_L k_ht_split_scan<Pol><<<(int)std::min<int64_t>(ns, 152 * 4), 1024, 0, s>>>(pol, sl, ns, toff,
+                                                                                    scap, pool, gacc, ovf);
+    SNN_CUDA(cudaGetLastError());
+    if (limit > 0) {
+        SNN_CUDA(cudaMemsetAsync(nagain, 0, sizeof(int64_t), s));
+        SNN_L k_ht_collect_ovf<<<grid_for(ns, 256), 256, 0, s>>>(sl, ns, ovf, again, nagain);
+        SNN_CUDA(cudaGetLastError());
+        SNN_CUDA(cudaMemcpyAsync(h_cnt, nagain, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        SNN_CUDA(cudaStreamSynchronize(s));
+    }
+    return Status{};
+}
+
 // Host driver: work, classification and the warp, block and big-block tiers
 // run without host synchronization; the split tier follows reads of its
-// sizes. d_cnt: >= HT_NTIER device int64; h_cnt: a pinned host int64[>=2];
+// sizes. d_cnt: >= HT_NTIER device int64; h_cnt: a pinned host int64[>=3];
 // status: device word.
 template <class Pol>
 Status run_histogram(const Pol& pol, Arena& ar, cudaStream_t s, int64_t* d_cnt, int64_t* h_cnt,
@@ -718,61 +819,16 @@ Status run_histogram(const Pol& pol, Arena& ar, cudaStream_t s, int64_t* d_cnt, 
     int64_t ns = h_cnt[0];
     if (ns == 0) return Status{};
     const int32_t* sl = lists + (int64_t)HT_TIER_SPLIT * V;
-    int64_t *toff, *deg, *od, *tot;
-    SNN_TRY(ar.alloc(&toff, ns + 1));
-    SNN_TRY(ar.alloc(&deg, ns));
-    SNN_TRY(ar.alloc(&od, ns + 1));
-    SNN_TRY(ar.alloc(&tot, 4));
-    SNN_CUDA(cudaMemsetAsync(tot, 0, 4 * sizeof(int64_t), s));
-    SNN_TRY(scan_exclusive_i64(scap, toff, ns, tot, ar, s));
-    SNN_L k_ht_split_deg<Pol><<<grid_for(ns, 256), 256, 0, s>>>(pol, sl, ns, deg, workv, tot + 2);
-    SNN_CUDA(cudaGetLastError());
-    SNN_TRY(scan_exclusive_i64(deg, od, ns, od + ns, ar, s));
-    SNN_CUDA(cudaMemcpyAsync(h_cnt, tot, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    SNN_CUDA(cudaMemcpyAsync(h_cnt + 1, od + ns, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    SNN_CUDA(cudaMemcpyAsync(h_cnt + 2, tot + 2, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    SNN_CUDA(cudaStreamSynchronize(s));
-    int64_t slots = h_cnt[0], D = h_cnt[1];
-    int64_t item = pow2_ceil(h_cnt[2] / (152 * 64 * 2) + 1);
-    item = item < 1024 ? 1024 : (item > 16384 ? 16384 : item);
-    int64_t *len, *x, *item_f0;
-    int32_t *start, *pos;
-    SNN_TRY(ar.alloc(&len, D));
-    SNN_TRY(ar.alloc(&x, D));
-    SNN_TRY(ar.alloc(&start, D));
-    SNN_TRY(ar.alloc(&pos, D));
-    SNN_TRY(ar.alloc(&item_f0, D));
-    SNN_L k_ht_split_len<Pol><<<grid_for(D, 256), 256, 0, s>>>(pol, sl, ns, od, D, len);
-    SNN_CUDA(cudaGetLastError());
-    SNN_TRY(scan_exclusive_i64(len, x, D, nullptr, ar, s));
-    SNN_L k_ht_split_starts<<<grid_for(D, 256), 256, 0, s>>>(ns, od, D, x, len, start, item);
-    SNN_CUDA(cudaGetLastError());
-    SNN_TRY(scan_exclusive_i32(start, pos, D, (int32_t*)(tot + 1), ar, s));
-    SNN_L k_ht_split_items<<<grid_for(D, 256), 256, 0, s>>>(D, start, pos, item_f0);
-    SNN_CUDA(cudaGetLastError());
-    SNN_CUDA(cudaMemcpyAsync(h_cnt, tot + 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    SNN_CUDA(cudaStreamSynchronize(s));
-    int64_t items = h_cnt[0];
-    unsigned char* pool;
-    typename Pol::Acc* gacc;
-    SNN_TRY(ar.alloc(&pool, slots * (int64_t)slot_bytes<S>()));
-    SNN_TRY(ar.alloc(&gacc, ns));
-    SNN_CUDA(cudaMemsetAsync(gacc, 0, (size_t)ns * sizeof(typename Pol::Acc), s));
-    SNN_L k_ht_pool_clear<S><<<(int)std::min<int64_t>(ns, 152 * 8), 256, 0, s>>>(pool, toff, scap, ns);
-    SNN_CUDA(cudaGetLastError());
-    static bool vattr = false;
-    if (!vattr) {
-        SNN_TRY(set_smem(k_ht_split_visit<Pol>, wsm));
-        vattr = true;
-    }
-    SNN_L k_ht_split_visit<Pol><<<(int)std::min<int64_t>(ceil_div(items, HT_WARPS), 152 * 8),
-                                  HT_WARPS * 32, wsm, s>>>(pol, sl, ns, od, D, item_f0, items, toff,
-                                                           scap, pool, gacc, status);
-    SNN_CUDA(cudaGetLastError());
-    SNN_L k_ht_split_scan<Pol><<<(int)std::min<int64_t>(ns, 152 * 4), 1024, 0, s>>>(pol, sl, ns, toff,
-                                                                                    scap, pool, gacc);
-    SNN_CUDA(cudaGetLastError());
-    return Status{};
+    // first pass with tables capped at 2 * HT_SPLIT_CAP slots; vertices that
+    // overflow them are redone with tables sized to their exact key bound
+    int32_t* again;
+    int64_t* nagain;
+    SNN_TRY(ar.alloc(&again, ns));
+    SNN_TRY(ar.alloc(&nagain, 1));
+    SNN_TRY(run_split(pol, ar, s, sl, ns, workv, HT_SPLIT_CAP, again, nagain, h_cnt));
+    int64_t n2 = h_cnt[0];
+    if (n2 == 0) return Status{};
+    return run_split(pol, ar, s, again, n2, workv, 0, nullptr, nullptr, h_cnt);
 }
 
 }  // namespace snn

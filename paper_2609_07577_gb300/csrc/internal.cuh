@@ -47,6 +47,8 @@ struct snnmap_hgraph {
     int32_t* cov = nullptr;
     int32_t* match = nullptr;
     int32_t cap_v = 0;           // capacity of the four arrays above
+    int64_t level_budget = 0;    // bytes of intermediate levels kept resident
+    int32_t keep_stride = 1;     // intermediate levels kept: multiples of this
     bool have_matching = false;
     int32_t last_pairs = 0;
     bool wide = false;           // some neighbour score may reach 2^32
@@ -85,6 +87,8 @@ Status zero_scalars(snnmap_hgraph* h);
 // level memory
 Status level_alloc(snnmap_hgraph* h, Level& L, LevelExtra& X, int32_t V, int32_t E, int64_t P);
 void level_free(snnmap_hgraph* h, Level& L);
+// frees a level's arrays, keeping its sizes and cid map
+void level_release(snnmap_hgraph* h, Level& L);
 
 // S0: level 0 from the caller's arrays
 Status build_level0(snnmap_hgraph* h, int32_t V, int32_t E, const int64_t* d_off,
@@ -96,6 +100,13 @@ Status build_incidence(snnmap_hgraph* h, Level& L);
 Status coarsen_level(snnmap_hgraph* h, int32_t* n_cand, int32_t* n_pairs);
 // S3: next level from h->match
 Status contract_level(snnmap_hgraph* h);
+// materializes levels[dst] from resident levels[src] through map (V(src) ids)
+Status build_coarse(snnmap_hgraph* h, int32_t src, const int32_t* map, const int64_t* d_V2,
+                    int32_t dst);
+// rebuilds a released level from the nearest resident level below it
+Status ensure_resident(snnmap_hgraph* h, int32_t level);
+// releases intermediate levels while their memory exceeds the budget
+void thin_levels(snnmap_hgraph* h);
 // S5
 Status project(snnmap_hgraph* h, int32_t level, const int32_t* rho_coarse, int32_t* rho_fine);
 // S6-S12 on one level; rho in place

@@ -1,0 +1,128 @@
+"""Full-size checks on the 1,048,576-neuron conv workload, in the launch
+configuration bench.py times (device-resident inputs, snnmap_partition).
+
+The oracle cannot run whole passes at this size, so it checks a random
+sample of level-0 candidates one vertex at a time, and everything else is
+checked through properties that hold at any size: the matching pairs
+vertices along candidate arcs and never twice, contraction conserves
+neurons, inbound pins and axons, the final partition respects Omega, Phi and
+Delta, its Conn recomputed independently equals the reported cost, and the
+host-buffer entry point returns the same partition.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import snngen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def big():
+    import __graft_entry__ as g
+    g.build()
+    hg = snngen.cfg2()
+    return hg
+
+
+def conn_np(hg, rho):
+    E = hg.E
+    hid = np.repeat(np.arange(E, dtype=np.int64), np.diff(hg.off))
+    K = int(rho.max()) + 1
+    key = np.unique(hid * K + rho[hg.pins].astype(np.int64))
+    lam = np.bincount(key // K, minlength=E)
+    return int((hg.w.astype(np.int64) * (lam - 1)).sum())
+
+
+def test_level0_candidates_sampled(big):
+    from paper_2609_07577_gb300 import HGraph
+    hg = big
+    prm = oracle.params_of(hg)
+    G = HGraph.from_hypergraph(hg)
+    try:
+        nc, npairs = G.coarsen_level()
+        cand, cs, cov, match = G.last_matching()
+    finally:
+        G.close()
+    L = oracle.Level.from_hypergraph(hg, prm)
+    rng = np.random.default_rng(7)
+    sample = np.concatenate([rng.choice(hg.V, 1500, replace=False), [0, hg.V - 1]])
+    for n in sample:
+        assert (cand[n], cs[n], cov[n]) == L.cand_one(int(n), prm), n
+    assert nc == int((cand >= 0).sum())
+    # matching: symmetric, along candidate arcs, roots matched
+    idx = np.nonzero(match >= 0)[0]
+    assert (match[match[idx]] == idx).all()
+    assert ((cand[idx] == match[idx]) | (cand[match[idx]] == idx)).all()
+    has = cand >= 0
+    roots = has & (cand[np.where(has, cand, 0)] == np.arange(hg.V))
+    assert (match[roots] == cand[roots]).all()
+    assert npairs == int((match > np.arange(hg.V)).sum())
+
+
+def test_full_pass_properties(big):
+    from paper_2609_07577_gb300 import HGraph, params_for, snnmap_partition_host
+    hg = big
+    G = HGraph.from_hypergraph(hg)
+    try:
+        rho_t, cost, st = G.partition()
+        rho = rho_t.cpu().numpy()
+        levels = G.level_logs()
+        rounds = G.round_logs()
+        a0 = G.level_arrays(0)
+    finally:
+        G.close()
+    assert cost == conn_np(hg, rho)
+    assert st["cost_initial"] - sum(r["gain"] for r in rounds) == cost
+    assert all(r["gain"] > 0 for r in rounds if r["istar"] > 0)
+    K = st["n_parts"]
+    assert rho.min() >= 0 and rho.max() < K
+    assert (np.bincount(rho, minlength=K) <= hg.omega).all()
+    assert (np.bincount(rho, weights=a0["inpins"], minlength=K) <= hg.phi).all()
+    isdst = np.ones(hg.P, bool)
+    isdst[hg.off[:-1]] = False
+    hid = np.repeat(np.arange(hg.E, dtype=np.int64), np.diff(hg.off))
+    key = np.unique(rho[hg.pins[isdst]].astype(np.int64) * hg.E + hid[isdst])
+    assert (np.bincount(key // hg.E, minlength=K) <= hg.delta).all()
+    # coarsening shrinks the vertex count at every contraction
+    Vs = [g["V"] for g in levels]
+    assert all(b < a for a, b in zip(Vs, Vs[1:]))
+    # the host-buffer entry point gives the same partition
+    h_rho = np.empty(hg.V, np.int32)
+    c2, _ = snnmap_partition_host(params_for(hg.omega, hg.delta, hg.phi), hg.V, hg.E,
+                                  np.ascontiguousarray(hg.off), np.ascontiguousarray(hg.pins),
+                                  np.ascontiguousarray(hg.w), h_rho)
+    assert c2 == cost and np.array_equal(h_rho, rho)
+
+
+def test_contraction_conserves(big):
+    from paper_2609_07577_gb300 import HGraph
+    hg = big
+    G = HGraph.from_hypergraph(hg)
+    try:
+        a0 = G.level_arrays(0)
+        for _ in range(3):
+            nc, npairs = G.coarsen_level()
+            if npairs == 0:
+                break
+            G.contract()
+        a = G.level_arrays(G.num_levels() - 1)
+    finally:
+        G.close()
+    assert int(a["size"].sum()) == hg.V
+    assert int(a["inpins"].sum()) == int(a0["inpins"].sum())
+    assert int(a["k"].sum()) + int(a["in_internal"].sum()) == a0["E"]
+    # in_count equals its recomputation from the coarse hyperedges
+    inc = a["in_internal"].astype(np.int64).copy()
+    lens = np.diff(a["off"])
+    hid = np.repeat(np.arange(a["E"]), lens)
+    isdst = np.ones(a["P"], bool)
+    isdst[a["off"][:-1]] = False
+    np.add.at(inc, a["pins"][isdst], a["k"][hid[isdst]])
+    sd = a["selfdst"].astype(bool)
+    np.add.at(inc, a["pins"][a["off"][:-1]][sd], a["k"][sd])
+    assert (inc == a["in_count"]).all()
+    assert (a["size"] <= hg.omega).all() and (a["inpins"] <= hg.phi).all()
+    assert (a["in_count"] <= hg.delta).all()

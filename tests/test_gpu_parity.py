@@ -31,13 +31,15 @@ def test_coarsening_lockstep(name):
     assert n >= 1
 
 
-def _partition_both(hg, **kw):
+def _partition_both(hg, budget=None, **kw):
     from paper_2609_07577_gb300 import partition
     prm = oracle.params_of(hg, **kw)
     rho_o, cost_o, st_o, lv_o, rl_o = oracle.partition(hg, prm)
     from paper_2609_07577_gb300 import HGraph, params_for
     G = HGraph.from_hypergraph(hg, params=params_for(hg.omega, hg.delta, hg.phi, **kw))
     try:
+        if budget is not None:
+            G.set_level_budget(budget)
         rho, cost, st = G.partition()
         rl = G.round_logs()
         lv = G.level_logs()
@@ -46,10 +48,15 @@ def _partition_both(hg, **kw):
     return (rho.cpu().numpy(), cost, st, lv, rl), (rho_o, cost_o, st_o, lv_o, rl_o)
 
 
-@pytest.mark.parametrize("name", ["cfg1s", "cfg1", "cfg2s", "cfg3s"])
-def test_partition_parity(name):
+@pytest.mark.parametrize("name,budget", [("cfg1s", None), ("cfg1", None), ("cfg2s", None),
+                                         ("cfg3s", None), ("cfg1", 1), ("cfg3s", 1),
+                                         ("cfg2s", 4 << 20)])
+def test_partition_parity(name, budget):
+    """budget=1 releases every intermediate level during coarsening, so
+    uncoarsening rebuilds each one from level 0 through composed cid maps;
+    4 MiB keeps a stride of them."""
     hg = snngen.by_name(name)
-    (rho, cost, st, lv, rl), (rho_o, cost_o, st_o, lv_o, rl_o) = _partition_both(hg)
+    (rho, cost, st, lv, rl), (rho_o, cost_o, st_o, lv_o, rl_o) = _partition_both(hg, budget)
     assert cost == cost_o
     assert np.array_equal(rho, rho_o)
     for k in ("levels", "n_parts", "nonempty_parts", "rounds", "moves", "cost_initial", "cost"):
@@ -146,3 +153,31 @@ def test_connectivity_entry_point():
             assert e.value.code == N.ERR_INVALID
         finally:
             G.close()
+
+
+def test_rebuilt_levels_equal_oracle_levels():
+    """Levels released under a tiny memory budget and rebuilt on demand equal
+    the oracle's levels (arrays compared canonically)."""
+    from gpu_helpers import assert_level_equal
+    from paper_2609_07577_gb300 import HGraph
+    hg = snngen.by_name("cfg3s")
+    prm = oracle.params_of(hg)
+    G = HGraph.from_hypergraph(hg)
+    try:
+        G.set_level_budget(1)
+        L = oracle.Level.from_hypergraph(hg, prm)
+        olevels = [L]
+        for _ in range(12):
+            nc, npairs = G.coarsen_level()
+            if npairs == 0:
+                break
+            G.contract()
+            cand, cs, cov = olevels[-1].affinity(prm)
+            m, _ = oracle.match(cand, cs)
+            C, _ = olevels[-1].contract(m, cand, cov)
+            olevels.append(C)
+        assert len(olevels) > 5
+        for lev in (3, 1, len(olevels) - 2, 2):
+            assert_level_equal(G.level_arrays(lev), olevels[lev].arrays(), f"rebuilt level {lev}")
+    finally:
+        G.close()
