@@ -255,6 +255,11 @@ int snnmap_set_level_budget(snnmap_hgraph* h, int64_t bytes);
 /* Bytes of device memory the handle currently holds. */
 int snnmap_device_bytes(const snnmap_hgraph* h, int64_t* bytes);
 
+/* Largest figure snnmap_device_bytes would have reported at the library's
+ * checkpoints (after each contraction, level rebuild and refinement) since
+ * the handle was built. */
+int snnmap_peak_bytes(const snnmap_hgraph* h, int64_t* bytes);
+
 void snnmap_free(snnmap_hgraph* h);
 
 /*
@@ -285,6 +290,89 @@ void snnmap_free(snnmap_hgraph* h);
 int snnmap_connectivity_noalloc(int32_t n_vertices, int32_t n_hedges, const int64_t* d_offsets,
                                 const int32_t* d_pins, const int32_t* d_w, const int32_t* d_rho,
                                 int32_t n_parts, int64_t* d_cost_out, void* stream);
+
+/*
+ * Batched and served forms. The paper maps one network at a time; these calls
+ * run many independent mapping jobs (each the whole pass of snnmap_partition,
+ * with bit-identical results) on one GPU at once. A server owns `slots`
+ * worker threads, each with its own CUDA stream, so the kernels of different
+ * jobs overlap on the device. Jobs start in submission order (FIFO); the job
+ * at the head of the queue starts when a slot is free and its predicted
+ * footprint (snnmap_job_footprint) fits in mem_budget beside the footprints
+ * already reserved, or at once when nothing is reserved. A footprint stays
+ * reserved while the job runs and, for jobs with keep_hierarchy set, until
+ * snnmap_serve_release. Each job keeps at most about its level-0 size of
+ * intermediate levels in memory (snnmap_set_level_budget), which bounds its
+ * footprint; this changes no result.
+ */
+typedef struct snnmap_server snnmap_server;
+
+typedef struct {
+    /* inputs: the layout of snnmap_build_hgraph */
+    snnmap_params params;
+    int32_t n_vertices, n_hedges;
+    const int64_t* offsets;   /* [n_hedges + 1] */
+    const int32_t* pins;      /* [offsets[n_hedges]]; pin 0 of a hyperedge is its source */
+    const int32_t* w;         /* [n_hedges] */
+    int32_t* rho_out;         /* [n_vertices] result */
+    int32_t on_host;          /* 1: the four arrays are host memory (pinned memory lets
+                                 copies overlap other jobs); 0: device memory */
+    int32_t keep_hierarchy;   /* 1: the job's handle (level hierarchy) stays on the device
+                                 until snnmap_serve_release; see snnmap_serve_hgraph */
+    /* outputs, written before the job counts as done */
+    int32_t status;           /* SNNMAP_OK or the job's error code */
+    int32_t slot;             /* worker slot that ran the job */
+    int64_t cost;             /* Conn of rho_out */
+    snnmap_stats stats;
+    int64_t footprint;        /* predicted device bytes reserved for the job */
+    int64_t peak_bytes;       /* measured: handle peak plus the job's input copies */
+    double t_submit_ms, t_start_ms, t_end_ms;  /* host clock, ms since the server's creation */
+    char error[128];          /* snnmap_last_error text of a failed job */
+} snnmap_job;
+
+typedef struct {
+    int32_t slots;            /* jobs in flight at once (one stream each); 0: 8 */
+    int32_t dry_run_us;       /* > 0: host-only run for testing the scheduler: no GPU is
+                                 touched, each job holds its slot this many microseconds
+                                 per million pins (at least 1 ms) and ends with status OK */
+    int64_t mem_budget;       /* bytes of footprint admitted at once; 0: 80% of the device
+                                 memory free at creation (dry run: 2^36) */
+} snnmap_serve_opts;
+
+/* Predicted peak device bytes of one job with the given level-0 sizes
+ * (host-only arithmetic; no GPU needed). on_host adds the job's input copies.
+ * Errors: SNNMAP_ERR_INVALID for negative sizes or a NULL output. */
+int snnmap_job_footprint(int32_t n_vertices, int32_t n_hedges, int64_t n_pins, int32_t on_host,
+                         int64_t* bytes);
+
+int snnmap_serve_create(const snnmap_serve_opts* opts, snnmap_server** out);
+/* Queues a job; the job struct and its buffers must stay valid (and
+ * unmodified) until the job is done. *ticket identifies it (>= 1). Returns
+ * at once. Errors: SNNMAP_ERR_INVALID (NULL or negative sizes),
+ * SNNMAP_ERR_STATE (server shutting down). Input errors of the job itself are
+ * reported in job->status. */
+int snnmap_serve_submit(snnmap_server* s, snnmap_job* job, int64_t* ticket);
+/* Blocks until the job is done or timeout_ms passes (< 0: no limit); *done
+ * (may be NULL) receives 1 if it is done. */
+int snnmap_serve_wait(snnmap_server* s, int64_t ticket, double timeout_ms, int32_t* done);
+/* The resident hierarchy of a done job submitted with keep_hierarchy (owned
+ * by the server; valid until snnmap_serve_release). SNNMAP_ERR_STATE if the
+ * job is not done, failed, or kept nothing. */
+int snnmap_serve_hgraph(snnmap_server* s, int64_t ticket, snnmap_hgraph** out);
+/* Frees a done job's hierarchy and footprint and forgets the ticket. */
+int snnmap_serve_release(snnmap_server* s, int64_t ticket);
+/* Jobs waiting, jobs running, and bytes of footprint reserved now; any
+ * output may be NULL. */
+int snnmap_serve_info(snnmap_server* s, int32_t* queued, int32_t* running, int64_t* reserved);
+/* Finishes running jobs, marks queued ones SNNMAP_ERR_STATE, frees every kept
+ * hierarchy and the server. */
+int snnmap_serve_destroy(snnmap_server* s);
+
+/* Runs n_jobs jobs to completion on one server (largest pin count first) and
+ * returns SNNMAP_OK when every job succeeded, else the first failed job's
+ * status; every job's own status, cost, stats and times are filled in.
+ * keep_hierarchy is ignored. */
+int snnmap_batch_partition(snnmap_job* jobs, int32_t n_jobs, const snnmap_serve_opts* opts);
 
 /* Kernels launched by the library in this process so far. */
 int64_t snnmap_launch_count(void);

@@ -43,6 +43,21 @@ class StageTime(C.Structure):
     _fields_ = [("name", C.c_char_p), ("calls", C.c_int64), ("ms", C.c_double)]
 
 
+class Job(C.Structure):
+    """snnmap_job: one independent mapping job of the batched/served forms."""
+    _fields_ = [("params", Params), ("n_vertices", C.c_int32), ("n_hedges", C.c_int32),
+                ("offsets", C.c_void_p), ("pins", C.c_void_p), ("w", C.c_void_p),
+                ("rho_out", C.c_void_p), ("on_host", C.c_int32), ("keep_hierarchy", C.c_int32),
+                ("status", C.c_int32), ("slot", C.c_int32), ("cost", C.c_int64),
+                ("stats", Stats), ("footprint", C.c_int64), ("peak_bytes", C.c_int64),
+                ("t_submit_ms", C.c_double), ("t_start_ms", C.c_double),
+                ("t_end_ms", C.c_double), ("error", C.c_char * 128)]
+
+
+class ServeOpts(C.Structure):
+    _fields_ = [("slots", C.c_int32), ("dry_run_us", C.c_int32), ("mem_budget", C.c_int64)]
+
+
 class SnnmapError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"snnmap error {code}: {msg}")
@@ -79,6 +94,16 @@ _SIGS = {
     "snnmap_launch_count": (_i64, []),
     "snnmap_set_level_budget": (C.c_int, [_vp, _i64]),
     "snnmap_connectivity_noalloc": (C.c_int, [_i32, _i32, _vp, _vp, _vp, _vp, _i32, _vp, _vp]),
+    "snnmap_peak_bytes": (C.c_int, [_vp, C.POINTER(_i64)]),
+    "snnmap_job_footprint": (C.c_int, [_i32, _i32, _i64, _i32, C.POINTER(_i64)]),
+    "snnmap_serve_create": (C.c_int, [C.POINTER(ServeOpts), C.POINTER(_vp)]),
+    "snnmap_serve_submit": (C.c_int, [_vp, C.POINTER(Job), C.POINTER(_i64)]),
+    "snnmap_serve_wait": (C.c_int, [_vp, _i64, C.c_double, C.POINTER(_i32)]),
+    "snnmap_serve_hgraph": (C.c_int, [_vp, _i64, C.POINTER(_vp)]),
+    "snnmap_serve_release": (C.c_int, [_vp, _i64]),
+    "snnmap_serve_info": (C.c_int, [_vp, C.POINTER(_i32), C.POINTER(_i32), C.POINTER(_i64)]),
+    "snnmap_serve_destroy": (C.c_int, [_vp]),
+    "snnmap_batch_partition": (C.c_int, [C.POINTER(Job), _i32, C.POINTER(ServeOpts)]),
     "snnmap_free": (None, [_vp]),
     "snnmap_last_error": (C.c_char_p, []),
 }
@@ -262,6 +287,66 @@ def snnmap_connectivity_noalloc(n_vertices, n_hedges, d_offsets, d_pins, d_w, d_
 
 def snnmap_set_level_budget(h, nbytes):
     check(lib().snnmap_set_level_budget(h, int(nbytes)))
+
+
+def snnmap_peak_bytes(h):
+    b = C.c_int64()
+    check(lib().snnmap_peak_bytes(h, C.byref(b)))
+    return b.value
+
+
+def snnmap_job_footprint(n_vertices, n_hedges, n_pins, on_host=False):
+    b = C.c_int64()
+    check(lib().snnmap_job_footprint(int(n_vertices), int(n_hedges), int(n_pins),
+                                     1 if on_host else 0, C.byref(b)))
+    return b.value
+
+
+def snnmap_serve_create(slots=0, mem_budget=0, dry_run_us=0):
+    o = ServeOpts(int(slots), int(dry_run_us), int(mem_budget))
+    s = C.c_void_p()
+    check(lib().snnmap_serve_create(C.byref(o), C.byref(s)))
+    return s
+
+
+def snnmap_serve_submit(s, job):
+    """job: a Job struct the caller keeps alive (with its buffers) until done."""
+    t = C.c_int64()
+    check(lib().snnmap_serve_submit(s, C.byref(job), C.byref(t)))
+    return t.value
+
+
+def snnmap_serve_wait(s, ticket, timeout_ms=-1.0):
+    d = C.c_int32()
+    check(lib().snnmap_serve_wait(s, int(ticket), float(timeout_ms), C.byref(d)))
+    return bool(d.value)
+
+
+def snnmap_serve_hgraph(s, ticket):
+    h = C.c_void_p()
+    check(lib().snnmap_serve_hgraph(s, int(ticket), C.byref(h)))
+    return h
+
+
+def snnmap_serve_release(s, ticket):
+    check(lib().snnmap_serve_release(s, int(ticket)))
+
+
+def snnmap_serve_info(s):
+    q, r, b = C.c_int32(), C.c_int32(), C.c_int64()
+    check(lib().snnmap_serve_info(s, C.byref(q), C.byref(r), C.byref(b)))
+    return q.value, r.value, b.value
+
+
+def snnmap_serve_destroy(s):
+    check(lib().snnmap_serve_destroy(s))
+
+
+def snnmap_batch_partition(jobs, slots=0, mem_budget=0, dry_run_us=0):
+    """jobs: a ctypes array of Job. Returns the library's return code (job
+    statuses are in the structs)."""
+    o = ServeOpts(int(slots), int(dry_run_us), int(mem_budget))
+    return lib().snnmap_batch_partition(jobs, len(jobs), C.byref(o))
 
 
 def snnmap_launch_count():

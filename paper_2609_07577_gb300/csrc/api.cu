@@ -295,6 +295,7 @@ int snnmap_partition(snnmap_hgraph* h, void* stream, int32_t* d_rho_out, int64_t
                                             h->extra.back().n_block, h->extra.back().n_global});
         if (nc == 0 || np == 0) break;
         API_TRY(snn::contract_level(h));
+        snn::note_bytes(h);
         snn::thin_levels(h);
     }
     int32_t nl = (int32_t)h->levels.size();
@@ -319,6 +320,7 @@ int snnmap_partition(snnmap_hgraph* h, void* stream, int32_t* d_rho_out, int64_t
                 snn::level_release(h, h->levels[l + 1]);
             s2 = snn::ensure_resident(h, l);
             if (!s2.ok()) break;
+            snn::note_bytes(h);
             s2 = snn::project(h, l, cur, oth);
             if (!s2.ok()) break;
             std::swap(cur, oth);
@@ -326,6 +328,7 @@ int snnmap_partition(snnmap_hgraph* h, void* stream, int32_t* d_rho_out, int64_t
         int64_t c0 = 0;
         s2 = snn::refine_level(h, l, K, cur, &cost, l == nl - 1 ? &c0 : nullptr);
         if (l == nl - 1) st.cost_initial = c0;
+        snn::note_bytes(h);
     }
     cudaFreeAsync(tmp, h->stream);
     if (!s2.ok()) return fail(s2);
@@ -507,9 +510,15 @@ int snnmap_stage_times(snnmap_hgraph* h, snnmap_stage_time* out, int32_t cap, in
 int snnmap_device_bytes(const snnmap_hgraph* h, int64_t* bytes)
 {
     if (!h || !bytes) return fail(SNNMAP_ERR_INVALID, "NULL argument");
-    int64_t t = (int64_t)h->scratch.held() + (int64_t)h->cap_v * 20;
-    for (auto& L : h->levels) t += (int64_t)L.bytes + 4 * (int64_t)L.V;
-    *bytes = t;
+    *bytes = snn::held_bytes(h);
+    return SNNMAP_OK;
+}
+
+int snnmap_peak_bytes(const snnmap_hgraph* h, int64_t* bytes)
+{
+    if (!h || !bytes) return fail(SNNMAP_ERR_INVALID, "NULL argument");
+    snn::note_bytes(const_cast<snnmap_hgraph*>(h));
+    *bytes = h->peak_bytes;
     return SNNMAP_OK;
 }
 

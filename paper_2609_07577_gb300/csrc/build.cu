@@ -112,6 +112,19 @@ Status level_alloc(snnmap_hgraph* h, Level& L, LevelExtra& X, int32_t V, int32_t
     return Status{};
 }
 
+int64_t held_bytes(const snnmap_hgraph* h)
+{
+    int64_t t = (int64_t)h->scratch.held() + (int64_t)h->cap_v * 20;
+    for (auto& L : h->levels) t += (int64_t)L.bytes + 4 * (int64_t)L.V;
+    return t;
+}
+
+void note_bytes(snnmap_hgraph* h)
+{
+    int64_t b = held_bytes(h);
+    if (b > h->peak_bytes) h->peak_bytes = b;
+}
+
 void level_free(snnmap_hgraph* h, Level& L)
 {
     if (L.block) cudaFreeAsync(L.block, h->stream);

@@ -750,12 +750,8 @@ Status run_split(const Pol& pol, Arena& ar, cudaStream_t s, const int32_t* sl, i
     SNN_CUDA(cudaMemsetAsync(gacc, 0, (size_t)ns * sizeof(typename Pol::Acc), s));
     SNN_L k_ht_pool_clear<S><<<(int)std::min<int64_t>(ns, 152 * 8), 256, 0, s>>>(pool, toff, scap, ns);
     SNN_CUDA(cudaGetLastError());
-    static bool vattr = false;
     size_t wsm = (size_t)HT_WARPS * HT_WCAP * slot_bytes<S>();
-    if (!vattr) {
-        SNN_TRY(set_smem(k_ht_split_visit<Pol>, wsm));
-        vattr = true;
-    }
+    SNN_TRY(set_smem(k_ht_split_visit<Pol>, wsm));
     SNN_L k_ht_split_visit<Pol><<<(int)std::min<int64_t>(ceil_div(items, HT_WARPS), 152 * 8),
                                   HT_WARPS * 32, wsm, s>>>(pol, sl, ns, od, D, item_f0, items, toff,
                                                            scap, pool, gacc, ovf,
@@ -795,18 +791,16 @@ Status run_histogram(const Pol& pol, Arena& ar, cudaStream_t s, int64_t* d_cnt, 
     SNN_CUDA(cudaGetLastError());
     SNN_L k_ht_classify<Pol><<<grid_for(V, 256), 256, 0, s>>>(pol, workv, lists, d_cnt, scap);
     SNN_CUDA(cudaGetLastError());
-    static bool attrs = false;
     size_t wsm = (size_t)HT_WARPS * HT_WCAP * slot_bytes<S>();
     size_t bsm = (size_t)HT_BCAP * slot_bytes<S>();
     size_t gsm = (size_t)big_cap<S>() * slot_bytes<S>();
     auto kb = k_ht_block<Pol, HT_BTHREADS, HT_BCAP, HT_TIER_BLOCK, HT_TIER_BIG>;
     auto kg = k_ht_block<Pol, HT_GTHREADS, big_cap<S>(), HT_TIER_BIG, HT_TIER_SPLIT>;
-    if (!attrs) {
-        SNN_TRY(set_smem(k_ht_warp<Pol>, wsm));
-        SNN_TRY(set_smem(kb, bsm));
-        SNN_TRY(set_smem(kg, gsm));
-        attrs = true;
-    }
+    // set on every call: the attribute is per device, and handles on other
+    // host threads may reach this point concurrently
+    SNN_TRY(set_smem(k_ht_warp<Pol>, wsm));
+    SNN_TRY(set_smem(kb, bsm));
+    SNN_TRY(set_smem(kg, gsm));
     SNN_L k_ht_warp<Pol><<<(int)std::min<int64_t>(ceil_div(V, HT_WARPS), 152 * 8), HT_WARPS * 32, wsm,
                            s>>>(pol, lists, d_cnt, workv, scap);
     SNN_CUDA(cudaGetLastError());

@@ -49,6 +49,7 @@ struct snnmap_hgraph {
     int32_t cap_v = 0;           // capacity of the four arrays above
     int64_t level_budget = 0;    // bytes of intermediate levels kept resident
     int32_t keep_stride = 1;     // intermediate levels kept: multiples of this
+    int64_t peak_bytes = 0;      // largest held_bytes() seen at a checkpoint
     bool have_matching = false;
     int32_t last_pairs = 0;
     bool wide = false;           // some neighbour score may reach 2^32
@@ -80,9 +81,17 @@ struct ProfScope {
 void prof_collect(snnmap_hgraph* h);
 void prof_release(snnmap_hgraph* h);
 
+// text of snnmap_last_error for the calling thread (api.cu)
+void set_last_error(const std::string& msg);
+
 // scalars: copy the SC_COUNT slots device->host and synchronize the stream
 Status read_scalars(snnmap_hgraph* h);
 Status zero_scalars(snnmap_hgraph* h);
+
+// device bytes the handle holds now (levels, cid maps, scratch, per-vertex
+// arrays), and the running maximum of that figure
+int64_t held_bytes(const snnmap_hgraph* h);
+void note_bytes(snnmap_hgraph* h);
 
 // level memory
 Status level_alloc(snnmap_hgraph* h, Level& L, LevelExtra& X, int32_t V, int32_t E, int64_t P);

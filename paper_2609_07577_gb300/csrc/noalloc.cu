@@ -136,10 +136,6 @@ __global__ void k_na_store(const unsigned long long* acc, int64_t* out) { *out =
 
 }  // namespace
 
-namespace snn {
-void set_last_error(const std::string& msg);   // api.cu: text of snnmap_last_error
-}
-
 extern "C" {
 
 int snnmap_connectivity_noalloc(int32_t n_vertices, int32_t n_hedges, const int64_t* d_offsets,

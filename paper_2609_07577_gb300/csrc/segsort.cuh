@@ -215,13 +215,9 @@ Status seg_run(const Job& job, const SegBuckets& b, int32_t E, Arena& ar, cudaSt
     SNN_L k_seg_b1<Job><<<seg_grid_small(E), 256, 0, s>>>(job, b.list, b.meta);
     SNN_CUDA(cudaGetLastError());
     {
-        static bool attr_set = false;
         size_t smem = SEG_B2_CAP * sizeof(uint32_t);
-        if (!attr_set) {
-            SNN_CUDA(cudaFuncSetAttribute(k_seg_big<Job>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem));
-            attr_set = true;
-        }
+        SNN_CUDA(cudaFuncSetAttribute(k_seg_big<Job>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
         SNN_L k_seg_big<Job><<<seg_grid_big(E), SEG_B2_THREADS, smem, s>>>(job, b.list, b.meta,
                                                                             SEG_BB2, nullptr, 0);
         SNN_CUDA(cudaGetLastError());

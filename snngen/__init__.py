@@ -189,7 +189,7 @@ def powerlaw(V=1 << 23, block=65536, fmin=8, fmax=16384, alpha=2.1, local=0.7,
 
     Fan-out is the integer part of an inverse-CDF draw of a Pareto law with
     survival proportional to x^-alpha, truncated to [fmin, fmax]. Each pin is
-    drawn from the source's aligned ``block``-ID block with probability
+    drawn from the source's aligned ``block``-ID block (cut at V) with probability
     ``local``, else uniformly over all V neurons. Weight = max(1,
     round(lognormal(mu=1, sigma=1))).
     """
@@ -203,7 +203,12 @@ def powerlaw(V=1 << 23, block=65536, fmin=8, fmax=16384, alpha=2.1, local=0.7,
     total = int(fan.sum())
     hid = np.repeat(np.arange(V, dtype=np.int64), fan)
     is_local = rng.random(total) < local
-    loc = (hid // block) * block + rng.integers(0, block, size=total)
+    # the last block is cut at V when V is not a multiple of block; a draw r
+    # in [0, block) is scaled onto it (unchanged for full blocks)
+    base = (hid // block) * block
+    width = np.minimum(block, V - base)
+    loc = base + (rng.integers(0, block, size=total) * width) // block
+    del base, width
     uni = rng.integers(0, V, size=total)
     cand = np.where(is_local, loc, uni)
     del loc, uni, is_local

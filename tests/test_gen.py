@@ -71,3 +71,13 @@ def test_batch_and_serve_descriptors():
     assert all(x < y for x, y in zip(t, t[1:]))
     _layout_ok(snngen.serve_job({"n": 5000, "kind": 0, "seed": 1}))
     _layout_ok(snngen.serve_job({"n": 5000, "kind": 1, "seed": 2}))
+
+
+def test_powerlaw_pins_in_range_when_v_is_not_a_block_multiple():
+    hg = snngen.powerlaw(10_000, 4096, 8, 512, 2.1, 0.7, seed=9, omega=256, delta=1024,
+                         phi=4096)
+    assert hg.pins.min() >= 0 and hg.pins.max() < hg.V
+    # the cut last block still receives its local pins
+    src = np.repeat(hg.pins[hg.off[:-1]], np.diff(hg.off))
+    last = src >= 8192
+    assert (hg.pins[last] >= 8192).mean() > 0.5
