@@ -51,7 +51,14 @@ CONFIGS = {
     # quarter-width conv workload (profiling captures: inputs still larger than L2)
     "cfg2q": ("Conv-like layered SNN, 8 layers of 64x64x8 (262,144 neurons)",
               lambda: snngen.by_name("cfg2q")),
+    "cfg4": ("Batched: independent jobs of 10k-500k neurons (log-uniform), layered and "
+             "power-law generators alternating, seed = job index, Omega from {256,1024,4096}",
+             None),
+    "cfg5": ("Served: Poisson arrivals (200 jobs/s) of jobs of 10k-2M neurons (log-uniform), "
+             "conv-like or power-law, admitted by HBM footprint", None),
 }
+BATCH_METRIC = "batched jobs/s (1 GB300)"
+SERVE_METRIC = "served jobs/s with p50/p99 latency (1 GB300)"
 
 
 def parse():
@@ -65,6 +72,11 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-clocks", action="store_true",
                     help="do not sample nvidia-smi (for runs under a profiler)")
+    ap.add_argument("--jobs", type=int, default=0,
+                    help="cfg4/cfg5: jobs in the sample (default 32 / 48)")
+    ap.add_argument("--slots", type=int, default=8, help="cfg4/cfg5: concurrent jobs")
+    ap.add_argument("--max-neurons", type=int, default=0,
+                    help="cfg5: skip stream jobs larger than this (0: keep all)")
     return ap.parse_args()
 
 
@@ -362,10 +374,210 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def _dist_setup():
+    import torch
+    import torch.distributed as dist
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    return rank, world, local
+
+
+def _max_over_ranks(x, world, local):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], device=torch.device("cuda", local), dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _barrier(world, local):
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize(torch.device("cuda", local))
+
+
+def run_batch(args):
+    """cfg4: every rank partitions its share of the jobs (job j on rank
+    j % N, no collective) in one batched call; timed against the same jobs
+    run one at a time (one slot)."""
+    import torch
+    rank, world, local = _dist_setup()
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2609_07577_gb300 as P
+    from paper_2609_07577_gb300 import JobBuffers
+    n_jobs = args.jobs or 32
+    mine = [j for j in range(n_jobs) if j % world == rank]
+    t0 = time.perf_counter()
+    hgs = [snngen.batch_jobs_one(j) for j in mine]
+    gen_s = time.perf_counter() - t0
+    dev_bufs = [JobBuffers(hg, on_host=False) for hg in hgs]
+    host_bufs = [JobBuffers(hg, on_host=True) for hg in hgs]
+
+    def batch(bufs, slots):
+        arr = (P.Job * len(bufs))(*[b.job for b in bufs])
+        rc = P.snnmap_batch_partition(arr, slots)
+        assert rc == 0, (rc, [arr[i].error for i in range(len(bufs)) if arr[i].status])
+        return [(arr[i].cost, arr[i].stats.levels, arr[i].peak_bytes, arr[i].footprint)
+                for i in range(len(bufs))]
+
+    # warm-up: the smallest jobs of this rank's share (kernel loading, pools)
+    small = sorted(dev_bufs, key=lambda b: b.hg.P)[:max(1, min(8, len(dev_bufs)))]
+    for _ in range(args.warmup):
+        batch(small, args.slots)
+    sampler = None if args.no_clocks else ClockSampler(gpu_uuid(torch, local))
+    time.sleep(0.3)
+    _barrier(world, local)
+    l0 = P.snnmap_launch_count()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        res = batch(dev_bufs, args.slots)
+    _barrier(world, local)
+    t_batch = (time.perf_counter() - t0) / args.steps
+    launches = P.snnmap_launch_count() - l0
+    clocks = sampler.stop() if sampler else {"sm_mhz": None, "sm_max_mhz": None,
+                                             "reasons": ["not sampled"]}
+    t_batch = _max_over_ranks(t_batch, world, local)
+    # one job at a time, same jobs
+    t0 = time.perf_counter()
+    ser = batch(dev_bufs, 1)
+    _barrier(world, local)
+    t_serial = _max_over_ranks(time.perf_counter() - t0, world, local)
+    assert [r[0] for r in ser] == [r[0] for r in res], "batched costs differ from serial"
+    # end to end: host inputs and results, copies inside the timed region
+    t0 = time.perf_counter()
+    eres = batch(host_bufs, args.slots)
+    _barrier(world, local)
+    t_e2e = _max_over_ranks(time.perf_counter() - t0, world, local)
+    assert [r[0] for r in eres] == [r[0] for r in res]
+    if rank == 0:
+        pins = sum(hg.P for hg in hgs) * world
+        line = {
+            "metric": BATCH_METRIC, "value": n_jobs / t_batch, "unit": "jobs/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t_batch * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": "cfg4", "description": CONFIGS["cfg4"][0], "jobs": n_jobs,
+                       "slots": args.slots, "parallelism": f"jobs sharded over {world} GPU(s)",
+                       "neurons_rank0": sum(hg.V for hg in hgs), "pins_rank0": sum(hg.P for hg in hgs),
+                       "warmup_jobs": "the 8 smallest jobs of the rank's share per warm-up step",
+                       "gen_s_rank0": round(gen_s, 1),
+                       "l2": "every job's inputs are read once per pass; no flush"},
+            "serial": {"value": n_jobs / t_serial, "unit": "jobs/s", "s": t_serial,
+                       "speedup_batched": t_serial / t_batch},
+            "pins_per_s": pins / t_batch,
+            "peak_over_footprint_max": max(r[2] / r[3] for r in res),
+            "e2e": {"value": n_jobs / t_e2e, "unit": "jobs/s",
+                    "h2d_bytes_per_step": sum(8 * (hg.E + 1) + 4 * hg.P + 4 * hg.E for hg in hgs) * world,
+                    "d2h_bytes_per_step": sum(4 * hg.V for hg in hgs) * world},
+            "gpu_launches": launches, "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_serve(args):
+    """cfg5: replay a Poisson arrival stream into a server (jobs admitted by
+    footprint as slots free up); latency = completion - arrival. Compared
+    with the same stream served one job at a time."""
+    import torch
+    rank, world, local = _dist_setup()
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2609_07577_gb300 import JobBuffers, Server
+    n_jobs = args.jobs or 48
+    stream = snngen.serve_stream(n_jobs)
+    if args.max_neurons:
+        stream = [d for d in stream if d["n"] <= args.max_neurons]
+    mine = [d for i, d in enumerate(stream) if i % world == rank]
+    t0 = time.perf_counter()
+    bufs = [JobBuffers(snngen.serve_job(d), on_host=True) for d in mine]
+    gen_s = time.perf_counter() - t0
+    t_arr = [d["t"] for d in mine]
+
+    def replay(slots):
+        with Server(slots=slots) as S:
+            base = time.perf_counter()
+            tickets = []
+            for b, ta in zip(bufs, t_arr):
+                dt = ta - (time.perf_counter() - base)
+                if dt > 0:
+                    time.sleep(dt)
+                tickets.append((S.submit_buffers(b), ta))
+            t_sub0 = None
+            out = []
+            for t, ta in tickets:
+                r = S.wait(t)
+                assert r["status"] == 0, r["error"]
+                out.append(r)
+            # latency from the scheduled arrival: the server clock starts at
+            # creation, just before `base`
+            lat = [r["t_end_ms"] / 1e3 - ta for r, (_, ta) in zip(out, tickets)]
+            span = max(r["t_end_ms"] for r in out) / 1e3
+            for t, _ in tickets:
+                S.release(t)
+        return out, lat, span
+
+    # warm-up: the smallest job, alone
+    small = min(bufs, key=lambda b: b.hg.P)
+    for _ in range(args.warmup):
+        with Server(slots=1) as S:
+            S.wait(S.submit_buffers(small))
+    sampler = None if args.no_clocks else ClockSampler(gpu_uuid(torch, local))
+    _barrier(world, local)
+    out, lat, span = replay(args.slots)
+    clocks = sampler.stop() if sampler else {"sm_mhz": None, "sm_max_mhz": None,
+                                             "reasons": ["not sampled"]}
+    out1, lat1, span1 = replay(1)
+    assert [r["cost"] for r in out] == [r["cost"] for r in out1], "served costs differ from serial"
+    span = _max_over_ranks(span, world, local)
+    span1 = _max_over_ranks(span1, world, local)
+    if rank == 0:
+        q = lambda xs, p: float(np.percentile(np.array(xs) * 1e3, p))
+        line = {
+            "metric": SERVE_METRIC, "value": len(stream) / span, "unit": "jobs/s",
+            "n_gpus": world, "steps": 1, "warmup": args.warmup, "ms_per_step": span * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic",
+            "config": {"workload": "cfg5", "description": CONFIGS["cfg5"][0],
+                       "jobs": len(stream), "slots": args.slots, "rate_jobs_per_s": 200.0,
+                       "max_neurons": args.max_neurons or None,
+                       "neurons_rank0": sum(b.hg.V for b in bufs),
+                       "pins_rank0": sum(b.hg.P for b in bufs), "gen_s_rank0": round(gen_s, 1),
+                       "parallelism": f"jobs sharded over {world} GPU(s)",
+                       "inputs": "pinned host memory, copied in and out by the server"},
+            "latency_ms": {"p50": q(lat, 50), "p99": q(lat, 99), "max": q(lat, 100)},
+            "serial": {"value": len(stream) / span1, "unit": "jobs/s",
+                       "latency_ms": {"p50": q(lat1, 50), "p99": q(lat1, 99)}},
+            "e2e": {"value": len(stream) / span, "unit": "jobs/s",
+                    "h2d_bytes_per_step": sum(8 * (b.hg.E + 1) + 4 * b.hg.P + 4 * b.hg.E for b in bufs) * world,
+                    "d2h_bytes_per_step": sum(4 * b.hg.V for b in bufs) * world},
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.config == "cfg4":
+        run_batch(args)
+    elif args.config == "cfg5":
+        run_serve(args)
     else:
         run_ours(args)
 

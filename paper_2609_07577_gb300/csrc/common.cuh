@@ -164,6 +164,13 @@ struct Arena {
         *p = (T*)v;
         return Status{};
     }
+    // position of the bump pointer; rewind(m) hands back everything taken
+    // after mark() returned m (chunks added since are freed, stream-ordered)
+    struct Mark {
+        size_t nchunks, used, step_total;
+    };
+    Mark mark() const { return Mark{chunks.size(), used, step_total}; }
+    void rewind(const Mark& m);
     void reset();              // forget this step's allocations (stream-ordered)
     void release();            // free everything
     size_t held() const;

@@ -695,7 +695,8 @@ inline Status set_smem(K kernel, size_t bytes)
 constexpr int64_t HT_SPLIT_CAP = 1 << 16;
 
 // Split tier for the vertices slist[0..ns). limit > 0 caps the tables and
-// collects the vertices that overflowed into `again` (count in h_cnt[0]);
+// appends the vertices that overflowed to `again` at the device counter
+// *nagain (the caller clears it; h_cnt[0] receives its new value);
 // limit == 0 sizes every table to its exact bound, which cannot overflow.
 template <class Pol>
 Status run_split(const Pol& pol, Arena& ar, cudaStream_t s, const int32_t* sl, int64_t ns,
@@ -761,7 +762,6 @@ Status run_split(const Pol& pol, Arena& ar, cudaStream_t s, const int32_t* sl, i
                                                                                     scap, pool, gacc, ovf);
     SNN_CUDA(cudaGetLastError());
     if (limit > 0) {
-        SNN_CUDA(cudaMemsetAsync(nagain, 0, sizeof(int64_t), s));
         SNN_L k_ht_collect_ovf<<<grid_for(ns, 256), 256, 0, s>>>(sl, ns, ovf, again, nagain);
         SNN_CUDA(cudaGetLastError());
         SNN_CUDA(cudaMemcpyAsync(h_cnt, nagain, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -815,14 +815,35 @@ Status run_histogram(const Pol& pol, Arena& ar, cudaStream_t s, int64_t* d_cnt, 
     const int32_t* sl = lists + (int64_t)HT_TIER_SPLIT * V;
     // first pass with tables capped at 2 * HT_SPLIT_CAP slots; vertices that
     // overflow them are redone with tables sized to their exact key bound
+    // Both passes run over chunks of vertices whose tables fit in a pool of
+    // max(64 MiB, 4 bytes per pin of the level), so the scratch of this tier
+    // stays bounded whatever the degree distribution.
     int32_t* again;
     int64_t* nagain;
     SNN_TRY(ar.alloc(&again, ns));
     SNN_TRY(ar.alloc(&nagain, 1));
-    SNN_TRY(run_split(pol, ar, s, sl, ns, workv, HT_SPLIT_CAP, again, nagain, h_cnt));
+    SNN_CUDA(cudaMemsetAsync(nagain, 0, sizeof(int64_t), s));
+    const int64_t pool_budget = std::max<int64_t>((int64_t)64 << 20, 4 * pol.L.P);
+    const int64_t sb = (int64_t)slot_bytes<S>();
+    const int64_t chunk1 = std::max<int64_t>(1, pool_budget / (2 * HT_SPLIT_CAP * sb));
+    h_cnt[0] = 0;
+    for (int64_t c0 = 0; c0 < ns; c0 += chunk1) {
+        Arena::Mark m = ar.mark();
+        SNN_TRY(run_split(pol, ar, s, sl + c0, std::min(chunk1, ns - c0), workv, HT_SPLIT_CAP,
+                          again, nagain, h_cnt));
+        ar.rewind(m);
+    }
     int64_t n2 = h_cnt[0];
     if (n2 == 0) return Status{};
-    return run_split(pol, ar, s, again, n2, workv, 0, nullptr, nullptr, h_cnt);
+    const int64_t kb2 = pol.keys > 16 ? pol.keys : 16;
+    const int64_t chunk2 = std::max<int64_t>(1, pool_budget / (pow2_ceil(2 * kb2) * sb));
+    for (int64_t c0 = 0; c0 < n2; c0 += chunk2) {
+        Arena::Mark m = ar.mark();
+        SNN_TRY(run_split(pol, ar, s, again + c0, std::min(chunk2, n2 - c0), workv, 0, nullptr,
+                          nullptr, h_cnt));
+        ar.rewind(m);
+    }
+    return Status{};
 }
 
 }  // namespace snn

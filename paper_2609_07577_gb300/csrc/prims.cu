@@ -67,6 +67,18 @@ void Arena::reset()
     step_total = 0;
 }
 
+void Arena::rewind(const Mark& m)
+{
+    if (step_total > peak) peak = step_total;
+    while (chunks.size() > m.nchunks && !chunks.empty()) {
+        cudaFreeAsync(chunks.back(), stream);
+        chunks.pop_back();
+        sizes.pop_back();
+    }
+    used = m.used;
+    step_total = m.step_total;
+}
+
 void Arena::release()
 {
     for (void* p : chunks) cudaFreeAsync(p, stream);

@@ -38,13 +38,13 @@ int64_t level_bytes(int64_t V, int64_t E, int64_t P)
 
 // Footprint model of one pass: level 0, the newest contracted level (at most
 // the size of level 0), the intermediate levels kept under a budget of one
-// level 0, the scratch arena (hash tables, sort buffers and pin counts, at
-// most about three level 0s on the generated workloads), the per-vertex
-// matching arrays, and a fixed allowance (the scratch arena never holds less
-// than one 64 MiB chunk).
+// level 0, the scratch arena (sort buffers, pin counts and the hash-table
+// pools, which the histogram engine bounds by max(64 MiB, 4 bytes per pin)),
+// the per-vertex matching arrays, and a fixed allowance for the arena's
+// 64 MiB minimum chunk and the split tier's minimum pool.
 constexpr int64_t kFootLevels = 3;
 constexpr int64_t kFootScratch = 3;
-constexpr int64_t kFootFixed = (int64_t)96 << 20;   // covers the arena's 64 MiB minimum chunk
+constexpr int64_t kFootFixed = (int64_t)160 << 20;
 
 int64_t input_bytes(int64_t V, int64_t E, int64_t P)
 {

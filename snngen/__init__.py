@@ -258,24 +258,25 @@ def cfg3() -> Hypergraph:
                     omega=4096, delta=16384, phi=65536, name="cfg3")
 
 
+def batch_jobs_one(j, nmin=10_000, nmax=500_000):
+    """Job j of a batched run: seed j; size log-uniform on [nmin, nmax]; even
+    jobs are layered (4 layers), odd jobs power-law with locality block
+    min(65536, N); Omega from {256, 1024, 4096}, Delta = 4*Omega,
+    Phi = 16*Omega."""
+    rng = np.random.Generator(np.random.PCG64(j))
+    n = int(round(math.exp(rng.uniform(math.log(nmin), math.log(nmax)))))
+    om = int(rng.choice([256, 1024, 4096]))
+    if j % 2 == 0:
+        width = max(64, n // 4)
+        return layered(4, width, 32, 8, seed=j, omega=om, delta=4 * om, phi=16 * om,
+                       name=f"job{j}")
+    return powerlaw(n, min(65536, n), 8, 16384, 2.1, 0.7, seed=j, omega=om, delta=4 * om,
+                    phi=16 * om, name=f"job{j}")
+
+
 def batch_jobs(n_jobs=256, nmin=10_000, nmax=500_000):
-    """Independent jobs of a batched run: job j uses seed j; size is
-    log-uniform on [nmin, nmax]; even jobs are layered (4 layers), odd jobs
-    power-law with locality block min(65536, N); Omega from {256, 1024, 4096},
-    Delta = 4*Omega, Phi = 16*Omega."""
-    jobs = []
-    for j in range(n_jobs):
-        rng = np.random.Generator(np.random.PCG64(j))
-        n = int(round(math.exp(rng.uniform(math.log(nmin), math.log(nmax)))))
-        om = int(rng.choice([256, 1024, 4096]))
-        if j % 2 == 0:
-            width = max(64, n // 4)
-            jobs.append(layered(4, width, 32, 8, seed=j, omega=om, delta=4 * om,
-                                phi=16 * om, name=f"job{j}"))
-        else:
-            jobs.append(powerlaw(n, min(65536, n), 8, 16384, 2.1, 0.7, seed=j,
-                                 omega=om, delta=4 * om, phi=16 * om, name=f"job{j}"))
-    return jobs
+    """The jobs 0..n_jobs-1 of a batched run (see batch_jobs_one)."""
+    return [batch_jobs_one(j, nmin, nmax) for j in range(n_jobs)]
 
 
 def serve_stream(n_jobs=2000, rate=200.0, nmin=10_000, nmax=2_000_000, seed=5):
