@@ -72,6 +72,8 @@ typedef struct {
     int32_t level, round;
     int32_t n_props;  /* vertices that proposed a move */
     int32_t istar;    /* length of the enacted prefix (0: none) */
+    int32_t n_active; /* vertices with save > 0, the only ones a move can gain on */
+    int32_t rows;     /* 1: gains read from connection rows (snnmap_set_row_budget) */
     int64_t gain;     /* Conn removed by the enacted prefix */
 } snnmap_round_log;
 
@@ -251,6 +253,17 @@ int snnmap_stage_times(snnmap_hgraph* h, snnmap_stage_time* out, int32_t cap, in
  * the budget.
  */
 int snnmap_set_level_budget(snnmap_hgraph* h, int64_t bytes);
+
+/*
+ * Memory for connection rows in the refinement of snnmap_partition: for the
+ * levels (from the coarsest down) whose vertices times the partitions fit in
+ * `bytes` (8 bytes per vertex and partition), each vertex keeps its
+ * connection weight and inbound overlap to every partition, updated as moves
+ * are enacted and carried to the next finer level, instead of a histogram
+ * per round. -1: the default, 1/8 of the device's memory; 0: none. Results do
+ * not depend on it (used only when the summed omega stays below 2^31).
+ */
+int snnmap_set_row_budget(snnmap_hgraph* h, int64_t bytes);
 
 /* Bytes of device memory the handle currently holds. */
 int snnmap_device_bytes(const snnmap_hgraph* h, int64_t* bytes);

@@ -30,7 +30,8 @@ class Stats(C.Structure):
 
 class RoundLog(C.Structure):
     _fields_ = [("level", C.c_int32), ("round", C.c_int32), ("n_props", C.c_int32),
-                ("istar", C.c_int32), ("gain", C.c_int64)]
+                ("istar", C.c_int32), ("n_active", C.c_int32), ("rows", C.c_int32),
+                ("gain", C.c_int64)]
 
 
 class LevelLog(C.Structure):
@@ -93,6 +94,7 @@ _SIGS = {
     "snnmap_stage_times": (C.c_int, [_vp, _vp, _i32, C.POINTER(_i32)]),
     "snnmap_launch_count": (_i64, []),
     "snnmap_set_level_budget": (C.c_int, [_vp, _i64]),
+    "snnmap_set_row_budget": (C.c_int, [_vp, _i64]),
     "snnmap_connectivity_noalloc": (C.c_int, [_i32, _i32, _vp, _vp, _vp, _vp, _i32, _vp, _vp]),
     "snnmap_peak_bytes": (C.c_int, [_vp, C.POINTER(_i64)]),
     "snnmap_job_footprint": (C.c_int, [_i32, _i32, _i64, _i32, C.POINTER(_i64)]),
@@ -347,6 +349,10 @@ def snnmap_batch_partition(jobs, slots=0, mem_budget=0, dry_run_us=0):
     statuses are in the structs)."""
     o = ServeOpts(int(slots), int(dry_run_us), int(mem_budget))
     return lib().snnmap_batch_partition(jobs, len(jobs), C.byref(o))
+
+
+def snnmap_set_row_budget(h, nbytes):
+    check(lib().snnmap_set_row_budget(h, int(nbytes)))
 
 
 def snnmap_launch_count():

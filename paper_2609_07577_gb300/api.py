@@ -116,6 +116,10 @@ class HGraph:
     def level_logs(self):
         return N.snnmap_level_logs(self._h)
 
+    def set_row_budget(self, nbytes):
+        """Bytes for refinement connection rows (-1 default, 0 none)."""
+        N.snnmap_set_row_budget(self._h, nbytes)
+
     def set_level_budget(self, nbytes):
         N.snnmap_set_level_budget(self._h, nbytes)
 

@@ -4,6 +4,7 @@
 // partition per coarsest vertex, then project and refine down to level 0.
 #include "internal.cuh"
 
+#include <climits>
 #include <new>
 #include <string>
 
@@ -122,6 +123,7 @@ void snnmap_free(snnmap_hgraph* h)
     if (!h) return;
     cudaStreamSynchronize(h->stream);
     snn::prof_release(h);
+    snn::dense_close(h);
     drop_levels_above(h, 0);
     h->scratch.release();
     if (h->cand) cudaFreeAsync(h->cand, h->stream);
@@ -312,6 +314,21 @@ int snnmap_partition(snnmap_hgraph* h, void* stream, int32_t* d_rho_out, int64_t
     int32_t* cur = ((nl - 1) % 2 == 0) ? d_rho_out : tmp;
     int32_t* oth = cur == d_rho_out ? tmp : d_rho_out;
     snn::Status s2 = snn::iota_i32(cur, K, h->stream);
+    // connection rows for the levels from the coarsest down to the finest one
+    // whose rows fit the row budget (conn is stored in int32: needs the
+    // summed omega below 2^31); without room the levels use histograms
+    int32_t ld = nl;
+    {
+        int64_t rb = snn::dense_row_budget(h);
+        int64_t per = ((((int64_t)K + 3) & ~(int64_t)3) * 8 + 12);
+        if (rb > 0 && !h->wide && h->wsum <= INT32_MAX)
+            for (int32_t l = nl - 1; l >= 0 && (int64_t)h->levels[l].V * per <= rb; l--) ld = l;
+        if (ld < nl && !snn::dense_open(h, K, h->levels[ld].V).ok()) {
+            snn::dense_close(h);
+            cudaGetLastError();
+            ld = nl;
+        }
+    }
     int64_t cost = 0;
     for (int32_t l = nl - 1; s2.ok() && l >= 0; l--) {
         if (l < nl - 1) {
@@ -324,6 +341,15 @@ int snnmap_partition(snnmap_hgraph* h, void* stream, int32_t* d_rho_out, int64_t
             s2 = snn::project(h, l, cur, oth);
             if (!s2.ok()) break;
             std::swap(cur, oth);
+            if (l >= ld) {
+                snn::ProfScope prof(h, snn::PS_ROWS);
+                s2 = snn::dense_descend(h, l);
+            }
+            else if (h->dense.C) snn::dense_close(h);
+            if (!s2.ok()) break;
+        } else if (ld <= l) {
+            s2 = snn::dense_begin(h, l);
+            if (!s2.ok()) break;
         }
         int64_t c0 = 0;
         s2 = snn::refine_level(h, l, K, cur, &cost, l == nl - 1 ? &c0 : nullptr);
@@ -331,6 +357,7 @@ int snnmap_partition(snnmap_hgraph* h, void* stream, int32_t* d_rho_out, int64_t
         snn::note_bytes(h);
     }
     cudaFreeAsync(tmp, h->stream);
+    snn::dense_close(h);
     if (!s2.ok()) return fail(s2);
     if (cur != d_rho_out) return fail(SNNMAP_ERR_CUDA, "internal: level parity");
     int32_t ne = 0;
@@ -519,6 +546,13 @@ int snnmap_peak_bytes(const snnmap_hgraph* h, int64_t* bytes)
     if (!h || !bytes) return fail(SNNMAP_ERR_INVALID, "NULL argument");
     snn::note_bytes(const_cast<snnmap_hgraph*>(h));
     *bytes = h->peak_bytes;
+    return SNNMAP_OK;
+}
+
+int snnmap_set_row_budget(snnmap_hgraph* h, int64_t bytes)
+{
+    if (!h || bytes < -1) return fail(SNNMAP_ERR_INVALID, "bad arguments");
+    h->row_budget = bytes;
     return SNNMAP_OK;
 }
 

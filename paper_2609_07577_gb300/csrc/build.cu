@@ -21,7 +21,8 @@ Status read_scalars(snnmap_hgraph* h)
 
 const char* const kStageNames[PS_N] = {"build",    "affinity",  "match",  "contract",
                                        "incidence", "pincount", "gains",  "sortmoves",
-                                       "replay",   "validity",  "apply"};
+                                       "replay",   "validity",  "apply",  "save",
+                                       "rows",     "cross"};
 
 static cudaEvent_t prof_event(snnmap_hgraph* h)
 {
@@ -115,6 +116,7 @@ Status level_alloc(snnmap_hgraph* h, Level& L, LevelExtra& X, int32_t V, int32_t
 int64_t held_bytes(const snnmap_hgraph* h)
 {
     int64_t t = (int64_t)h->scratch.held() + (int64_t)h->cap_v * 20;
+    if (h->dense.C) t += h->dense.cap * (h->dense.Kp * 8 + 12);
     for (auto& L : h->levels) t += (int64_t)L.bytes + 4 * (int64_t)L.V;
     return t;
 }
@@ -453,6 +455,7 @@ Status build_level0(snnmap_hgraph* h, int32_t V, int32_t E, const int64_t* d_off
     int64_t P0 = h->h_scal[SC_B];
     int32_t maxlen = (int32_t)h->h_scal[SC_C];
     h->wide = (uint64_t)h->h_scal[SC_D] >= 0xffffffffull;
+    h->wsum = h->h_scal[SC_D];
 
     h->levels.emplace_back();
     h->extra.emplace_back();

@@ -770,6 +770,51 @@ Status run_split(const Pol& pol, Arena& ar, cudaStream_t s, const int32_t* sl, i
     return Status{};
 }
 
+// table capacity of each split-tier vertex (as k_ht_split_deg sizes it)
+template <class Pol>
+__global__ void k_ht_split_caps(Pol pol, const int32_t* __restrict__ slist, int64_t ns,
+                                const int64_t* __restrict__ workv, int64_t limit, int64_t* caps)
+{
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < ns;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        int64_t work = workv[slist[j]];
+        int64_t bound = work < pol.keys ? work : pol.keys;
+        if (limit > 0 && bound > limit) bound = limit;
+        caps[j] = pow2_ceil(2 * (bound > 16 ? bound : 16));
+    }
+}
+
+// cuts[c] .. cuts[c+1]: consecutive runs of slist whose tables hold at most
+// pool_slots slots together (a single larger vertex forms its own run)
+template <class Pol>
+Status split_cuts(const Pol& pol, Arena& ar, cudaStream_t s, const int32_t* sl, int64_t ns,
+                  const int64_t* workv, int64_t limit, int64_t pool_slots,
+                  std::vector<int64_t>& cuts)
+{
+    cuts.assign(1, 0);
+    if (ns <= 0) return Status{};
+    Arena::Mark m = ar.mark();
+    int64_t *caps, *pre;
+    SNN_TRY(ar.alloc(&caps, ns));
+    SNN_TRY(ar.alloc(&pre, ns));
+    SNN_L k_ht_split_caps<Pol><<<grid_for(ns, 256), 256, 0, s>>>(pol, sl, ns, workv, limit, caps);
+    SNN_CUDA(cudaGetLastError());
+    SNN_TRY(scan_inclusive_i64(caps, pre, ns, ar, s));
+    std::vector<int64_t> hp((size_t)ns);
+    SNN_CUDA(cudaMemcpyAsync(hp.data(), pre, (size_t)ns * 8, cudaMemcpyDeviceToHost, s));
+    SNN_CUDA(cudaStreamSynchronize(s));
+    ar.rewind(m);
+    int64_t start = 0;
+    while (start < ns) {
+        int64_t base = start > 0 ? hp[(size_t)start - 1] : 0;
+        int64_t j = std::upper_bound(hp.begin() + start, hp.end(), base + pool_slots) - hp.begin();
+        if (j <= start) j = start + 1;
+        cuts.push_back(j);
+        start = j;
+    }
+    return Status{};
+}
+
 // Host driver: work, classification and the warp, block and big-block tiers
 // run without host synchronization; the split tier follows reads of its
 // sizes. d_cnt: >= HT_NTIER device int64; h_cnt: a pinned host int64[>=3];
@@ -817,29 +862,30 @@ Status run_histogram(const Pol& pol, Arena& ar, cudaStream_t s, int64_t* d_cnt, 
     // overflow them are redone with tables sized to their exact key bound
     // Both passes run over chunks of vertices whose tables fit in a pool of
     // max(64 MiB, 4 bytes per pin of the level), so the scratch of this tier
-    // stays bounded whatever the degree distribution.
+    // stays bounded whatever the degree distribution; chunks are cut from
+    // the vertices' actual table sizes.
     int32_t* again;
     int64_t* nagain;
     SNN_TRY(ar.alloc(&again, ns));
     SNN_TRY(ar.alloc(&nagain, 1));
     SNN_CUDA(cudaMemsetAsync(nagain, 0, sizeof(int64_t), s));
-    const int64_t pool_budget = std::max<int64_t>((int64_t)64 << 20, 4 * pol.L.P);
-    const int64_t sb = (int64_t)slot_bytes<S>();
-    const int64_t chunk1 = std::max<int64_t>(1, pool_budget / (2 * HT_SPLIT_CAP * sb));
+    const int64_t pool_slots =
+        std::max<int64_t>((int64_t)64 << 20, 4 * pol.L.P) / (int64_t)slot_bytes<S>();
+    std::vector<int64_t> cuts;
+    SNN_TRY(split_cuts(pol, ar, s, sl, ns, workv, HT_SPLIT_CAP, pool_slots, cuts));
     h_cnt[0] = 0;
-    for (int64_t c0 = 0; c0 < ns; c0 += chunk1) {
+    for (size_t c = 0; c + 1 < cuts.size(); c++) {
         Arena::Mark m = ar.mark();
-        SNN_TRY(run_split(pol, ar, s, sl + c0, std::min(chunk1, ns - c0), workv, HT_SPLIT_CAP,
+        SNN_TRY(run_split(pol, ar, s, sl + cuts[c], cuts[c + 1] - cuts[c], workv, HT_SPLIT_CAP,
                           again, nagain, h_cnt));
         ar.rewind(m);
     }
     int64_t n2 = h_cnt[0];
     if (n2 == 0) return Status{};
-    const int64_t kb2 = pol.keys > 16 ? pol.keys : 16;
-    const int64_t chunk2 = std::max<int64_t>(1, pool_budget / (pow2_ceil(2 * kb2) * sb));
-    for (int64_t c0 = 0; c0 < n2; c0 += chunk2) {
+    SNN_TRY(split_cuts(pol, ar, s, again, n2, workv, 0, pool_slots, cuts));
+    for (size_t c = 0; c + 1 < cuts.size(); c++) {
         Arena::Mark m = ar.mark();
-        SNN_TRY(run_split(pol, ar, s, again + c0, std::min(chunk2, n2 - c0), workv, 0, nullptr,
+        SNN_TRY(run_split(pol, ar, s, again + cuts[c], cuts[c + 1] - cuts[c], workv, 0, nullptr,
                           nullptr, h_cnt));
         ar.rewind(m);
     }

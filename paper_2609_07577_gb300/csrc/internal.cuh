@@ -26,10 +26,28 @@ struct LevelExtra {
 // pipeline stages timed by the profiler
 enum ProfStage : int {
     PS_BUILD, PS_AFFINITY, PS_MATCH, PS_CONTRACT, PS_INCIDENCE, PS_PINCOUNT, PS_GAINS,
-    PS_SORTMOVES, PS_REPLAY, PS_VALIDITY, PS_APPLY, PS_N
+    PS_SORTMOVES, PS_REPLAY, PS_VALIDITY, PS_APPLY, PS_SAVE, PS_ROWS, PS_CROSS, PS_N
 };
 extern const char* const kStageNames[PS_N];
 
+}  // namespace snn
+
+namespace snn {
+// Connection rows of the refinement levels that fit the row budget: C and O
+// hold cap rows of Kp (K rounded up to 4) int32 entries; rowid maps the
+// current level's vertices to rows.
+struct DenseRows {
+    int32_t K = 0;
+    int64_t Kp = 0;
+    int64_t cap = 0;
+    int32_t* C = nullptr;
+    int32_t* O = nullptr;
+    int32_t* rowid = nullptr;
+    int32_t* rowid2 = nullptr;
+    int32_t* fresh = nullptr;
+    int32_t level = -1;       // level the rows describe
+    bool pending = false;     // fresh rows of this level not computed yet
+};
 }  // namespace snn
 
 struct snnmap_hgraph {
@@ -53,6 +71,9 @@ struct snnmap_hgraph {
     bool have_matching = false;
     int32_t last_pairs = 0;
     bool wide = false;           // some neighbour score may reach 2^32
+    int64_t wsum = 0;            // sum of omega over the input hyperedges
+    int64_t row_budget = -1;     // bytes for connection rows (-1: default, 0: none)
+    snn::DenseRows dense;
     std::vector<snnmap_round_log> rlog;
     std::vector<snnmap_level_log> llog;
     // profiler
@@ -119,6 +140,15 @@ void thin_levels(snnmap_hgraph* h);
 // S5
 Status project(snnmap_hgraph* h, int32_t level, const int32_t* rho_coarse, int32_t* rho_fine);
 // S6-S12 on one level; rho in place
+// connection rows: allocation for `rows` vertices and K partitions; rows of
+// every vertex of `level` (the coarsest refined level) marked fresh; descent
+// from level+1 to `level` after projection; release
+Status dense_open(snnmap_hgraph* h, int32_t K, int64_t rows);
+Status dense_begin(snnmap_hgraph* h, int32_t level);
+Status dense_descend(snnmap_hgraph* h, int32_t level);
+void dense_close(snnmap_hgraph* h);
+int64_t dense_row_budget(const snnmap_hgraph* h);
+
 Status refine_level(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* rho, int64_t* cost,
                     int64_t* cost_start);
 // caller-provided rho must index existing partitions

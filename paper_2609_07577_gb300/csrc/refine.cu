@@ -46,6 +46,7 @@ enum : int {
     RS_NEV = SC_F,     // inbound events emitted
     RS_NHV = SC_G,     // hyperedges replayed by the block tier
     RS_DEG = 8,        // incidences of proposing vertices
+    RS_ACT = 10,       // vertices with save > 0
 };
 
 constexpr int REPLAY_WARP_MAX = 32;
@@ -210,6 +211,50 @@ __global__ void k_check_pstate(int32_t K, PState ps, int32_t omega, int32_t delt
     if (__any_sync(FULL, bad) && (threadIdx.x & 31) == 0) atomicOr((int*)&scal[SC_STATUS], ST_BADSTATE);
 }
 
+// counts of partition p in hyperedge a at round start (entries sorted by p)
+__device__ __forceinline__ void lookup_count(const PinCounts& pc, int64_t b, int32_t lam, int32_t p,
+                                             int32_t& cnt, int32_t& dcnt)
+{
+    int32_t lo = 0, hi = lam;
+    while (lo < hi) {
+        int32_t mid = (lo + hi) >> 1;
+        if (pc.p[b + mid] < p) lo = mid + 1;
+        else hi = mid;
+    }
+    if (lo < lam && pc.p[b + lo] == p) {
+        cnt = pc.cnt[b + lo];
+        dcnt = pc.dcnt[b + lo];
+    } else {
+        cnt = 0;
+        dcnt = 0;
+    }
+}
+
+// save(n) = omega of incident hyperedges in which n is the last pin of its
+// partition, W(n) = omega of all incident hyperedges. A move of n gains
+// save(n) - W(n) + conn(n, p) <= save(n), so a vertex with save(n) = 0
+// never proposes. One warp per hyperedge, lanes over its pins (both arrays
+// cleared before).
+__global__ void __launch_bounds__(256)
+    k_save(Level L, PinCounts pc, const int32_t* __restrict__ rho, int64_t* savev, int64_t* Wv)
+{
+    int lane = threadIdx.x & 31;
+    int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t a = gw; a < L.E; a += nw) {
+        int64_t b = L.hoff[a], e = L.hoff[a + 1];
+        int32_t lam = pc.lam[a];
+        unsigned long long w = (unsigned long long)L.hw[a];
+        for (int64_t j = b + lane; j < e; j += 32) {
+            int32_t x = L.hpins[j];
+            atomicAdd((unsigned long long*)&Wv[x], w);
+            int32_t c, d;
+            lookup_count(pc, b, lam, rho[x], c, d);
+            if (c == 1) atomicAdd((unsigned long long*)&savev[x], w);
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // S7: partition connection histogram per vertex
 
@@ -249,8 +294,9 @@ struct GainPol {
     int32_t omega, delta, phi;
     int32_t* pto;
     int64_t* pgain;
+    const int64_t* savev;
 
-    __device__ bool skip(int32_t) const { return false; }
+    __device__ bool skip(int32_t n) const { return savev[n] == 0; }
     __device__ int64_t vb(int32_t n) const { return L.voff[n]; }
     __device__ int64_t ve(int32_t n) const { return L.voff[n + 1]; }
     __device__ int64_t seg_len(int64_t i) const
@@ -308,15 +354,295 @@ struct GainPol {
     }
 };
 
+struct Moves {
+    int32_t* n;
+    int32_t* from;
+    int32_t* to;
+};
+
+// ---------------------------------------------------------------------------
+// Connection rows (refinement levels whose rows fit the memory budget)
+//
+// Row r of vertex n (r = rowid[n]) holds, for every partition p,
+// C[r][p] = conn(n, p) = sum of omega(e) over incident e with cnt(p, e) > 0,
+// and O[r][p] = sum of k(e) over e in which n is a destination and
+// dcnt(p, e) > 0. A round then needs no histogram: the best move of n is a
+// scan of its row against the partition state. Rows change only when a
+// partition's count in a hyperedge crosses zero, which applied moves report
+// (k_dense_cross). Projection to the next finer level leaves the rows of
+// unmatched vertices exact (their hyperedges map one to one onto hyperedges
+// of the same omega, k, destination role and partition set); the two
+// members of each contracted pair get fresh rows (RowPol).
+
+template <typename S_>
+struct RowPol {
+    using S = S_;
+    static constexpr bool kOptimistic = true;
+    struct Acc {
+        __device__ Acc() {}
+        __device__ void add(const Acc&) {}
+        __device__ void atomic_into(Acc*) const {}
+    };
+    static __device__ Acc warp_reduce(const Acc& a) { return a; }
+
+    Level L;
+    PinCounts pc;
+    int32_t V;
+    int64_t keys;
+    const int32_t* fresh;
+    const int32_t* rowid;
+    int32_t* C;
+    int32_t* O;
+    int64_t Kp;
+
+    __device__ bool skip(int32_t n) const { return fresh[n] == 0; }
+    __device__ int64_t vb(int32_t n) const { return L.voff[n]; }
+    __device__ int64_t ve(int32_t n) const { return L.voff[n + 1]; }
+    __device__ int64_t seg_len(int64_t i) const
+    {
+        return pc.lam[(int32_t)((uint32_t)L.vinc[i] & ~SRC_BIT)];
+    }
+    __device__ Seg<S> seg(int64_t i, Acc&) const
+    {
+        uint32_t inc = (uint32_t)L.vinc[i];
+        int32_t a = (int32_t)(inc & ~SRC_BIT);
+        Seg<S> g;
+        g.sd = L.hsd[a];
+        g.nd = !(inc & SRC_BIT) || g.sd;
+        g.b = L.hoff[a];
+        g.len = pc.lam[a];
+        g.w = (S)L.hw[a];
+        g.k = (uint32_t)L.hk[a];
+        return g;
+    }
+    template <class Tb>
+    __device__ bool elem(int32_t, const Seg<S>& g, int32_t off, const Tb& t, Acc&) const
+    {
+        int64_t e = g.b + off;
+        return t.add(pc.p[e], g.w, (g.nd && pc.dcnt[e] > 0) ? g.k : 0u);
+    }
+    // every key of the finished histogram lands in the row (stores, so a
+    // vertex redone by a later tier overwrites its partial entries)
+    __device__ void consider(int32_t n, int32_t p, int64_t conn, uint32_t o, const Acc&, int64_t&,
+                             int32_t&, uint32_t&) const
+    {
+        int64_t r = (int64_t)rowid[n] * Kp + p;
+        C[r] = (int32_t)conn;
+        O[r] = (int32_t)o;
+    }
+    __device__ void write(int32_t, int64_t, int32_t, uint32_t, const Acc&) const {}
+};
+
+// best move per vertex from its row: largest gain = C - (W - save) over
+// partitions p != rho(n) that can take n, ties to the lower p; proposed if
+// positive
+__global__ void __launch_bounds__(256)
+    k_dense_best(Level L, const int32_t* __restrict__ rho, PState ps,
+                 const int64_t* __restrict__ savev, const int64_t* __restrict__ Wv,
+                 const int32_t* __restrict__ rowid, const int32_t* __restrict__ C,
+                 const int32_t* __restrict__ O, int64_t Kp, int32_t K, int32_t omega,
+                 int32_t delta, int32_t phi, int32_t* pto, int64_t* pgain)
+{
+    int lane = threadIdx.x & 31;
+    int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t n = gw; n < L.V; n += nw) {
+        int64_t sv = savev[n];
+        if (sv == 0) {
+            if (lane == 0) {
+                pto[n] = -1;
+                pgain[n] = 0;
+            }
+            continue;
+        }
+        int64_t T = Wv[n] - sv;
+        int32_t own = rho[n];
+        int64_t sz = L.vsize[n], ip = L.vinpins[n], ic = L.vincnt[n];
+        int64_t r0 = (int64_t)rowid[n] * Kp;
+        const int4* row = reinterpret_cast<const int4*>(C + r0);
+        int64_t bs = 0;
+        int32_t bk = -1;
+        for (int64_t q = lane; 4 * q < K; q += 32) {
+            int4 c4 = row[q];
+            int cv[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                int32_t p = (int32_t)(4 * q + u);
+                int64_t g = (int64_t)cv[u] - T;
+                if (p < K && g > bs && p != own && ps.size[p] + sz <= omega &&
+                    ps.inpins[p] + ip <= phi && ps.pincnt[p] + ic - (int64_t)O[r0 + p] <= delta) {
+                    bs = g;
+                    bk = p;
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            int64_t s2 = __shfl_xor_sync(FULL, bs, o);
+            int32_t m2 = __shfl_xor_sync(FULL, bk, o);
+            if (better(s2, m2, bs, bk)) {
+                bs = s2;
+                bk = m2;
+            }
+        }
+        if (lane == 0) {
+            pto[n] = bk;
+            pgain[n] = bk >= 0 ? bs : 0;
+        }
+    }
+}
+
+// Row updates for the enacted prefix: per hyperedge, the moves of its pins
+// with index <= i* give each touched partition's count after the prefix;
+// where cnt(p, e) crosses zero every pin's C[.][p] changes by omega(e), and
+// where dcnt(p, e) crosses zero every destination's O[.][p] by k(e). One
+// warp per hyperedge; buf (one word per pin) collects the enacted moves.
+__global__ void __launch_bounds__(256)
+    k_dense_cross(Level L, PinCounts pc, const int32_t* __restrict__ moveidx, Moves mv,
+                  const int64_t* __restrict__ scal, const int32_t* __restrict__ rowid, int32_t* C,
+                  int32_t* O, int64_t Kp, uint32_t* buf)
+{
+    int64_t istar = scal[RS_BEST] > 0 ? scal[RS_ISTAR] : -1;
+    if (istar < 0) return;
+    int lane = threadIdx.x & 31;
+    unsigned lt = lanemask_lt();
+    int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t a = gw; a < L.E; a += nw) {
+        int64_t b = L.hoff[a], e = L.hoff[a + 1];
+        int sd = L.hsd[a];
+        int m = 0;
+        for (int64_t cb = b; cb < e; cb += 32) {
+            int64_t j = cb + lane;
+            int32_t mi = -1;
+            if (j < e) mi = moveidx[L.hpins[j]];
+            bool ap = mi >= 0 && mi <= istar;
+            unsigned mk = __ballot_sync(FULL, ap);
+            if (ap) buf[b + m + __popc(mk & lt)] = ((uint32_t)mi << 1) | ((j != b || sd) ? 1u : 0u);
+            m += __popc(mk);
+        }
+        if (m == 0) continue;
+        __syncwarp();
+        int32_t lam = pc.lam[a];
+        int64_t w = L.hw[a];
+        int32_t k = L.hk[a];
+        for (int ib = 0; ib < m; ib += 32) {
+            int ii = ib + lane;
+            // up to two crossing records per lane: partition, C sign, O sign
+            int32_t rp[2] = {-1, -1};
+            int rc[2] = {0, 0}, rd[2] = {0, 0};
+            if (ii < m) {
+                int32_t mi = (int32_t)(buf[b + ii] >> 1);
+                int32_t cand[2] = {mv.from[mi], mv.to[mi]};
+                for (int u = 0; u < 2; u++) {
+                    int32_t p = cand[u];
+                    bool first = true;
+                    int nc = 0, nd = 0;
+                    for (int jj = 0; jj < m; jj++) {
+                        uint32_t rj = buf[b + jj];
+                        int32_t mj = (int32_t)(rj >> 1);
+                        int32_t fj = mv.from[mj], tj = mv.to[mj];
+                        if (jj < ii && (fj == p || tj == p)) first = false;
+                        int dlt = (tj == p) - (fj == p);
+                        nc += dlt;
+                        if (rj & 1) nd += dlt;
+                    }
+                    if (!first) continue;
+                    int32_t c0, d0;
+                    lookup_count(pc, b, lam, p, c0, d0);
+                    int cs = ((c0 + nc) > 0) - (c0 > 0);
+                    int ds = ((d0 + nd) > 0) - (d0 > 0);
+                    if (cs || ds) {
+                        rp[u] = p;
+                        rc[u] = cs;
+                        rd[u] = ds;
+                    }
+                }
+            }
+            for (int u = 0; u < 2; u++) {
+                unsigned has = __ballot_sync(FULL, rp[u] >= 0);
+                while (has) {
+                    int src = __ffs(has) - 1;
+                    has &= has - 1;
+                    int32_t p = __shfl_sync(FULL, rp[u], src);
+                    int cs = __shfl_sync(FULL, rc[u], src);
+                    int ds = __shfl_sync(FULL, rd[u], src);
+                    for (int64_t j = b + lane; j < e; j += 32) {
+                        int64_t r = (int64_t)rowid[L.hpins[j]] * Kp + p;
+                        if (cs) atomicAdd(&C[r], (int32_t)(cs * w));
+                        if (ds && (j != b || sd)) atomicAdd(&O[r], ds * k);
+                    }
+                }
+            }
+        }
+    }
+}
+
+// descent to the next finer level: member counts and smallest member per
+// coarse vertex
+__global__ void k_dense_members(int32_t V, const int32_t* __restrict__ cid, int32_t* mcount,
+                                int32_t* first)
+{
+    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < V;
+         n += (int64_t)gridDim.x * blockDim.x) {
+        atomicAdd(&mcount[cid[n]], 1);
+        atomicMin(&first[cid[n]], (int32_t)n);
+    }
+}
+
+__global__ void k_dense_flags(int32_t V, const int32_t* __restrict__ cid,
+                              const int32_t* __restrict__ mcount, const int32_t* __restrict__ first,
+                              int32_t* nonrep, int32_t* fresh)
+{
+    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < V;
+         n += (int64_t)gridDim.x * blockDim.x) {
+        int32_t c = cid[n];
+        nonrep[n] = first[c] != (int32_t)n;
+        fresh[n] = mcount[c] > 1;
+    }
+}
+
+// the smaller member keeps its super-node's row, the other takes row
+// Vc + (its rank among non-representatives)
+__global__ void k_dense_rowid(int32_t V, int32_t Vc, const int32_t* __restrict__ cid,
+                              const int32_t* __restrict__ nonrep, const int32_t* __restrict__ idx,
+                              const int32_t* __restrict__ rowc, int32_t* rowf)
+{
+    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < V;
+         n += (int64_t)gridDim.x * blockDim.x)
+        rowf[n] = nonrep[n] ? Vc + idx[n] : rowc[cid[n]];
+}
+
+// clears the rows of vertices flagged fresh (one warp per vertex)
+__global__ void k_dense_zero(int32_t V, const int32_t* __restrict__ fresh,
+                             const int32_t* __restrict__ rowid, int32_t* C, int32_t* O, int64_t Kp)
+{
+    int lane = threadIdx.x & 31;
+    int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t n = gw; n < V; n += nw) {
+        if (!fresh[n]) continue;
+        int4* c = reinterpret_cast<int4*>(C + (int64_t)rowid[n] * Kp);
+        int4* o = reinterpret_cast<int4*>(O + (int64_t)rowid[n] * Kp);
+        for (int64_t q = lane; q < Kp / 4; q += 32) {
+            c[q] = make_int4(0, 0, 0, 0);
+            o[q] = make_int4(0, 0, 0, 0);
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // S8
 
 __global__ void k_prop_stats(Level L, const int32_t* __restrict__ pto,
-                             const int64_t* __restrict__ pgain, int32_t* flag, int64_t* scal)
+                             const int64_t* __restrict__ pgain,
+                             const int64_t* __restrict__ savev, int32_t* flag, int64_t* scal)
 {
     int64_t mg = 0, deg = 0;
+    int act = 0;
     for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < L.V;
          n += (int64_t)gridDim.x * blockDim.x) {
+        act += savev[n] > 0;
         int f = pto[n] >= 0;
         flag[n] = f;
         if (f) {
@@ -330,9 +656,11 @@ __global__ void k_prop_stats(Level L, const int32_t* __restrict__ pto,
         mg = m2 > mg ? m2 : mg;
         deg += __shfl_xor_sync(FULL, deg, o);
     }
+    act = warp_sum(act);
     if ((threadIdx.x & 31) == 0) {
         if (mg) atomicMax((unsigned long long*)&scal[RS_MAXG], (unsigned long long)mg);
         if (deg) atomicAdd((unsigned long long*)&scal[RS_DEG], (unsigned long long)deg);
+        if (act) atomicAdd((unsigned long long*)&scal[RS_ACT], (unsigned long long)act);
     }
 }
 
@@ -348,12 +676,6 @@ __global__ void k_prop_keys(int32_t V, const int32_t* __restrict__ pto,
         vals[i] = (uint32_t)n;
     }
 }
-
-struct Moves {
-    int32_t* n;
-    int32_t* from;
-    int32_t* to;
-};
 
 __global__ void k_moves(int32_t M, const uint32_t* __restrict__ vals, const int32_t* __restrict__ rho,
                         const int32_t* __restrict__ pto, Moves mv, int32_t* moveidx)
@@ -413,25 +735,6 @@ __device__ __forceinline__ void emit_inbound(const Events& ev, int64_t* scal, in
     ev.dsize[pos] = 0;
     ev.dinp[pos] = 0;
     ev.dpc[pos] = d;
-}
-
-// counts of partition p in hyperedge a at round start (entries sorted by p)
-__device__ __forceinline__ void lookup_count(const PinCounts& pc, int64_t b, int32_t lam, int32_t p,
-                                             int32_t& cnt, int32_t& dcnt)
-{
-    int32_t lo = 0, hi = lam;
-    while (lo < hi) {
-        int32_t mid = (lo + hi) >> 1;
-        if (pc.p[b + mid] < p) lo = mid + 1;
-        else hi = mid;
-    }
-    if (lo < lam && pc.p[b + lo] == p) {
-        cnt = pc.cnt[b + lo];
-        dcnt = pc.dcnt[b + lo];
-    } else {
-        cnt = 0;
-        dcnt = 0;
-    }
 }
 
 // one moved pin's replay given the deltas of earlier moves of the same hyperedge
@@ -664,9 +967,11 @@ __global__ void k_round_init(int64_t* scal) { scal[RS_ISTAR] = INT64_MAX; }
 
 template <typename S>
 static Status gains(snnmap_hgraph* h, Level& L, const PinCounts& pc, const int32_t* rho,
-                    const PState& ps, int32_t K, int32_t* pto, int64_t* pgain)
+                    const PState& ps, int32_t K, int32_t* pto, int64_t* pgain,
+                    const int64_t* savev)
 {
     GainPol<S> pol;
+    pol.savev = savev;
     pol.L = L;
     pol.pc = pc;
     pol.ps = ps;
@@ -681,6 +986,110 @@ static Status gains(snnmap_hgraph* h, Level& L, const PinCounts& pc, const int32
     int64_t* cnt;
     SNN_TRY(h->scratch.alloc(&cnt, HT_NTIER));
     return run_histogram(pol, h->scratch, h->stream, cnt, h->h_scal + 12, h->d_scal);
+}
+
+// rows of the vertices flagged fresh, from the round's pin counts
+static Status dense_fresh(snnmap_hgraph* h, Level& L, const PinCounts& pc)
+{
+    DenseRows& D = h->dense;
+    RowPol<uint32_t> pol;
+    pol.L = L;
+    pol.pc = pc;
+    pol.V = L.V;
+    pol.keys = D.K;
+    pol.fresh = D.fresh;
+    pol.rowid = D.rowid;
+    pol.C = D.C;
+    pol.O = D.O;
+    pol.Kp = D.Kp;
+    int64_t* cnt;
+    SNN_TRY(h->scratch.alloc(&cnt, HT_NTIER));
+    return run_histogram(pol, h->scratch, h->stream, cnt, h->h_scal + 12, h->d_scal);
+}
+
+int64_t dense_row_budget(const snnmap_hgraph* h)
+{
+    if (h->row_budget >= 0) return h->row_budget;
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return 0;
+    return (int64_t)(tot / 8);
+}
+
+Status dense_open(snnmap_hgraph* h, int32_t K, int64_t rows)
+{
+    dense_close(h);
+    DenseRows& D = h->dense;
+    cudaStream_t s = h->stream;
+    D.K = K;
+    D.Kp = ((int64_t)K + 3) & ~(int64_t)3;
+    D.cap = rows > 0 ? rows : 1;
+    SNN_CUDA(cudaMallocAsync(&D.C, (size_t)(D.cap * D.Kp) * 4, s));
+    SNN_CUDA(cudaMallocAsync(&D.O, (size_t)(D.cap * D.Kp) * 4, s));
+    SNN_CUDA(cudaMallocAsync(&D.rowid, (size_t)D.cap * 4, s));
+    SNN_CUDA(cudaMallocAsync(&D.rowid2, (size_t)D.cap * 4, s));
+    SNN_CUDA(cudaMallocAsync(&D.fresh, (size_t)D.cap * 4, s));
+    D.level = -1;
+    D.pending = false;
+    return Status{};
+}
+
+void dense_close(snnmap_hgraph* h)
+{
+    DenseRows& D = h->dense;
+    for (int32_t* p : {D.C, D.O, D.rowid, D.rowid2, D.fresh})
+        if (p) cudaFreeAsync(p, h->stream);
+    D = DenseRows{};
+}
+
+Status dense_begin(snnmap_hgraph* h, int32_t level)
+{
+    DenseRows& D = h->dense;
+    const Level& L = h->levels[level];
+    if (!D.C || L.V > D.cap) return Status{SNNMAP_ERR_STATE, "connection rows: capacity"};
+    SNN_TRY(iota_i32(D.rowid, L.V, h->stream));
+    SNN_TRY(fill_i32(D.fresh, 1, L.V, h->stream));
+    if (L.V > 0) {
+        SNN_L k_dense_zero<<<grid_for((int64_t)L.V * 32, 256), 256, 0, h->stream>>>(L.V, D.fresh, D.rowid,
+                                                                            D.C, D.O, D.Kp);
+        SNN_CUDA(cudaGetLastError());
+    }
+    D.level = level;
+    D.pending = true;
+    return Status{};
+}
+
+Status dense_descend(snnmap_hgraph* h, int32_t level)
+{
+    DenseRows& D = h->dense;
+    const Level& L = h->levels[level];
+    int32_t Vc = h->levels[level + 1].V;
+    if (!D.C || D.level != level + 1 || L.V > D.cap)
+        return Status{SNNMAP_ERR_STATE, "connection rows: descent out of order"};
+    cudaStream_t s = h->stream;
+    Arena& ar = h->scratch;
+    int32_t *mcount, *first, *nonrep, *idx;
+    SNN_TRY(ar.alloc(&mcount, Vc));
+    SNN_TRY(ar.alloc(&first, Vc));
+    SNN_TRY(ar.alloc(&nonrep, L.V));
+    SNN_TRY(ar.alloc(&idx, L.V));
+    SNN_CUDA(cudaMemsetAsync(mcount, 0, (size_t)(Vc > 0 ? Vc : 1) * 4, s));
+    SNN_TRY(fill_i32(first, INT_MAX, Vc, s));
+    if (L.V > 0) {
+        int g = grid_for(L.V, 256);
+        SNN_L k_dense_members<<<g, 256, 0, s>>>(L.V, L.cid, mcount, first);
+        SNN_L k_dense_flags<<<g, 256, 0, s>>>(L.V, L.cid, mcount, first, nonrep, D.fresh);
+        SNN_CUDA(cudaGetLastError());
+        SNN_TRY(scan_exclusive_i32(nonrep, idx, L.V, nullptr, ar, s));
+        SNN_L k_dense_rowid<<<g, 256, 0, s>>>(L.V, Vc, L.cid, nonrep, idx, D.rowid, D.rowid2);
+        SNN_CUDA(cudaGetLastError());
+        std::swap(D.rowid, D.rowid2);
+        SNN_L k_dense_zero<<<grid_for((int64_t)L.V * 32, 256), 256, 0, s>>>(L.V, D.fresh, D.rowid, D.C,
+                                                                     D.O, D.Kp);
+        SNN_CUDA(cudaGetLastError());
+    }
+    D.level = level;
+    D.pending = true;
+    return Status{};
 }
 
 // pin counts + partition state + Conn for rho
@@ -726,7 +1135,7 @@ Status level_cost(snnmap_hgraph* h, int32_t level, int32_t K, const int32_t* rho
 // round start.
 static Status refine_round(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* rho,
                            int32_t* moveidx, int32_t* n_props, int32_t* applied, int64_t* gain,
-                           int64_t* cost)
+                           int64_t* cost, int32_t* n_active, int32_t* rows)
 {
     cudaStream_t s = h->stream;
     Arena& ar = h->scratch;
@@ -735,6 +1144,8 @@ static Status refine_round(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* 
     const snnmap_params& prm = h->prm;
     int32_t V = L.V;
     *n_props = 0;
+    *n_active = 0;
+    *rows = 0;
     *applied = 0;
     *gain = 0;
     SNN_TRY(zero_scalars(h));
@@ -749,26 +1160,51 @@ static Status refine_round(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* 
         SNN_L k_check_pstate<<<grid_for(K, 256), 256, 0, s>>>(K, ps, prm.omega, prm.delta, prm.phi, h->d_scal);
         SNN_CUDA(cudaGetLastError());
     }
-    std::unique_ptr<ProfScope> prof(new ProfScope(h, PS_GAINS));
-
+    DenseRows& D = h->dense;
+    const bool dense = D.C && D.level == level;
+    std::unique_ptr<ProfScope> prof;
+    if (dense && D.pending) {
+        prof.reset(new ProfScope(h, PS_ROWS));
+        SNN_TRY(dense_fresh(h, L, pc));
+        D.pending = false;
+    }
     int32_t *pto, *flag, *pos;
-    int64_t* pgain;
+    int64_t *pgain, *savev, *Wv;
     SNN_TRY(ar.alloc(&pto, V));
     SNN_TRY(ar.alloc(&pgain, V));
     SNN_TRY(ar.alloc(&flag, V));
     SNN_TRY(ar.alloc(&pos, V));
-    if (h->wide) {
-        SNN_TRY(gains<unsigned long long>(h, L, pc, rho, ps, K, pto, pgain));
+    SNN_TRY(ar.alloc(&savev, V));
+    SNN_TRY(ar.alloc(&Wv, V));
+    prof.reset(new ProfScope(h, PS_SAVE));
+    SNN_CUDA(cudaMemsetAsync(savev, 0, (size_t)(V > 0 ? V : 1) * 8, s));
+    SNN_CUDA(cudaMemsetAsync(Wv, 0, (size_t)(V > 0 ? V : 1) * 8, s));
+    if (L.E > 0) {
+        SNN_L k_save<<<grid_for((int64_t)L.E * 32, 256), 256, 0, s>>>(L, pc, rho, savev, Wv);
+        SNN_CUDA(cudaGetLastError());
+    }
+    prof.reset(new ProfScope(h, PS_GAINS));
+    if (dense) {
+        if (V > 0) {
+            SNN_L k_dense_best<<<grid_for((int64_t)V * 32, 256), 256, 0, s>>>(
+                L, rho, ps, savev, Wv, D.rowid, D.C, D.O, D.Kp, K, prm.omega, prm.delta, prm.phi,
+                pto, pgain);
+            SNN_CUDA(cudaGetLastError());
+        }
+    } else if (h->wide) {
+        SNN_TRY(gains<unsigned long long>(h, L, pc, rho, ps, K, pto, pgain, savev));
     } else {
-        SNN_TRY(gains<uint32_t>(h, L, pc, rho, ps, K, pto, pgain));
+        SNN_TRY(gains<uint32_t>(h, L, pc, rho, ps, K, pto, pgain, savev));
     }
     int gv = grid_for(V, 256);
-    SNN_L k_prop_stats<<<gv, 256, 0, s>>>(L, pto, pgain, flag, h->d_scal);
+    SNN_L k_prop_stats<<<gv, 256, 0, s>>>(L, pto, pgain, savev, flag, h->d_scal);
     SNN_CUDA(cudaGetLastError());
     SNN_TRY(scan_exclusive_i32(flag, pos, V, (int32_t*)(h->d_scal + RS_M), ar, s));
     prof.reset();
     SNN_TRY(read_scalars(h));
     *cost = h->h_scal[RS_COST];
+    *n_active = (int32_t)h->h_scal[RS_ACT];
+    *rows = dense ? 1 : 0;
     if (h->h_scal[SC_STATUS] & ST_BADSTATE)
         return Status{SNNMAP_ERR_INVALID, "refinement input breaks a per-core limit"};
     int32_t M = (int32_t)(h->h_scal[RS_M] & 0xffffffff);
@@ -860,6 +1296,12 @@ static Status refine_round(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* 
     SNN_TRY(scan_inclusive_i32(dv, nviol, M, ar, s));
     SNN_L k_best1<<<gm, 256, 0, s>>>(M, G, nviol, h->d_scal);
     SNN_L k_best2<<<gm, 256, 0, s>>>(M, G, nviol, h->d_scal);
+    if (dense && L.E > 0) {
+        prof.reset(new ProfScope(h, PS_CROSS));
+        SNN_L k_dense_cross<<<grid_for((int64_t)L.E * 32, 256), 256, 0, s>>>(
+            L, pc, moveidx, mv, h->d_scal, D.rowid, D.C, D.O, D.Kp, mvbuf);
+        prof.reset(new ProfScope(h, PS_APPLY));
+    }
     SNN_L k_apply<<<gm, 256, 0, s>>>(M, mv, rho, moveidx, h->d_scal);
     SNN_CUDA(cudaGetLastError());
     prof.reset();
@@ -905,12 +1347,12 @@ Status refine_level(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* rho, in
     int64_t c = 0;
     bool have_cost = false;
     for (int32_t r = 0; st.ok() && r < h->prm.max_refine_rounds; r++) {
-        int32_t props = 0, applied = 0;
+        int32_t props = 0, applied = 0, act = 0, rows = 0;
         int64_t g = 0, c0 = 0;
-        st = refine_round(h, level, K, rho, moveidx, &props, &applied, &g, &c0);
+        st = refine_round(h, level, K, rho, moveidx, &props, &applied, &g, &c0, &act, &rows);
         h->scratch.reset();
         if (!st.ok()) break;
-        h->rlog.push_back(snnmap_round_log{level, r, props, applied, g});
+        h->rlog.push_back(snnmap_round_log{level, r, props, applied, act, rows, g});
         if (!have_cost && cost_start) *cost_start = c0;
         c = c0 - g;
         have_cost = true;

@@ -31,7 +31,7 @@ def test_coarsening_lockstep(name):
     assert n >= 1
 
 
-def _partition_both(hg, budget=None, **kw):
+def _partition_both(hg, budget=None, rows=None, **kw):
     from paper_2609_07577_gb300 import partition
     prm = oracle.params_of(hg, **kw)
     rho_o, cost_o, st_o, lv_o, rl_o = oracle.partition(hg, prm)
@@ -40,6 +40,8 @@ def _partition_both(hg, budget=None, **kw):
     try:
         if budget is not None:
             G.set_level_budget(budget)
+        if rows is not None:
+            G.set_row_budget(rows)
         rho, cost, st = G.partition()
         rl = G.round_logs()
         lv = G.level_logs()
@@ -48,15 +50,19 @@ def _partition_both(hg, budget=None, **kw):
     return (rho.cpu().numpy(), cost, st, lv, rl), (rho_o, cost_o, st_o, lv_o, rl_o)
 
 
-@pytest.mark.parametrize("name,budget", [("cfg1s", None), ("cfg1", None), ("cfg2s", None),
-                                         ("cfg3s", None), ("cfg1", 1), ("cfg3s", 1),
-                                         ("cfg2s", 4 << 20)])
-def test_partition_parity(name, budget):
+@pytest.mark.parametrize("name,budget,rows", [
+    ("cfg1s", None, None), ("cfg1", None, None), ("cfg2s", None, None), ("cfg3s", None, None),
+    ("cfg1", 1, None), ("cfg3s", 1, None), ("cfg2s", 4 << 20, None),
+    ("cfg1s", None, 0), ("cfg1", None, 0), ("cfg2s", None, 0), ("cfg3s", None, 0),
+    ("cfg1", None, 1 << 20), ("cfg2s", None, 1 << 20), ("cfg3s", None, 4 << 20)])
+def test_partition_parity(name, budget, rows):
     """budget=1 releases every intermediate level during coarsening, so
     uncoarsening rebuilds each one from level 0 through composed cid maps;
-    4 MiB keeps a stride of them."""
+    4 MiB keeps a stride of them. rows=None refines every level of these
+    sizes from connection rows, rows=0 from per-round histograms, and a few
+    MiB switches from rows to histograms partway down the hierarchy."""
     hg = snngen.by_name(name)
-    (rho, cost, st, lv, rl), (rho_o, cost_o, st_o, lv_o, rl_o) = _partition_both(hg, budget)
+    (rho, cost, st, lv, rl), (rho_o, cost_o, st_o, lv_o, rl_o) = _partition_both(hg, budget, rows)
     assert cost == cost_o
     assert np.array_equal(rho, rho_o)
     for k in ("levels", "n_parts", "nonempty_parts", "rounds", "moves", "cost_initial", "cost"):
