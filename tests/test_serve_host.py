@@ -130,6 +130,10 @@ def test_destroy_marks_queued_jobs():
     jobs = [HostJob(10) for _ in range(4)]
     for hj in jobs:
         N.snnmap_serve_submit(s, hj.job)
+    import time
+    t0 = time.time()
+    while N.snnmap_serve_info(s)[1] == 0 and time.time() - t0 < 10:
+        time.sleep(0.001)       # until the first job runs
     N.snnmap_serve_destroy(s)
     st = [hj.job.status for hj in jobs]
     assert st[0] == 0
