@@ -72,7 +72,9 @@ typedef struct {
     int32_t level, round;
     int32_t n_props;  /* vertices that proposed a move */
     int32_t istar;    /* length of the enacted prefix (0: none) */
-    int32_t n_active; /* vertices with save > 0, the only ones a move can gain on */
+    int32_t n_active; /* vertices whose best move was evaluated: save > 0 and, after a
+                         level's first round on the histogram path, affected by
+                         the previous round's moves */
     int32_t rows;     /* 1: gains read from connection rows (snnmap_set_row_budget) */
     int64_t gain;     /* Conn removed by the enacted prefix */
 } snnmap_round_log;
@@ -315,8 +317,10 @@ int snnmap_connectivity_noalloc(int32_t n_vertices, int32_t n_hedges, const int6
  * already reserved, or at once when nothing is reserved. A footprint stays
  * reserved while the job runs and, for jobs with keep_hierarchy set, until
  * snnmap_serve_release. Each job keeps at most about its level-0 size of
- * intermediate levels in memory (snnmap_set_level_budget), which bounds its
- * footprint; this changes no result.
+ * intermediate levels in memory (snnmap_set_level_budget) and gets 4 times
+ * its level-0 size plus 256 MiB for connection rows and the score matrix
+ * (snnmap_set_row_budget), which bounds its footprint; this changes no
+ * result.
  */
 typedef struct snnmap_server snnmap_server;
 

@@ -124,6 +124,7 @@ void snnmap_free(snnmap_hgraph* h)
     cudaStreamSynchronize(h->stream);
     snn::prof_release(h);
     snn::dense_close(h);
+    snn::mat_close(h);
     drop_levels_above(h, 0);
     h->scratch.release();
     if (h->cand) cudaFreeAsync(h->cand, h->stream);
@@ -282,6 +283,7 @@ int snnmap_partition(snnmap_hgraph* h, void* stream, int32_t* d_rho_out, int64_t
     if (!is_device_ptr(d_rho_out)) return fail(SNNMAP_ERR_INVALID, "d_rho_out must be device memory");
     bind(h, stream);
     drop_levels_above(h, 1);
+    snn::mat_close(h);
     h->keep_stride = 1;
     h->rlog.clear();
     h->llog.clear();
@@ -313,6 +315,7 @@ int snnmap_partition(snnmap_hgraph* h, void* stream, int32_t* d_rho_out, int64_t
     // rho of the current level lives in `cur`; projection writes `oth`
     int32_t* cur = ((nl - 1) % 2 == 0) ? d_rho_out : tmp;
     int32_t* oth = cur == d_rho_out ? tmp : d_rho_out;
+    snn::mat_close(h);
     snn::Status s2 = snn::iota_i32(cur, K, h->stream);
     // connection rows for the levels from the coarsest down to the finest one
     // whose rows fit the row budget (conn is stored in int32: needs the

@@ -315,7 +315,10 @@ Status coarsen_level(snnmap_hgraph* h, int32_t* n_cand, int32_t* n_pairs)
     if (V == 0) return Status{};
     {
         ProfScope prof(h, PS_AFFINITY);
-        if (h->wide) {
+        bool done = false;
+        SNN_TRY(mat_affinity(h, (int32_t)h->levels.size() - 1, &done));
+        if (done) {
+        } else if (h->wide) {
             SNN_TRY(affinity<unsigned long long>(h, L));
         } else {
             SNN_TRY(affinity<uint32_t>(h, L));

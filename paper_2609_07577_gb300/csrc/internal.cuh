@@ -48,6 +48,19 @@ struct DenseRows {
     int32_t level = -1;       // level the rows describe
     bool pending = false;     // fresh rows of this level not computed yet
 };
+
+// Neighbour score and shared inbound count of every vertex pair of the
+// coarsest level when it is small: S and OV are V x Vs int32 (Vs = V rounded
+// up to 4), S2/OV2 the buffers the next level is gathered into.
+struct ScoreMat {
+    int64_t cap = 0;   // entries per buffer
+    int64_t Vs = 0;
+    int32_t* S = nullptr;
+    int32_t* OV = nullptr;
+    int32_t* S2 = nullptr;
+    int32_t* OV2 = nullptr;
+    int32_t level = -1;   // level the matrix describes
+};
 }  // namespace snn
 
 struct snnmap_hgraph {
@@ -74,6 +87,7 @@ struct snnmap_hgraph {
     int64_t wsum = 0;            // sum of omega over the input hyperedges
     int64_t row_budget = -1;     // bytes for connection rows (-1: default, 0: none)
     snn::DenseRows dense;
+    snn::ScoreMat mat;
     std::vector<snnmap_round_log> rlog;
     std::vector<snnmap_level_log> llog;
     // profiler
@@ -140,6 +154,13 @@ void thin_levels(snnmap_hgraph* h);
 // S5
 Status project(snnmap_hgraph* h, int32_t level, const int32_t* rho_coarse, int32_t* rho_fine);
 // S6-S12 on one level; rho in place
+// score matrix: candidates of `level` from the matrix (built on the first
+// small level; *done false when the level is too large or memory short),
+// carried through a contraction of `src`, released
+Status mat_affinity(snnmap_hgraph* h, int32_t level, bool* done);
+Status mat_descend(snnmap_hgraph* h, int32_t src);
+void mat_close(snnmap_hgraph* h);
+
 // connection rows: allocation for `rows` vertices and K partitions; rows of
 // every vertex of `level` (the coarsest refined level) marked fresh; descent
 // from level+1 to `level` after projection; release

@@ -295,8 +295,9 @@ struct GainPol {
     int32_t* pto;
     int64_t* pgain;
     const int64_t* savev;
+    const int32_t* dirty;   // vertices to evaluate; the others keep pto/pgain
 
-    __device__ bool skip(int32_t n) const { return savev[n] == 0; }
+    __device__ bool skip(int32_t n) const { return savev[n] == 0 || !dirty[n]; }
     __device__ int64_t vb(int32_t n) const { return L.voff[n]; }
     __device__ int64_t ve(int32_t n) const { return L.voff[n + 1]; }
     __device__ int64_t seg_len(int64_t i) const
@@ -348,6 +349,7 @@ struct GainPol {
     }
     __device__ void write(int32_t n, int64_t bs, int32_t bk, uint32_t, const Acc&) const
     {
+        if (!dirty[n]) return;
         bool prop = bk >= 0 && bs > 0;
         pto[n] = prop ? bk : -1;
         pgain[n] = prop ? bs : 0;
@@ -632,17 +634,104 @@ __global__ void k_dense_zero(int32_t V, const int32_t* __restrict__ fresh,
 }
 
 // ---------------------------------------------------------------------------
+// Incremental rounds on histogram levels. After an enacted prefix, a
+// vertex's best move can change only if (a) one of its hyperedges holds a
+// moved pin (its conn, overlap and save change only there), (b) it is
+// adjacent to a partition that lost load (a source of an enacted move) and
+// was tight before -- a partition with room for the largest vertex of the
+// level in all three limits was feasible for every vertex before and still
+// is, and partitions that only gained load lose feasibility, which matters
+// only for (c) -- or (c) its proposed target changed state. Every other
+// vertex keeps its proposal, which a full evaluation would reproduce.
+
+__global__ void k_level_max(Level L, int32_t* vmax)
+{
+    int32_t a = 0, b = 0, c = 0;
+    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < L.V;
+         n += (int64_t)gridDim.x * blockDim.x) {
+        a = max(a, L.vsize[n]);
+        b = max(b, L.vinpins[n]);
+        c = max(c, L.vincnt[n]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a = max(a, __shfl_xor_sync(FULL, a, o));
+        b = max(b, __shfl_xor_sync(FULL, b, o));
+        c = max(c, __shfl_xor_sync(FULL, c, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&vmax[0], a);
+        atomicMax(&vmax[1], b);
+        atomicMax(&vmax[2], c);
+    }
+}
+
+// partitions touched by the enacted prefix (pchg) and the tight sources
+// among them (prel), with the round-start state
+__global__ void k_inc_parts(int32_t M, Moves mv, const int64_t* __restrict__ scal, PState ps,
+                            const int32_t* __restrict__ vmax, int32_t omega, int32_t delta,
+                            int32_t phi, uint8_t* pchg, uint8_t* prel)
+{
+    int64_t istar = scal[RS_BEST] > 0 ? scal[RS_ISTAR] : -1;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= istar && i < M;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t f = mv.from[i], t = mv.to[i];
+        pchg[f] = 1;
+        pchg[t] = 1;
+        if (ps.size[f] + vmax[0] > omega || ps.inpins[f] + vmax[1] > phi ||
+            ps.pincnt[f] + vmax[2] > delta)
+            prel[f] = 1;
+    }
+}
+
+// (a) and (b): every pin of a hyperedge holding an enacted moved pin or a
+// partition of prel (round-start pin counts) is marked
+__global__ void __launch_bounds__(256)
+    k_inc_hedges(Level L, PinCounts pc, const int32_t* __restrict__ moveidx,
+                 const int64_t* __restrict__ scal, const uint8_t* __restrict__ prel, int32_t* dirty)
+{
+    int64_t istar = scal[RS_BEST] > 0 ? scal[RS_ISTAR] : -1;
+    if (istar < 0) return;
+    int lane = threadIdx.x & 31;
+    int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t a = gw; a < L.E; a += nw) {
+        int64_t b = L.hoff[a], e = L.hoff[a + 1];
+        bool hit = false;
+        for (int64_t j = b + lane; j < e && !hit; j += 32) {
+            int32_t mi = moveidx[L.hpins[j]];
+            if (mi >= 0 && mi <= istar) hit = true;
+        }
+        int32_t lam = pc.lam[a];
+        for (int32_t r = lane; r < lam && !hit; r += 32)
+            if (prel[pc.p[b + r]]) hit = true;
+        if (!__any_sync(FULL, hit)) continue;
+        for (int64_t j = b + lane; j < e; j += 32) dirty[L.hpins[j]] = 1;
+    }
+}
+
+// (c)
+__global__ void k_inc_targets(int32_t V, const int32_t* __restrict__ pto,
+                              const uint8_t* __restrict__ pchg, int32_t* dirty)
+{
+    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < V;
+         n += (int64_t)gridDim.x * blockDim.x)
+        if (pto[n] >= 0 && pchg[pto[n]]) dirty[n] = 1;
+}
+
+// ---------------------------------------------------------------------------
 // S8
 
 __global__ void k_prop_stats(Level L, const int32_t* __restrict__ pto,
                              const int64_t* __restrict__ pgain,
-                             const int64_t* __restrict__ savev, int32_t* flag, int64_t* scal)
+                             const int64_t* __restrict__ savev,
+                             const int32_t* __restrict__ dirty, int32_t* flag, int64_t* scal)
 {
     int64_t mg = 0, deg = 0;
     int act = 0;
     for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < L.V;
          n += (int64_t)gridDim.x * blockDim.x) {
-        act += savev[n] > 0;
+        act += savev[n] > 0 && (!dirty || dirty[n]);
         int f = pto[n] >= 0;
         flag[n] = f;
         if (f) {
@@ -968,10 +1057,11 @@ __global__ void k_round_init(int64_t* scal) { scal[RS_ISTAR] = INT64_MAX; }
 template <typename S>
 static Status gains(snnmap_hgraph* h, Level& L, const PinCounts& pc, const int32_t* rho,
                     const PState& ps, int32_t K, int32_t* pto, int64_t* pgain,
-                    const int64_t* savev)
+                    const int64_t* savev, const int32_t* dirty)
 {
     GainPol<S> pol;
     pol.savev = savev;
+    pol.dirty = dirty;
     pol.L = L;
     pol.pc = pc;
     pol.ps = ps;
@@ -1131,11 +1221,24 @@ Status level_cost(snnmap_hgraph* h, int32_t level, int32_t K, const int32_t* rho
     return Status{};
 }
 
+// Per-level buffers that outlive a round: proposals (kept by vertices the
+// previous round did not touch), the vertices to evaluate, partition flags
+// and the level's largest vertex state.
+struct IncState {
+    int32_t* pto = nullptr;
+    int64_t* pgain = nullptr;
+    int32_t* dirty = nullptr;
+    uint8_t* pchg = nullptr;
+    uint8_t* prel = nullptr;
+    int32_t* vmax = nullptr;
+};
+
 // One round; *applied = moves enacted, *gain = Conn removed, *cost = Conn at
 // round start.
 static Status refine_round(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* rho,
-                           int32_t* moveidx, int32_t* n_props, int32_t* applied, int64_t* gain,
-                           int64_t* cost, int32_t* n_active, int32_t* rows)
+                           int32_t* moveidx, const IncState& inc, int32_t* n_props,
+                           int32_t* applied, int64_t* gain, int64_t* cost, int32_t* n_active,
+                           int32_t* rows)
 {
     cudaStream_t s = h->stream;
     Arena& ar = h->scratch;
@@ -1168,10 +1271,10 @@ static Status refine_round(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* 
         SNN_TRY(dense_fresh(h, L, pc));
         D.pending = false;
     }
-    int32_t *pto, *flag, *pos;
-    int64_t *pgain, *savev, *Wv;
-    SNN_TRY(ar.alloc(&pto, V));
-    SNN_TRY(ar.alloc(&pgain, V));
+    int32_t* pto = inc.pto;
+    int64_t* pgain = inc.pgain;
+    int32_t *flag, *pos;
+    int64_t *savev, *Wv;
     SNN_TRY(ar.alloc(&flag, V));
     SNN_TRY(ar.alloc(&pos, V));
     SNN_TRY(ar.alloc(&savev, V));
@@ -1192,12 +1295,13 @@ static Status refine_round(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* 
             SNN_CUDA(cudaGetLastError());
         }
     } else if (h->wide) {
-        SNN_TRY(gains<unsigned long long>(h, L, pc, rho, ps, K, pto, pgain, savev));
+        SNN_TRY(gains<unsigned long long>(h, L, pc, rho, ps, K, pto, pgain, savev, inc.dirty));
     } else {
-        SNN_TRY(gains<uint32_t>(h, L, pc, rho, ps, K, pto, pgain, savev));
+        SNN_TRY(gains<uint32_t>(h, L, pc, rho, ps, K, pto, pgain, savev, inc.dirty));
     }
     int gv = grid_for(V, 256);
-    SNN_L k_prop_stats<<<gv, 256, 0, s>>>(L, pto, pgain, savev, flag, h->d_scal);
+    SNN_L k_prop_stats<<<gv, 256, 0, s>>>(L, pto, pgain, savev, dense ? nullptr : inc.dirty, flag,
+                                          h->d_scal);
     SNN_CUDA(cudaGetLastError());
     SNN_TRY(scan_exclusive_i32(flag, pos, V, (int32_t*)(h->d_scal + RS_M), ar, s));
     prof.reset();
@@ -1302,6 +1406,19 @@ static Status refine_round(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* 
             L, pc, moveidx, mv, h->d_scal, D.rowid, D.C, D.O, D.Kp, mvbuf);
         prof.reset(new ProfScope(h, PS_APPLY));
     }
+    if (!dense) {
+        // vertices the enacted prefix can affect, for the next round
+        SNN_CUDA(cudaMemsetAsync(inc.dirty, 0, (size_t)(V > 0 ? V : 1) * 4, s));
+        SNN_CUDA(cudaMemsetAsync(inc.pchg, 0, (size_t)(K > 0 ? K : 1), s));
+        SNN_CUDA(cudaMemsetAsync(inc.prel, 0, (size_t)(K > 0 ? K : 1), s));
+        SNN_L k_inc_parts<<<gm, 256, 0, s>>>(M, mv, h->d_scal, ps, inc.vmax, prm.omega, prm.delta,
+                                             prm.phi, inc.pchg, inc.prel);
+        if (L.E > 0)
+            SNN_L k_inc_hedges<<<grid_for((int64_t)L.E * 32, 256), 256, 0, s>>>(
+                L, pc, moveidx, h->d_scal, inc.prel, inc.dirty);
+        SNN_L k_inc_targets<<<gv, 256, 0, s>>>(V, pto, inc.pchg, inc.dirty);
+        SNN_CUDA(cudaGetLastError());
+    }
     SNN_L k_apply<<<gm, 256, 0, s>>>(M, mv, rho, moveidx, h->d_scal);
     SNN_CUDA(cudaGetLastError());
     prof.reset();
@@ -1341,15 +1458,28 @@ Status refine_level(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* rho, in
                     int64_t* cost_start)
 {
     Level& L = h->levels[level];
+    cudaStream_t s = h->stream;
+    size_t nv = (size_t)(L.V > 0 ? L.V : 1), nk = (size_t)(K > 0 ? K : 1);
     int32_t* moveidx;
-    SNN_CUDA(cudaMallocAsync(&moveidx, (size_t)(L.V > 0 ? L.V : 1) * sizeof(int32_t), h->stream));
-    Status st = fill_i32(moveidx, -1, L.V, h->stream);
+    IncState inc;
+    SNN_CUDA(cudaMallocAsync(&moveidx, nv * sizeof(int32_t), s));
+    SNN_CUDA(cudaMallocAsync(&inc.pto, nv * 4, s));
+    SNN_CUDA(cudaMallocAsync(&inc.pgain, nv * 8, s));
+    SNN_CUDA(cudaMallocAsync(&inc.dirty, nv * 4, s));
+    SNN_CUDA(cudaMallocAsync(&inc.pchg, nk, s));
+    SNN_CUDA(cudaMallocAsync(&inc.prel, nk, s));
+    SNN_CUDA(cudaMallocAsync(&inc.vmax, 3 * 4, s));
+    SNN_CUDA(cudaMemsetAsync(inc.vmax, 0, 3 * 4, s));
+    if (L.V > 0) SNN_L k_level_max<<<grid_for(L.V, 256), 256, 0, s>>>(L, inc.vmax);
+    SNN_CUDA(cudaGetLastError());
+    Status st = fill_i32(moveidx, -1, L.V, s);
+    if (st.ok()) st = fill_i32(inc.dirty, 1, L.V, s);
     int64_t c = 0;
     bool have_cost = false;
     for (int32_t r = 0; st.ok() && r < h->prm.max_refine_rounds; r++) {
         int32_t props = 0, applied = 0, act = 0, rows = 0;
         int64_t g = 0, c0 = 0;
-        st = refine_round(h, level, K, rho, moveidx, &props, &applied, &g, &c0, &act, &rows);
+        st = refine_round(h, level, K, rho, moveidx, inc, &props, &applied, &g, &c0, &act, &rows);
         h->scratch.reset();
         if (!st.ok()) break;
         h->rlog.push_back(snnmap_round_log{level, r, props, applied, act, rows, g});
@@ -1358,7 +1488,10 @@ Status refine_level(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* rho, in
         have_cost = true;
         if (applied == 0) break;
     }
-    cudaFreeAsync(moveidx, h->stream);
+    cudaFreeAsync(moveidx, s);
+    for (void* p : {(void*)inc.pto, (void*)inc.pgain, (void*)inc.dirty, (void*)inc.pchg,
+                    (void*)inc.prel, (void*)inc.vmax})
+        cudaFreeAsync(p, s);
     if (!st.ok()) return st;
     if (!have_cost) {
         SNN_TRY(level_cost(h, level, K, rho, &c));

@@ -40,11 +40,16 @@ int64_t level_bytes(int64_t V, int64_t E, int64_t P)
 // the size of level 0), the intermediate levels kept under a budget of one
 // level 0, the scratch arena (sort buffers, pin counts and the hash-table
 // pools, which the histogram engine bounds by max(64 MiB, 4 bytes per pin)),
-// the per-vertex matching arrays, and a fixed allowance for the arena's
-// 64 MiB minimum chunk and the split tier's minimum pool.
+// the per-vertex matching arrays, a fixed allowance for the arena's 64 MiB
+// minimum chunk and the split tier's minimum pool, and the job's budget for
+// refinement connection rows and the coarsening score matrix.
 constexpr int64_t kFootLevels = 3;
 constexpr int64_t kFootScratch = 3;
 constexpr int64_t kFootFixed = (int64_t)160 << 20;
+
+// connection rows / score matrix memory granted to a job (part of its
+// footprint)
+int64_t job_row_budget(int64_t L0) { return 4 * L0 + ((int64_t)256 << 20); }
 
 int64_t input_bytes(int64_t V, int64_t E, int64_t P)
 {
@@ -54,7 +59,7 @@ int64_t input_bytes(int64_t V, int64_t E, int64_t P)
 int64_t footprint(int64_t V, int64_t E, int64_t P, bool on_host)
 {
     int64_t L0 = level_bytes(V, E, P);
-    int64_t f = (kFootLevels + kFootScratch) * L0 + 20 * V + kFootFixed;
+    int64_t f = (kFootLevels + kFootScratch) * L0 + 20 * V + kFootFixed + job_row_budget(L0);
     if (on_host) f += input_bytes(V, E, P);
     return f;
 }
@@ -155,7 +160,9 @@ void snnmap_server::run(Ticket* t, int slot)
         if (rc != SNNMAP_OK) msg = snnmap_last_error();
     }
     if (rc == SNNMAP_OK) {
-        snnmap_set_level_budget(h, level_bytes(j->n_vertices, j->n_hedges, h->levels[0].P));
+        int64_t L0 = level_bytes(j->n_vertices, j->n_hedges, h->levels[0].P);
+        snnmap_set_level_budget(h, L0);
+        snnmap_set_row_budget(h, job_row_budget(L0));
         rc = snnmap_partition(h, s, rho, &j->cost, &j->stats);
         if (rc != SNNMAP_OK) msg = snnmap_last_error();
     }
