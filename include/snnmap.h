@@ -257,6 +257,30 @@ int snnmap_stage_times(snnmap_hgraph* h, snnmap_stage_time* out, int32_t cap, in
 int snnmap_set_level_budget(snnmap_hgraph* h, int64_t bytes);
 
 /*
+ * The partition hypergraph G_P = (P, A, eta) of Sec. 3 ("Partitioning
+ * Definition") for a level-0 partition d_rho (device int32[V(0)], values in
+ * [0, n_parts)): every axon e is mapped through rho, its source's partition
+ * becoming the source and the other partitions of its pins the
+ * destinations (a destination in the source's partition is discarded, which
+ * breaks the self-cycle); axons with the same source partition and the same
+ * destination set merge, eta being their summed omega. An axon whose pins
+ * all lie in one partition keeps no destination and is left out of A; the
+ * sum of their omega is *internal_out (so sum(eta) + internal = sum(omega)).
+ * The result stays in the handle: *n_hedges_out = |A|, *n_pins_out = its
+ * pins; snnmap_partition_graph_copy fetches it. Errors: SNNMAP_ERR_INVALID
+ * (n_parts < 1, host d_rho, a value outside [0, n_parts)).
+ */
+int snnmap_partition_graph(snnmap_hgraph* h, int32_t n_parts, const int32_t* d_rho, void* stream,
+                           int32_t* n_hedges_out, int64_t* n_pins_out, int64_t* internal_out);
+/* Copies the last G_P into device buffers (any may be NULL): d_offsets
+ * int64[|A|+1], d_pins int32[pins] (per hyperedge: source partition, then
+ * destination partitions ascending), d_eta int64[|A|], d_axons int32[|A|]
+ * (axons merged into each). Hyperedge order is deterministic but otherwise
+ * unspecified. SNNMAP_ERR_STATE if no G_P was computed. */
+int snnmap_partition_graph_copy(const snnmap_hgraph* h, int64_t* d_offsets, int32_t* d_pins,
+                                int64_t* d_eta, int32_t* d_axons, void* stream);
+
+/*
  * Memory for connection rows in the refinement of snnmap_partition: for the
  * levels (from the coarsest down) whose vertices times the partitions fit in
  * `bytes` (8 bytes per vertex and partition), each vertex keeps its

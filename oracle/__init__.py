@@ -79,6 +79,8 @@ def lib():
             L.orc_contract.argtypes = [vp, vp, vp, vp, vp, C.POINTER(vp)]
             L.orc_contract.restype = C.c_int
             L.orc_conn.argtypes = [vp, vp]
+            L.orc_gp.restype = C.c_int
+            L.orc_gp.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
             L.orc_conn.restype = i64
             L.orc_refine.argtypes = [vp, i32, vp, vp, i32, vp, i32, vp, vp]
             L.orc_refine.restype = i32
@@ -180,6 +182,24 @@ class Level:
     def conn(self, rho) -> int:
         rho = np.ascontiguousarray(rho, np.int32)
         return int(lib().orc_conn(self._h, _ptr(rho)))
+
+    def partition_graph(self, rho):
+        """G_P of a partition of this level (R18): dict(off, pins, eta,
+        axons, internal), hyperedges in canonical order."""
+        V, E, P = self.dims()
+        rho = np.ascontiguousarray(rho, dtype=np.int32)
+        off = np.zeros(E + 1, np.int64)
+        pins = np.zeros(max(P, 1), np.int32)
+        eta = np.zeros(max(E, 1), np.int64)
+        axons = np.zeros(max(E, 1), np.int32)
+        ne, npins, inw = C.c_int32(), C.c_int64(), C.c_int64()
+        rc = _lib.orc_gp(self._h, _ptr(rho), _ptr(off), _ptr(pins), _ptr(eta), _ptr(axons),
+                         C.byref(ne), C.byref(npins), C.byref(inw))
+        if rc:
+            raise OracleError(rc)
+        e, p = ne.value, npins.value
+        return {"off": off[:e + 1], "pins": pins[:p], "eta": eta[:e], "axons": axons[:e],
+                "internal": inw.value}
 
     def refine(self, K, rho, prm: Params, level=0, log_cap=4096):
         """Refines ``rho`` in place; returns (rounds, moves, round logs)."""

@@ -38,6 +38,12 @@
  *  R13 Validity is evaluated after each whole move.
  *  R14 Refinement also runs on the coarsest level.
  *  R15 Partitions may end up empty; ids are those of the coarsest vertices.
+ *  R18 G_P (Sec. 3): the image of an axon keeps its direction: source
+ *      partition rho(src), destinations the other partitions of its pins
+ *      (a destination inside the source's partition is discarded). Axons
+ *      with equal (source, destination set) merge and eta sums their
+ *      omega; an axon left without destination is not in A and its omega
+ *      counts as internal weight.
  *
  * Error codes: 0 ok, 1 invalid input, 2 infeasible (one neuron alone breaks
  * a limit), 3 out of memory.
@@ -609,6 +615,76 @@ int orc_contract(const orc_level *L, const int32_t *match, const int32_t *cand, 
 oom:
     free(pool); free(tmp); free(rec); free(internal);
     return ORC_ERR_OOM;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Partition hypergraph G_P = (P, A, eta) of Sec. 3 ("Partitioning
+ * Definition"), R18: A = { rho(e) }, eta(a) = sum of omega(e) over the axons
+ * e with rho(e) = a. Output in canonical order (source, size, destination
+ * list); capacities: off E+1, pins P, eta and axons E (level 0's sizes). */
+int orc_gp(const orc_level *L, const int32_t *rho, int64_t *off, int32_t *pins, int64_t *eta,
+           int32_t *axons, int32_t *n_hedges, int64_t *n_pins, int64_t *internal)
+{
+    int32_t nrec = 0, E2 = 0;
+    int64_t poolpos = 0, maxlen = 0, P2 = 0, inw = 0;
+    int32_t *pool, *tmp;
+    hrec *rec;
+    for (int32_t a = 0; a < L->E; a++)
+        if (L->off[a + 1] - L->off[a] > maxlen) maxlen = L->off[a + 1] - L->off[a];
+    pool = (int32_t *)malloc(((size_t)L->P + 1) * sizeof(int32_t));
+    tmp = (int32_t *)malloc(((size_t)maxlen + 1) * sizeof(int32_t));
+    rec = (hrec *)malloc(((size_t)L->E + 1) * sizeof(hrec));
+    if (!pool || !tmp || !rec) {
+        free(pool); free(tmp); free(rec);
+        return ORC_ERR_OOM;
+    }
+    for (int32_t a = 0; a < L->E; a++) {
+        int32_t s2 = rho[L->pins[L->off[a]]];
+        int32_t nd = 0, len = 0;
+        for (int64_t j = L->off[a] + 1; j < L->off[a + 1]; j++) tmp[nd++] = rho[L->pins[j]];
+        qsort(tmp, (size_t)nd, sizeof(int32_t), cmp_i32);
+        for (int32_t i = 0; i < nd; i++) {
+            if (i > 0 && tmp[i] == tmp[i - 1]) continue;
+            if (tmp[i] == s2) continue;            /* self-cycle broken */
+            pool[poolpos + len++] = tmp[i];
+        }
+        if (len == 0) {
+            inw += L->w[a];
+            continue;
+        }
+        rec[nrec].s = s2; rec[nrec].sd = 0; rec[nrec].len = len;
+        rec[nrec].start = poolpos; rec[nrec].w = L->w[a]; rec[nrec].k = L->k[a];
+        nrec++;
+        poolpos += len;
+    }
+    g_pool = pool;
+    qsort(rec, (size_t)nrec, sizeof(hrec), cmp_hrec);
+    {
+        int32_t i = 0;
+        while (i < nrec) {
+            int32_t j = i + 1;
+            int64_t w = rec[i].w, k = rec[i].k;
+            while (j < nrec && cmp_hrec(&rec[i], &rec[j]) == 0) {
+                w += rec[j].w;
+                k += rec[j].k;
+                j++;
+            }
+            off[E2] = P2;
+            pins[P2++] = rec[i].s;
+            memcpy(pins + P2, pool + rec[i].start, (size_t)rec[i].len * sizeof(int32_t));
+            P2 += rec[i].len;
+            eta[E2] = w;
+            axons[E2] = (int32_t)k;
+            E2++;
+            i = j;
+        }
+        off[E2] = P2;
+    }
+    *n_hedges = E2;
+    *n_pins = P2;
+    *internal = inw;
+    free(pool); free(tmp); free(rec);
+    return ORC_OK;
 }
 
 /* ------------------------------------------------------------------------ */

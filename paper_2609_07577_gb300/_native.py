@@ -95,6 +95,9 @@ _SIGS = {
     "snnmap_launch_count": (_i64, []),
     "snnmap_set_level_budget": (C.c_int, [_vp, _i64]),
     "snnmap_set_row_budget": (C.c_int, [_vp, _i64]),
+    "snnmap_partition_graph": (C.c_int, [_vp, _i32, _vp, _vp, C.POINTER(_i32), C.POINTER(_i64),
+                                         C.POINTER(_i64)]),
+    "snnmap_partition_graph_copy": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "snnmap_connectivity_noalloc": (C.c_int, [_i32, _i32, _vp, _vp, _vp, _vp, _i32, _vp, _vp]),
     "snnmap_peak_bytes": (C.c_int, [_vp, C.POINTER(_i64)]),
     "snnmap_job_footprint": (C.c_int, [_i32, _i32, _i64, _i32, C.POINTER(_i64)]),
@@ -349,6 +352,20 @@ def snnmap_batch_partition(jobs, slots=0, mem_budget=0, dry_run_us=0):
     statuses are in the structs)."""
     o = ServeOpts(int(slots), int(dry_run_us), int(mem_budget))
     return lib().snnmap_batch_partition(jobs, len(jobs), C.byref(o))
+
+
+def snnmap_partition_graph(h, n_parts, d_rho, stream=None):
+    """Computes G_P; returns (n_hedges, n_pins, internal_weight)."""
+    e, p, w = C.c_int32(), C.c_int64(), C.c_int64()
+    check(lib().snnmap_partition_graph(h, int(n_parts), _p(d_rho), _stream(stream), C.byref(e),
+                                       C.byref(p), C.byref(w)))
+    return e.value, p.value, w.value
+
+
+def snnmap_partition_graph_copy(h, d_offsets=None, d_pins=None, d_eta=None, d_axons=None,
+                                stream=None):
+    check(lib().snnmap_partition_graph_copy(h, _p(d_offsets), _p(d_pins), _p(d_eta), _p(d_axons),
+                                            _stream(stream)))
 
 
 def snnmap_set_row_budget(h, nbytes):

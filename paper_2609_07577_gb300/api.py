@@ -116,6 +116,19 @@ class HGraph:
     def level_logs(self):
         return N.snnmap_level_logs(self._h)
 
+    def partition_graph(self, rho, n_parts):
+        """G_P of a level-0 partition (device tensor rho) as numpy arrays:
+        dict(off, pins, eta, axons, internal)."""
+        E, P, internal = N.snnmap_partition_graph(self._h, n_parts, rho, self.stream)
+        off = torch.empty(E + 1, dtype=torch.int64, device="cuda")
+        pins = torch.empty(max(P, 1), dtype=torch.int32, device="cuda")
+        eta = torch.empty(max(E, 1), dtype=torch.int64, device="cuda")
+        axons = torch.empty(max(E, 1), dtype=torch.int32, device="cuda")
+        N.snnmap_partition_graph_copy(self._h, off, pins, eta, axons, self.stream)
+        return {"off": off.cpu().numpy(), "pins": pins[:P].cpu().numpy(),
+                "eta": eta[:E].cpu().numpy(), "axons": axons[:E].cpu().numpy(),
+                "internal": internal}
+
     def set_row_budget(self, nbytes):
         """Bytes for refinement connection rows (-1 default, 0 none)."""
         N.snnmap_set_row_budget(self._h, nbytes)

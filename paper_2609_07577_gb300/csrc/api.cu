@@ -125,6 +125,7 @@ void snnmap_free(snnmap_hgraph* h)
     snn::prof_release(h);
     snn::dense_close(h);
     snn::mat_close(h);
+    snn::gp_free(h);
     drop_levels_above(h, 0);
     h->scratch.release();
     if (h->cand) cudaFreeAsync(h->cand, h->stream);
@@ -549,6 +550,46 @@ int snnmap_peak_bytes(const snnmap_hgraph* h, int64_t* bytes)
     if (!h || !bytes) return fail(SNNMAP_ERR_INVALID, "NULL argument");
     snn::note_bytes(const_cast<snnmap_hgraph*>(h));
     *bytes = h->peak_bytes;
+    return SNNMAP_OK;
+}
+
+int snnmap_partition_graph(snnmap_hgraph* h, int32_t n_parts, const int32_t* d_rho, void* stream,
+                           int32_t* n_hedges_out, int64_t* n_pins_out, int64_t* internal_out)
+{
+    g_err.clear();
+    if (!h || !h->levels.size() || n_parts < 1) return fail(SNNMAP_ERR_INVALID, "bad arguments");
+    if (h->levels[0].V > 0 && !is_device_ptr(d_rho))
+        return fail(SNNMAP_ERR_INVALID, "d_rho must be device memory");
+    bind(h, stream);
+    API_TRY(snn::check_rho(h, 0, n_parts, d_rho));
+    API_TRY(snn::emit_gp(h, n_parts, d_rho));
+    if (n_hedges_out) *n_hedges_out = h->gp.E;
+    if (n_pins_out) *n_pins_out = h->gp.P;
+    if (internal_out) *internal_out = h->gp.internal;
+    return SNNMAP_OK;
+}
+
+int snnmap_partition_graph_copy(const snnmap_hgraph* h, int64_t* d_offsets, int32_t* d_pins,
+                                int64_t* d_eta, int32_t* d_axons, void* stream)
+{
+    g_err.clear();
+    if (!h || !h->gp.hoff) return fail(SNNMAP_ERR_STATE, "no partition graph computed");
+    const snn::GpOut& G = h->gp;
+    cudaStream_t s = (cudaStream_t)stream;
+    struct Item {
+        void* dst;
+        const void* src;
+        size_t bytes;
+    } items[] = {{d_offsets, G.hoff, ((size_t)G.E + 1) * 8}, {d_pins, G.hpins, (size_t)G.P * 4},
+                 {d_eta, G.eta, (size_t)G.E * 8}, {d_axons, G.axons, (size_t)G.E * 4}};
+    for (auto& it : items) {
+        if (!it.dst || it.bytes == 0) continue;
+        if (!is_device_ptr(it.dst)) return fail(SNNMAP_ERR_INVALID, "outputs must be device memory");
+        cudaError_t e = cudaMemcpyAsync(it.dst, it.src, it.bytes, cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return fail(SNNMAP_ERR_CUDA, cudaGetErrorString(e));
+    }
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(SNNMAP_ERR_CUDA, cudaGetErrorString(e));
     return SNNMAP_OK;
 }
 

@@ -97,7 +97,9 @@ struct ContractJob {
     int32_t* tlen;
     uint8_t* tsd;
     uint32_t* thash;
-    int32_t* inint_next;
+    int32_t* inint_next;     // may be null (nothing recorded for dropped hyperedges)
+    bool discard_self = false;   // G_P: a destination in the source's part is discarded
+                                 // without marking selfdst
     __device__ int len(int32_t a) const { return (int)(hoff[a + 1] - hoff[a] - 1); }
     __device__ uint32_t load(int32_t a, int i) const
     {
@@ -109,7 +111,7 @@ struct ContractJob {
         int64_t base = hoff[a];
         uint32_t sp = (uint32_t)cid[hpins[base]];
         int cnt = 0;
-        int sd = hsd[a];
+        int sd = discard_self ? 0 : hsd[a];
         uint64_t hsum = 0;
         unsigned lt = lanemask_lt();
         for (int c = 0; c < n; c += 32) {
@@ -125,14 +127,14 @@ struct ContractJob {
                 hsum += mix64(v);
             }
             cnt += __popc(mk);
-            if (__any_sync(FULL, self)) sd = 1;
+            if (__any_sync(FULL, self) && !discard_self) sd = 1;
         }
         hsum = warp_sum(hsum);
         if (lane == 0) {
             tpins[base] = (int32_t)sp;
             if (cnt == 0) {
                 tlen[a] = 0;
-                if (sd) atomicAdd(&inint_next[sp], hk[a]);
+                if (sd && inint_next) atomicAdd(&inint_next[sp], hk[a]);
             } else {
                 tlen[a] = 1 + cnt;
                 tsd[a] = (uint8_t)sd;
@@ -145,13 +147,13 @@ struct ContractJob {
     {
         int64_t base = hoff[a];
         uint32_t sp = (uint32_t)cid[hpins[base]];
-        int cnt = 0, sd = hsd[a];
+        int cnt = 0, sd = discard_self ? 0 : hsd[a];
         uint64_t hsum = 0;
         for (int i = 0; i < n; i++) {
             uint32_t v = s[i];
             if (i > 0 && s[i - 1] == v) continue;
             if (v == sp) {
-                sd = 1;
+                if (!discard_self) sd = 1;
                 continue;
             }
             tpins[base + 1 + cnt++] = (int32_t)v;
@@ -160,7 +162,7 @@ struct ContractJob {
         tpins[base] = (int32_t)sp;
         if (cnt == 0) {
             tlen[a] = 0;
-            if (sd) atomicAdd(&inint_next[sp], hk[a]);
+            if (sd && inint_next) atomicAdd(&inint_next[sp], hk[a]);
         } else {
             tlen[a] = 1 + cnt;
             tsd[a] = (uint8_t)sd;
@@ -426,6 +428,125 @@ Status contract_level(snnmap_hgraph* h)
         ProfScope prof(h, PS_AFFINITY);
         SNN_TRY(mat_descend(h, src));
     }
+    return Status{};
+}
+
+// ---------------------------------------------------------------------------
+// G_P (Sec. 3, Partitioning Definition): the image of every axon under rho,
+// the source's partition as source, the other partitions of its pins as
+// destinations (a destination in the source's partition is discarded, which
+// breaks the self-cycle); axons with equal images merge and eta sums their
+// omega. An axon whose pins all share one partition keeps no destination:
+// it is left out of A and its omega reported as internal weight.
+
+__global__ void k_gp_internal(int32_t E, const int32_t* __restrict__ tlen,
+                              const int64_t* __restrict__ hw, int64_t* out)
+{
+    int64_t w = 0;
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < E;
+         a += (int64_t)gridDim.x * blockDim.x)
+        if (tlen[a] == 0) w += hw[a];
+    w = warp_sum(w);
+    if ((threadIdx.x & 31) == 0 && w) atomicAdd((unsigned long long*)out, (unsigned long long)w);
+}
+
+void gp_free(snnmap_hgraph* h)
+{
+    GpOut& G = h->gp;
+    for (void* p : {(void*)G.hoff, (void*)G.hpins, (void*)G.eta, (void*)G.axons, (void*)G.hsd})
+        if (p) cudaFreeAsync(p, h->stream);
+    G = GpOut{};
+}
+
+Status emit_gp(snnmap_hgraph* h, int32_t K, const int32_t* rho)
+{
+    cudaStream_t s = h->stream;
+    Arena& ar = h->scratch;
+    gp_free(h);
+    SNN_TRY(ensure_resident(h, 0));
+    Level& L = h->levels[0];
+    LevelExtra& X = h->extra[0];
+    int32_t E = L.E;
+    SNN_TRY(zero_scalars(h));
+    int32_t *tpins, *tlen;
+    uint8_t* tsd;
+    uint32_t* thash;
+    SNN_TRY(ar.alloc(&tpins, L.P));
+    SNN_TRY(ar.alloc(&tlen, E));
+    SNN_TRY(ar.alloc(&tsd, E));
+    SNN_TRY(ar.alloc(&thash, E));
+    ContractJob job{L.hoff, L.hpins, L.hsd, L.hk, rho, tpins, tlen, tsd, thash, nullptr, true};
+    SNN_TRY(seg_run(job, X.seg, E, ar, s));
+
+    uint64_t *keys, *keys2;
+    uint32_t *vals, *vals2;
+    int32_t *headpos, *runstart, *rep, *head, *gidh, *gid, *tk;
+    int64_t *tw, *newlen, *newoff;
+    SNN_TRY(ar.alloc(&keys, E));
+    SNN_TRY(ar.alloc(&keys2, E));
+    SNN_TRY(ar.alloc(&vals, E));
+    SNN_TRY(ar.alloc(&vals2, E));
+    SNN_TRY(ar.alloc(&headpos, E));
+    SNN_TRY(ar.alloc(&runstart, E));
+    SNN_TRY(ar.alloc(&rep, E));
+    SNN_TRY(ar.alloc(&head, E));
+    SNN_TRY(ar.alloc(&gidh, E));
+    SNN_TRY(ar.alloc(&gid, E));
+    SNN_TRY(ar.alloc(&tk, E));
+    SNN_TRY(ar.alloc(&tw, E));
+    SNN_TRY(ar.alloc(&newlen, E));
+    SNN_TRY(ar.alloc(&newoff, E));
+    int ge = grid_for(E, 256);
+    if (E > 0) {
+        SNN_L k_gp_internal<<<ge, 256, 0, s>>>(E, tlen, L.hw, h->d_scal + SC_D);
+        SNN_L k_dedup_keys<<<ge, 256, 0, s>>>(E, tlen, L.hoff, tpins, thash, (uint64_t)K, keys, vals);
+        SNN_CUDA(cudaGetLastError());
+        SNN_TRY(radix_sort_pairs(keys, vals, keys2, vals2, E, 32 + bits_for((uint64_t)K), ar, s));
+        SNN_L k_run_heads<<<ge, 256, 0, s>>>(E, keys, headpos);
+        SNN_CUDA(cudaGetLastError());
+    }
+    SNN_TRY(scan_inclusive_max_i32(headpos, runstart, E, ar, s));
+    if (E > 0) {
+        SNN_L k_dedup_rep<<<ge, 256, 0, s>>>(E, keys, vals, runstart, L.hoff, tpins, tlen, tsd, rep, head);
+        SNN_CUDA(cudaGetLastError());
+    }
+    SNN_TRY(scan_exclusive_i32(head, gidh, E, (int32_t*)(h->d_scal + SC_B), ar, s));
+    if (E > 0) {
+        SNN_CUDA(cudaMemsetAsync(tw, 0, (size_t)E * sizeof(int64_t), s));
+        SNN_CUDA(cudaMemsetAsync(tk, 0, (size_t)E * sizeof(int32_t), s));
+        SNN_CUDA(cudaMemsetAsync(newlen, 0, (size_t)E * sizeof(int64_t), s));
+        SNN_L k_dedup_accum<<<ge, 256, 0, s>>>(E, vals, rep, gidh, tlen, L.hw, L.hk, tw, tk, newlen, gid);
+        SNN_CUDA(cudaGetLastError());
+    }
+    SNN_TRY(scan_exclusive_i64(newlen, newoff, E, h->d_scal + SC_C, ar, s));
+    SNN_TRY(read_scalars(h));
+    int32_t E2 = (int32_t)(h->h_scal[SC_B] & 0xffffffff);
+    int64_t P2 = h->h_scal[SC_C];
+    GpOut& G = h->gp;
+    SNN_CUDA(cudaMallocAsync(&G.hoff, ((size_t)E2 + 1) * 8, s));
+    SNN_CUDA(cudaMallocAsync(&G.hpins, (size_t)(P2 > 0 ? P2 : 1) * 4, s));
+    SNN_CUDA(cudaMallocAsync(&G.eta, (size_t)(E2 > 0 ? E2 : 1) * 8, s));
+    SNN_CUDA(cudaMallocAsync(&G.axons, (size_t)(E2 > 0 ? E2 : 1) * 4, s));
+    SNN_CUDA(cudaMallocAsync(&G.hsd, (size_t)(E2 > 0 ? E2 : 1), s));
+    G.E = E2;
+    G.P = P2;
+    G.K = K;
+    G.internal = h->h_scal[SC_D];
+    Level N;
+    N.hoff = G.hoff;
+    N.hpins = G.hpins;
+    N.hsd = G.hsd;
+    N.hw = G.eta;
+    N.hk = G.axons;
+    if (E > 0) {
+        SNN_L k_dedup_emit<<<grid_for((int64_t)E * 32, 256), 256, 0, s>>>(
+            E, vals, rep, gid, L.hoff, tpins, tlen, tsd, tw, tk, newoff, N);
+        SNN_CUDA(cudaGetLastError());
+    }
+    SNN_L k_set_off_end<<<1, 1, 0, s>>>(G.hoff, E2, P2);
+    SNN_CUDA(cudaGetLastError());
+    SNN_CUDA(cudaStreamSynchronize(s));
+    ar.reset();
     return Status{};
 }
 

@@ -61,6 +61,18 @@ struct ScoreMat {
     int32_t* OV2 = nullptr;
     int32_t level = -1;   // level the matrix describes
 };
+
+// The partition hypergraph G_P of the last snnmap_partition_graph call.
+struct GpOut {
+    int64_t* hoff = nullptr;
+    int32_t* hpins = nullptr;
+    int64_t* eta = nullptr;
+    int32_t* axons = nullptr;
+    uint8_t* hsd = nullptr;
+    int32_t E = 0, K = 0;
+    int64_t P = 0;
+    int64_t internal = 0;
+};
 }  // namespace snn
 
 struct snnmap_hgraph {
@@ -88,6 +100,7 @@ struct snnmap_hgraph {
     int64_t row_budget = -1;     // bytes for connection rows (-1: default, 0: none)
     snn::DenseRows dense;
     snn::ScoreMat mat;
+    snn::GpOut gp;
     std::vector<snnmap_round_log> rlog;
     std::vector<snnmap_level_log> llog;
     // profiler
@@ -154,6 +167,10 @@ void thin_levels(snnmap_hgraph* h);
 // S5
 Status project(snnmap_hgraph* h, int32_t level, const int32_t* rho_coarse, int32_t* rho_fine);
 // S6-S12 on one level; rho in place
+// G_P of a level-0 partition (kept in h->gp until the next call or free)
+Status emit_gp(snnmap_hgraph* h, int32_t K, const int32_t* rho);
+void gp_free(snnmap_hgraph* h);
+
 // score matrix: candidates of `level` from the matrix (built on the first
 // small level; *done false when the level is too large or memory short),
 // carried through a contraction of `src`, released
