@@ -283,7 +283,8 @@ int snnmap_partition_graph_copy(const snnmap_hgraph* h, int64_t* d_offsets, int3
 /*
  * Memory for connection rows in the refinement of snnmap_partition: for the
  * levels (from the coarsest down) whose vertices times the partitions fit in
- * `bytes` (8 bytes per vertex and partition), each vertex keeps its
+ * `bytes` (8 bytes per vertex and partition) and which merged at most an
+ * eighth of their vertices into pairs, each vertex keeps its
  * connection weight and inbound overlap to every partition, updated as moves
  * are enacted and carried to the next finer level, instead of a histogram
  * per round. -1: the default, 1/8 of the device's memory; 0: none. Results do

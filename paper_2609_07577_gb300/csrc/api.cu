@@ -320,13 +320,21 @@ int snnmap_partition(snnmap_hgraph* h, void* stream, int32_t* d_rho_out, int64_t
     snn::Status s2 = snn::iota_i32(cur, K, h->stream);
     // connection rows for the levels from the coarsest down to the finest one
     // whose rows fit the row budget (conn is stored in int32: needs the
-    // summed omega below 2^31); without room the levels use histograms
+    // summed omega below 2^31) and that re-create at most a quarter of their
+    // rows on descent (2 x pairs <= V / 4; levels merging more pairs pay a
+    // histogram per fresh row and gain little over incremental histogram
+    // rounds); the finer levels use histograms
     int32_t ld = nl;
     {
         int64_t rb = snn::dense_row_budget(h);
         int64_t per = ((((int64_t)K + 3) & ~(int64_t)3) * 8 + 12);
         if (rb > 0 && !h->wide && h->wsum <= INT32_MAX)
-            for (int32_t l = nl - 1; l >= 0 && (int64_t)h->levels[l].V * per <= rb; l--) ld = l;
+            for (int32_t l = nl - 1; l >= 0; l--) {
+                int64_t V = h->levels[l].V;
+                int64_t fresh = l + 1 < nl ? 2 * (V - h->levels[l + 1].V) : 0;
+                if (V * per > rb || 4 * fresh > V) break;
+                ld = l;
+            }
         if (ld < nl && !snn::dense_open(h, K, h->levels[ld].V).ok()) {
             snn::dense_close(h);
             cudaGetLastError();

@@ -382,14 +382,14 @@ struct BuildCheckJob {
         }
         if (__any_sync(FULL, bad) && lane == 0) atomicOr((int*)&scal[SC_STATUS], ST_INVALID);
     }
-    __device__ void finish_thread(int32_t a, const uint32_t* s, int n) const
+    __device__ void finish_thread(int32_t a, const uint32_t* s, int n, int st) const
     {
         int64_t base = hoff[a];
         uint32_t src = (uint32_t)pins[base];
         int bad = 0;
         for (int i = 0; i < n; i++) {
-            if ((i > 0 && s[i - 1] == s[i]) || s[i] == src) bad = 1;
-            pins[base + 1 + i] = (int32_t)s[i];
+            if ((i > 0 && s[(i - 1) * st] == s[(i) * st]) || s[(i) * st] == src) bad = 1;
+            pins[base + 1 + i] = (int32_t)s[(i) * st];
         }
         if (bad) atomicOr((int*)&scal[SC_STATUS], ST_INVALID);
     }

@@ -58,6 +58,7 @@ struct AffPol {
     int64_t* cscore;
     int32_t* cov;
     const int32_t* vmin;   // smallest size and inbound pins over the level's vertices
+    bool prefilter;        // some pair can break Omega or Phi (else elem skips the test)
 
     // n cannot merge even with the smallest vertex: no candidate
     __device__ bool skip(int32_t n) const
@@ -91,7 +92,8 @@ struct AffPol {
         if (m == n) return true;
         // a neighbour whose size or inbound pins alone break Omega or Phi
         // with n can never be the candidate: leave it out of the table
-        if ((int64_t)L.vsize[n] + L.vsize[m] > omega || (int64_t)L.vinpins[n] + L.vinpins[m] > phi)
+        if (prefilter && ((int64_t)L.vsize[n] + L.vsize[m] > omega ||
+                          (int64_t)L.vinpins[n] + L.vinpins[m] > phi))
             return true;
         int md = off != 0 || g.sd;   // pin 0 is the source
         return t.add(m, g.w, (g.nd && md) ? g.k : 0u);
@@ -253,22 +255,29 @@ __global__ void k_match_finish(int32_t V, const int32_t* __restrict__ cand,
 
 // ---------------------------------------------------------------------------
 
-__global__ void k_level_min(Level L, int32_t* vmin)
+// vm[0], vm[1]: smallest size and inbound pins; vm[2], vm[3]: largest
+__global__ void k_level_min(Level L, int32_t* vm)
 {
-    int32_t ms = 0x7fffffff, mi = 0x7fffffff;
+    int32_t ms = 0x7fffffff, mi = 0x7fffffff, xs = 0, xi = 0;
     for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < L.V;
          n += (int64_t)gridDim.x * blockDim.x) {
         ms = min(ms, L.vsize[n]);
         mi = min(mi, L.vinpins[n]);
+        xs = max(xs, L.vsize[n]);
+        xi = max(xi, L.vinpins[n]);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         ms = min(ms, __shfl_xor_sync(FULL, ms, o));
         mi = min(mi, __shfl_xor_sync(FULL, mi, o));
+        xs = max(xs, __shfl_xor_sync(FULL, xs, o));
+        xi = max(xi, __shfl_xor_sync(FULL, xi, o));
     }
     if ((threadIdx.x & 31) == 0) {
-        atomicMin(&vmin[0], ms);
-        atomicMin(&vmin[1], mi);
+        atomicMin(&vm[0], ms);
+        atomicMin(&vm[1], mi);
+        atomicMax(&vm[2], xs);
+        atomicMax(&vm[3], xi);
     }
 }
 
@@ -276,12 +285,17 @@ template <typename S>
 static Status affinity(snnmap_hgraph* h, Level& L)
 {
     int32_t* vmin;
-    SNN_TRY(h->scratch.alloc(&vmin, 2));
+    SNN_TRY(h->scratch.alloc(&vmin, 4));
     SNN_TRY(fill_i32(vmin, 0x7fffffff, 2, h->stream));
+    SNN_CUDA(cudaMemsetAsync(vmin + 2, 0, 2 * sizeof(int32_t), h->stream));
     SNN_L k_level_min<<<grid_for(L.V, 256), 256, 0, h->stream>>>(L, vmin);
     SNN_CUDA(cudaGetLastError());
+    int32_t vm[4];
+    SNN_CUDA(cudaMemcpyAsync(vm, vmin, sizeof(vm), cudaMemcpyDeviceToHost, h->stream));
+    SNN_CUDA(cudaStreamSynchronize(h->stream));
     AffPol<S> pol;
     pol.vmin = vmin;
+    pol.prefilter = 2 * (int64_t)vm[2] > h->prm.omega || 2 * (int64_t)vm[3] > h->prm.phi;
     pol.L = L;
     pol.V = L.V;
     pol.keys = L.V;

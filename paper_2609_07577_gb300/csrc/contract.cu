@@ -143,15 +143,15 @@ struct ContractJob {
             }
         }
     }
-    __device__ void finish_thread(int32_t a, const uint32_t* s, int n) const
+    __device__ void finish_thread(int32_t a, const uint32_t* s, int n, int st) const
     {
         int64_t base = hoff[a];
         uint32_t sp = (uint32_t)cid[hpins[base]];
         int cnt = 0, sd = discard_self ? 0 : hsd[a];
         uint64_t hsum = 0;
         for (int i = 0; i < n; i++) {
-            uint32_t v = s[i];
-            if (i > 0 && s[i - 1] == v) continue;
+            uint32_t v = s[(i) * st];
+            if (i > 0 && s[(i - 1) * st] == v) continue;
             if (v == sp) {
                 if (!discard_self) sd = 1;
                 continue;

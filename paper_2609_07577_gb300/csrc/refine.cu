@@ -88,6 +88,18 @@ Status project(snnmap_hgraph* h, int32_t level, const int32_t* rho_coarse, int32
 // ---------------------------------------------------------------------------
 // S6
 
+// Conn is summed into COST_SLOTS partial sums (hyperedge id modulo) rather
+// than one word, so the per-hyperedge atomics do not all meet on one address
+constexpr int COST_SLOTS = 256;
+
+__global__ void k_cost_slots(const int64_t* __restrict__ slots, int64_t* out)
+{
+    int64_t v = 0;
+    for (int i = threadIdx.x; i < COST_SLOTS; i += blockDim.x) v += slots[i];
+    v = warp_sum(v);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd((unsigned long long*)out, (unsigned long long)v);
+}
+
 struct PinCountJob {
     const int64_t* hoff;
     const int32_t* hpins;
@@ -97,7 +109,7 @@ struct PinCountJob {
     const int32_t* rho;
     PinCounts pc;
     int64_t* pincnt;
-    int64_t* scal;
+    int64_t* cost;     // COST_SLOTS partial sums of Conn
     __device__ int len(int32_t a) const { return (int)(hoff[a + 1] - hoff[a]); }
     __device__ uint32_t load(int32_t a, int i) const
     {
@@ -151,36 +163,36 @@ struct PinCountJob {
         }
         if (lane == 0) {
             pc.lam[a] = R;
-            if (R > 1) atomicAdd((unsigned long long*)&scal[RS_COST], (unsigned long long)(hw[a] * (R - 1)));
+            if (R > 1) atomicAdd((unsigned long long*)&cost[a & (COST_SLOTS - 1)], (unsigned long long)(hw[a] * (R - 1)));
         }
     }
-    __device__ void finish_thread(int32_t a, const uint32_t* s, int n) const
+    __device__ void finish_thread(int32_t a, const uint32_t* s, int n, int st) const
     {
         int64_t base = hoff[a];
         int R = 0, c = 0, d = 0;
         for (int i = 0; i < n; i++) {
-            uint32_t p = s[i] >> 1;
-            if (i > 0 && p != (s[i - 1] >> 1)) {
-                pc.p[base + R] = (int32_t)(s[i - 1] >> 1);
+            uint32_t p = s[(i) * st] >> 1;
+            if (i > 0 && p != (s[(i - 1) * st] >> 1)) {
+                pc.p[base + R] = (int32_t)(s[(i - 1) * st] >> 1);
                 pc.cnt[base + R] = c;
                 pc.dcnt[base + R] = d;
-                if (d > 0) atomicAdd((unsigned long long*)&pincnt[s[i - 1] >> 1], (unsigned long long)hk[a]);
+                if (d > 0) atomicAdd((unsigned long long*)&pincnt[s[(i - 1) * st] >> 1], (unsigned long long)hk[a]);
                 R++;
                 c = 0;
                 d = 0;
             }
             c++;
-            d += (int)(s[i] & 1);
+            d += (int)(s[(i) * st] & 1);
         }
         if (n > 0) {
-            pc.p[base + R] = (int32_t)(s[n - 1] >> 1);
+            pc.p[base + R] = (int32_t)(s[(n - 1) * st] >> 1);
             pc.cnt[base + R] = c;
             pc.dcnt[base + R] = d;
-            if (d > 0) atomicAdd((unsigned long long*)&pincnt[s[n - 1] >> 1], (unsigned long long)hk[a]);
+            if (d > 0) atomicAdd((unsigned long long*)&pincnt[s[(n - 1) * st] >> 1], (unsigned long long)hk[a]);
             R++;
         }
         pc.lam[a] = R;
-        if (R > 1) atomicAdd((unsigned long long*)&scal[RS_COST], (unsigned long long)(hw[a] * (R - 1)));
+        if (R > 1) atomicAdd((unsigned long long*)&cost[a & (COST_SLOTS - 1)], (unsigned long long)(hw[a] * (R - 1)));
     }
 };
 
@@ -379,7 +391,8 @@ struct Moves {
 template <typename S_>
 struct RowPol {
     using S = S_;
-    static constexpr bool kOptimistic = true;
+    // a row holds every adjacent partition: warp tables would overflow
+    static constexpr bool kOptimistic = false;
     struct Acc {
         __device__ Acc() {}
         __device__ void add(const Acc&) {}
@@ -1202,8 +1215,13 @@ static Status pin_counts(snnmap_hgraph* h, Level& L, LevelExtra& X, int32_t K, c
         SNN_L k_pstate_vertices<<<grid_for(L.V, 256), 256, 0, s>>>(L, rho, ps);
         SNN_CUDA(cudaGetLastError());
     }
-    PinCountJob job{L.hoff, L.hpins, L.hsd, L.hk, L.hw, rho, pc, ps.pincnt, h->d_scal};
+    int64_t* slots;
+    SNN_TRY(ar.alloc(&slots, COST_SLOTS));
+    SNN_CUDA(cudaMemsetAsync(slots, 0, COST_SLOTS * sizeof(int64_t), s));
+    PinCountJob job{L.hoff, L.hpins, L.hsd, L.hk, L.hw, rho, pc, ps.pincnt, slots};
     SNN_TRY(seg_run(job, X.seg, L.E, ar, s));
+    SNN_L k_cost_slots<<<1, 256, 0, s>>>(slots, h->d_scal + RS_COST);
+    SNN_CUDA(cudaGetLastError());
     return Status{};
 }
 

@@ -15,7 +15,8 @@
 //   __device__ uint32_t load(int32_t a, int i)   key i (0 <= i < len)
 //   __device__ void finish(int32_t a, const uint32_t* s, int n)
 //        run by one full warp on the n sorted keys s[0..n)
-//   __device__ void finish_thread(int32_t a, const uint32_t* s, int n)
+//   __device__ void finish_thread(int32_t a, const uint32_t* s, int n, int st)
+//                                                   (key i at s[i * st])
 //        the same, run by a single thread
 #pragma once
 #include "common.cuh"
@@ -108,26 +109,46 @@ __device__ __forceinline__ void block_bitonic(uint32_t* s, int N)
 
 enum : int { SEG_BT = 0, SEG_BB0 = 1, SEG_BB1 = 2, SEG_BB2 = 3, SEG_BB3 = 4, SEG_NB = 5 };
 
+// One thread per list of at most SEG_T_CAP keys: the keys are sorted in
+// registers by a fully unrolled bitonic network (padding sorts last) and
+// handed to the epilogue through shared memory, slot i of thread t at
+// i * blockDim + t so that a warp's lanes touch consecutive banks.
 template <class Job>
 __global__ void __launch_bounds__(256) k_seg_t(Job job, const int32_t* __restrict__ lists,
                                                const int32_t* __restrict__ meta)
 {
+    __shared__ uint32_t sk[SEG_T_CAP * 256];
     const int32_t* list = lists + meta[SEG_BT];
     int n = meta[SEG_NB + SEG_BT];
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+    for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+        int idx = base + threadIdx.x;
+        if (idx >= n) continue;
         int32_t a = list[idx];
         int L = job.len(a);
         uint32_t k[SEG_T_CAP];
-        for (int i = 0; i < L; i++) {
-            uint32_t v = job.load(a, i);
-            int j = i;
-            while (j > 0 && k[j - 1] > v) {
-                k[j] = k[j - 1];
-                j--;
+#pragma unroll
+        for (int i = 0; i < SEG_T_CAP; i++) k[i] = i < L ? job.load(a, i) : KEY_PAD;
+#pragma unroll
+        for (int w = 2; w <= SEG_T_CAP; w <<= 1) {
+#pragma unroll
+            for (int j = w >> 1; j > 0; j >>= 1) {
+#pragma unroll
+                for (int i = 0; i < SEG_T_CAP; i++) {
+                    int l = i ^ j;
+                    if (l > i) {
+                        bool up = (i & w) == 0;
+                        uint32_t x = k[i], y = k[l];
+                        if ((x > y) == up) {
+                            k[i] = y;
+                            k[l] = x;
+                        }
+                    }
+                }
             }
-            k[j] = v;
         }
-        job.finish_thread(a, k, L);
+#pragma unroll
+        for (int i = 0; i < SEG_T_CAP; i++) sk[i * 256 + threadIdx.x] = k[i];
+        job.finish_thread(a, sk + threadIdx.x, L, 256);
     }
 }
 
