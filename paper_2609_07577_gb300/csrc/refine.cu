@@ -1195,19 +1195,13 @@ Status dense_descend(snnmap_hgraph* h, int32_t level)
     return Status{};
 }
 
-// pin counts + partition state + Conn for rho
-static Status pin_counts(snnmap_hgraph* h, Level& L, LevelExtra& X, int32_t K, const int32_t* rho,
-                         PinCounts& pc, PState& ps)
+// pin counts + partition state + Conn for rho, into buffers the caller owns
+// (Conn is added to *cost)
+static Status pin_counts_into(snnmap_hgraph* h, Level& L, LevelExtra& X, int32_t K,
+                              const int32_t* rho, PinCounts& pc, PState& ps, int64_t* cost)
 {
     cudaStream_t s = h->stream;
     Arena& ar = h->scratch;
-    SNN_TRY(ar.alloc(&pc.p, L.P));
-    SNN_TRY(ar.alloc(&pc.cnt, L.P));
-    SNN_TRY(ar.alloc(&pc.dcnt, L.P));
-    SNN_TRY(ar.alloc(&pc.lam, L.E));
-    SNN_TRY(ar.alloc(&ps.size, K));
-    SNN_TRY(ar.alloc(&ps.inpins, K));
-    SNN_TRY(ar.alloc(&ps.pincnt, K));
     SNN_CUDA(cudaMemsetAsync(ps.size, 0, (size_t)K * 8, s));
     SNN_CUDA(cudaMemsetAsync(ps.inpins, 0, (size_t)K * 8, s));
     SNN_CUDA(cudaMemsetAsync(ps.pincnt, 0, (size_t)K * 8, s));
@@ -1220,9 +1214,23 @@ static Status pin_counts(snnmap_hgraph* h, Level& L, LevelExtra& X, int32_t K, c
     SNN_CUDA(cudaMemsetAsync(slots, 0, COST_SLOTS * sizeof(int64_t), s));
     PinCountJob job{L.hoff, L.hpins, L.hsd, L.hk, L.hw, rho, pc, ps.pincnt, slots};
     SNN_TRY(seg_run(job, X.seg, L.E, ar, s));
-    SNN_L k_cost_slots<<<1, 256, 0, s>>>(slots, h->d_scal + RS_COST);
+    SNN_L k_cost_slots<<<1, 256, 0, s>>>(slots, cost);
     SNN_CUDA(cudaGetLastError());
     return Status{};
+}
+
+static Status pin_counts(snnmap_hgraph* h, Level& L, LevelExtra& X, int32_t K, const int32_t* rho,
+                         PinCounts& pc, PState& ps)
+{
+    Arena& ar = h->scratch;
+    SNN_TRY(ar.alloc(&pc.p, L.P));
+    SNN_TRY(ar.alloc(&pc.cnt, L.P));
+    SNN_TRY(ar.alloc(&pc.dcnt, L.P));
+    SNN_TRY(ar.alloc(&pc.lam, L.E));
+    SNN_TRY(ar.alloc(&ps.size, K));
+    SNN_TRY(ar.alloc(&ps.inpins, K));
+    SNN_TRY(ar.alloc(&ps.pincnt, K));
+    return pin_counts_into(h, L, X, K, rho, pc, ps, h->d_scal + RS_COST);
 }
 
 Status level_cost(snnmap_hgraph* h, int32_t level, int32_t K, const int32_t* rho, int64_t* cost)
@@ -1239,6 +1247,111 @@ Status level_cost(snnmap_hgraph* h, int32_t level, int32_t K, const int32_t* rho
     return Status{};
 }
 
+// ---------------------------------------------------------------------------
+// Carried pin counts. Only hyperedges holding a pin of the enacted prefix
+// change their counts; their old contributions (inbound k per partition,
+// omega (lambda - 1) to Conn, omega to the save of a pin alone in its
+// partition) are taken out before the moves, the moves' own size, inbound
+// pins and internal axons move between partitions, the hyperedges are
+// counted again, and their new contributions added back.
+
+__global__ void __launch_bounds__(256)
+    k_pc_mark(Level L, const int32_t* __restrict__ moveidx, const int64_t* __restrict__ scal,
+              int32_t* hdirty)
+{
+    int64_t istar = scal[RS_BEST] > 0 ? scal[RS_ISTAR] : -1;
+    int lane = threadIdx.x & 31;
+    int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t a = gw; a < L.E; a += nw) {
+        bool hit = false;
+        if (istar >= 0)
+            for (int64_t j = L.hoff[a] + lane; j < L.hoff[a + 1] && !hit; j += 32) {
+                int32_t mi = moveidx[L.hpins[j]];
+                if (mi >= 0 && mi <= istar) hit = true;
+            }
+        hit = __any_sync(FULL, hit);
+        if (lane == 0) hdirty[a] = hit ? 1 : 0;
+    }
+}
+
+// sign -1: remove the contributions of the marked hyperedges under the
+// current counts and rho; sign +1: add them
+__global__ void __launch_bounds__(256)
+    k_pc_contrib(Level L, PinCounts pc, const int32_t* __restrict__ hdirty,
+                 const int32_t* __restrict__ rho, PState ps, int64_t* savev, int64_t* costv,
+                 int sign)
+{
+    int lane = threadIdx.x & 31;
+    int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t a = gw; a < L.E; a += nw) {
+        if (!hdirty[a]) continue;
+        int64_t b = L.hoff[a], e = L.hoff[a + 1];
+        int32_t lam = pc.lam[a];
+        int64_t w = L.hw[a];
+        int64_t k = L.hk[a];
+        if (sign < 0) {
+            // the count pass adds inbound k and Conn itself for sign +1
+            for (int32_t r = lane; r < lam; r += 32)
+                if (pc.dcnt[b + r] > 0) atomicAdd((unsigned long long*)&ps.pincnt[pc.p[b + r]],
+                                                  (unsigned long long)(-k));
+            if (lane == 0 && lam > 1)
+                atomicAdd((unsigned long long*)costv, (unsigned long long)(-(w * (lam - 1))));
+        }
+        for (int64_t j = b + lane; j < e; j += 32) {
+            int32_t x = L.hpins[j];
+            int32_t c, d;
+            lookup_count(pc, b, lam, rho[x], c, d);
+            if (c == 1) atomicAdd((unsigned long long*)&savev[x], (unsigned long long)(sign * w));
+        }
+    }
+}
+
+// the enacted moves' own size, inbound pins and internal axons change
+// partition
+__global__ void k_ps_moves(int32_t M, Moves mv, Level L, const int64_t* __restrict__ scal, PState ps)
+{
+    int64_t istar = scal[RS_BEST] > 0 ? scal[RS_ISTAR] : -1;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= istar && i < M;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t n = mv.n[i], f = mv.from[i], t = mv.to[i];
+        int64_t sz = L.vsize[n], ip = L.vinpins[n], ii = L.vinint[n];
+        atomicAdd((unsigned long long*)&ps.size[f], (unsigned long long)(-sz));
+        atomicAdd((unsigned long long*)&ps.size[t], (unsigned long long)sz);
+        atomicAdd((unsigned long long*)&ps.inpins[f], (unsigned long long)(-ip));
+        atomicAdd((unsigned long long*)&ps.inpins[t], (unsigned long long)ip);
+        if (ii) {
+            atomicAdd((unsigned long long*)&ps.pincnt[f], (unsigned long long)(-ii));
+            atomicAdd((unsigned long long*)&ps.pincnt[t], (unsigned long long)ii);
+        }
+    }
+}
+
+// the level's size buckets restricted to marked hyperedges (each bucket keeps
+// its start; counts by atomics, order irrelevant)
+__global__ void k_seg_filter(const int32_t* __restrict__ list, const int32_t* __restrict__ meta,
+                             int32_t E, const int32_t* __restrict__ hdirty, int32_t* out,
+                             int32_t* meta2)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < E;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t a = list[i];
+        if (!hdirty[a]) continue;
+        int b = 0;
+        while (b + 1 < SEG_NB && i >= meta[b + 1]) b++;
+        int32_t pos = atomicAdd(&meta2[SEG_NB + b], 1);
+        out[meta[b] + pos] = a;
+    }
+}
+
+__global__ void k_seg_meta_copy(const int32_t* __restrict__ meta, int32_t* meta2)
+{
+    for (int b = threadIdx.x; b < SEG_NB; b += blockDim.x) meta2[b] = meta[b];
+}
+
+__global__ void k_copy_i64(const int64_t* __restrict__ src, int64_t* dst) { *dst = *src; }
+
 // Per-level buffers that outlive a round: proposals (kept by vertices the
 // previous round did not touch), the vertices to evaluate, partition flags
 // and the level's largest vertex state.
@@ -1249,6 +1362,18 @@ struct IncState {
     uint8_t* pchg = nullptr;
     uint8_t* prel = nullptr;
     int32_t* vmax = nullptr;
+    // pin counts, partition state, Conn (costv), save and W carried from
+    // round to round: a round after the first starts from them, and the
+    // enacted prefix updates them for the hyperedges holding a moved pin
+    PinCounts pc;
+    PState ps;
+    int64_t* costv = nullptr;
+    int64_t* savev = nullptr;
+    int64_t* Wv = nullptr;
+    int32_t* hdirty = nullptr;   // per hyperedge
+    int32_t* hlist = nullptr;    // bucket lists filtered to dirty hyperedges
+    int32_t* hmeta = nullptr;    // their bucket starts and counts (2 * SEG_NB)
+    bool ready = false;          // set once the first round computed them
 };
 
 // One round; *applied = moves enacted, *gain = Conn removed, *cost = Conn at
@@ -1273,11 +1398,15 @@ static Status refine_round(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* 
     SNN_L k_round_init<<<1, 1, 0, s>>>(h->d_scal);
     SNN_CUDA(cudaGetLastError());
 
-    PinCounts pc;
-    PState ps;
+    PinCounts pc = inc.pc;
+    PState ps = inc.ps;
     {
         ProfScope prof(h, PS_PINCOUNT);
-        SNN_TRY(pin_counts(h, L, X, K, rho, pc, ps));
+        if (!inc.ready) {
+            SNN_CUDA(cudaMemsetAsync(inc.costv, 0, sizeof(int64_t), s));
+            SNN_TRY(pin_counts_into(h, L, X, K, rho, pc, ps, inc.costv));
+        }
+        SNN_L k_copy_i64<<<1, 1, 0, s>>>(inc.costv, h->d_scal + RS_COST);
         SNN_L k_check_pstate<<<grid_for(K, 256), 256, 0, s>>>(K, ps, prm.omega, prm.delta, prm.phi, h->d_scal);
         SNN_CUDA(cudaGetLastError());
     }
@@ -1292,17 +1421,18 @@ static Status refine_round(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* 
     int32_t* pto = inc.pto;
     int64_t* pgain = inc.pgain;
     int32_t *flag, *pos;
-    int64_t *savev, *Wv;
+    int64_t* savev = inc.savev;
+    int64_t* Wv = inc.Wv;
     SNN_TRY(ar.alloc(&flag, V));
     SNN_TRY(ar.alloc(&pos, V));
-    SNN_TRY(ar.alloc(&savev, V));
-    SNN_TRY(ar.alloc(&Wv, V));
-    prof.reset(new ProfScope(h, PS_SAVE));
-    SNN_CUDA(cudaMemsetAsync(savev, 0, (size_t)(V > 0 ? V : 1) * 8, s));
-    SNN_CUDA(cudaMemsetAsync(Wv, 0, (size_t)(V > 0 ? V : 1) * 8, s));
-    if (L.E > 0) {
-        SNN_L k_save<<<grid_for((int64_t)L.E * 32, 256), 256, 0, s>>>(L, pc, rho, savev, Wv);
-        SNN_CUDA(cudaGetLastError());
+    if (!inc.ready) {
+        prof.reset(new ProfScope(h, PS_SAVE));
+        SNN_CUDA(cudaMemsetAsync(savev, 0, (size_t)(V > 0 ? V : 1) * 8, s));
+        SNN_CUDA(cudaMemsetAsync(Wv, 0, (size_t)(V > 0 ? V : 1) * 8, s));
+        if (L.E > 0) {
+            SNN_L k_save<<<grid_for((int64_t)L.E * 32, 256), 256, 0, s>>>(L, pc, rho, savev, Wv);
+            SNN_CUDA(cudaGetLastError());
+        }
     }
     prof.reset(new ProfScope(h, PS_GAINS));
     if (dense) {
@@ -1437,8 +1567,36 @@ static Status refine_round(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* 
         SNN_L k_inc_targets<<<gv, 256, 0, s>>>(V, pto, inc.pchg, inc.dirty);
         SNN_CUDA(cudaGetLastError());
     }
+    // carried pin counts: take out the hyperedges the prefix touches (old
+    // counts, old rho), move, count them again, add them back
+    prof.reset(new ProfScope(h, PS_PINCOUNT));
+    int ghe = grid_for((int64_t)(L.E > 0 ? L.E : 1) * 32, 256);
+    if (L.E > 0) {
+        SNN_L k_pc_mark<<<ghe, 256, 0, s>>>(L, moveidx, h->d_scal, inc.hdirty);
+        SNN_L k_pc_contrib<<<ghe, 256, 0, s>>>(L, pc, inc.hdirty, rho, ps, savev, inc.costv, -1);
+        SNN_CUDA(cudaGetLastError());
+    }
+    SNN_L k_ps_moves<<<gm, 256, 0, s>>>(M, mv, L, h->d_scal, ps);
     SNN_L k_apply<<<gm, 256, 0, s>>>(M, mv, rho, moveidx, h->d_scal);
     SNN_CUDA(cudaGetLastError());
+    if (L.E > 0) {
+        SNN_CUDA(cudaMemsetAsync(inc.hmeta, 0, 2 * SEG_NB * sizeof(int32_t), s));
+        SNN_L k_seg_meta_copy<<<1, 32, 0, s>>>(X.seg.meta, inc.hmeta);
+        SNN_L k_seg_filter<<<grid_for(L.E, 256), 256, 0, s>>>(X.seg.list, X.seg.meta, L.E, inc.hdirty,
+                                                             inc.hlist, inc.hmeta);
+        SNN_CUDA(cudaGetLastError());
+        SegBuckets db = X.seg;
+        db.list = inc.hlist;
+        db.meta = inc.hmeta;
+        int64_t* slots;
+        SNN_TRY(ar.alloc(&slots, COST_SLOTS));
+        SNN_CUDA(cudaMemsetAsync(slots, 0, COST_SLOTS * sizeof(int64_t), s));
+        PinCountJob job{L.hoff, L.hpins, L.hsd, L.hk, L.hw, rho, pc, ps.pincnt, slots};
+        SNN_TRY(seg_run(job, db, L.E, ar, s));
+        SNN_L k_cost_slots<<<1, 256, 0, s>>>(slots, inc.costv);
+        SNN_L k_pc_contrib<<<ghe, 256, 0, s>>>(L, pc, inc.hdirty, rho, ps, savev, inc.costv, 1);
+        SNN_CUDA(cudaGetLastError());
+    }
     prof.reset();
     SNN_TRY(read_scalars(h));
     int64_t best = h->h_scal[RS_BEST];
@@ -1487,6 +1645,20 @@ Status refine_level(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* rho, in
     SNN_CUDA(cudaMallocAsync(&inc.pchg, nk, s));
     SNN_CUDA(cudaMallocAsync(&inc.prel, nk, s));
     SNN_CUDA(cudaMallocAsync(&inc.vmax, 3 * 4, s));
+    size_t np = (size_t)(L.P > 0 ? L.P : 1), ne = (size_t)(L.E > 0 ? L.E : 1);
+    SNN_CUDA(cudaMallocAsync(&inc.pc.p, np * 4, s));
+    SNN_CUDA(cudaMallocAsync(&inc.pc.cnt, np * 4, s));
+    SNN_CUDA(cudaMallocAsync(&inc.pc.dcnt, np * 4, s));
+    SNN_CUDA(cudaMallocAsync(&inc.pc.lam, ne * 4, s));
+    SNN_CUDA(cudaMallocAsync(&inc.ps.size, nk * 8, s));
+    SNN_CUDA(cudaMallocAsync(&inc.ps.inpins, nk * 8, s));
+    SNN_CUDA(cudaMallocAsync(&inc.ps.pincnt, nk * 8, s));
+    SNN_CUDA(cudaMallocAsync(&inc.costv, 8, s));
+    SNN_CUDA(cudaMallocAsync(&inc.savev, nv * 8, s));
+    SNN_CUDA(cudaMallocAsync(&inc.Wv, nv * 8, s));
+    SNN_CUDA(cudaMallocAsync(&inc.hdirty, ne * 4, s));
+    SNN_CUDA(cudaMallocAsync(&inc.hlist, ne * 4, s));
+    SNN_CUDA(cudaMallocAsync(&inc.hmeta, 2 * SEG_NB * 4, s));
     SNN_CUDA(cudaMemsetAsync(inc.vmax, 0, 3 * 4, s));
     if (L.V > 0) SNN_L k_level_max<<<grid_for(L.V, 256), 256, 0, s>>>(L, inc.vmax);
     SNN_CUDA(cudaGetLastError());
@@ -1498,6 +1670,7 @@ Status refine_level(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* rho, in
         int32_t props = 0, applied = 0, act = 0, rows = 0;
         int64_t g = 0, c0 = 0;
         st = refine_round(h, level, K, rho, moveidx, inc, &props, &applied, &g, &c0, &act, &rows);
+        inc.ready = true;
         h->scratch.reset();
         if (!st.ok()) break;
         h->rlog.push_back(snnmap_round_log{level, r, props, applied, act, rows, g});
@@ -1508,7 +1681,11 @@ Status refine_level(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* rho, in
     }
     cudaFreeAsync(moveidx, s);
     for (void* p : {(void*)inc.pto, (void*)inc.pgain, (void*)inc.dirty, (void*)inc.pchg,
-                    (void*)inc.prel, (void*)inc.vmax})
+                    (void*)inc.prel, (void*)inc.vmax, (void*)inc.pc.p, (void*)inc.pc.cnt,
+                    (void*)inc.pc.dcnt, (void*)inc.pc.lam, (void*)inc.ps.size,
+                    (void*)inc.ps.inpins, (void*)inc.ps.pincnt, (void*)inc.costv,
+                    (void*)inc.savev, (void*)inc.Wv, (void*)inc.hdirty, (void*)inc.hlist,
+                    (void*)inc.hmeta})
         cudaFreeAsync(p, s);
     if (!st.ok()) return st;
     if (!have_cost) {
