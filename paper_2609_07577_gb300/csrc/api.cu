@@ -125,6 +125,7 @@ void snnmap_free(snnmap_hgraph* h)
     snn::prof_release(h);
     snn::dense_close(h);
     snn::mat_close(h);
+    snn::carry_close(h);
     snn::gp_free(h);
     drop_levels_above(h, 0);
     h->scratch.release();
@@ -341,6 +342,7 @@ int snnmap_partition(snnmap_hgraph* h, void* stream, int32_t* d_rho_out, int64_t
             ld = nl;
         }
     }
+    if (s2.ok()) s2 = snn::carry_open(h, V0);
     int64_t cost = 0;
     for (int32_t l = nl - 1; s2.ok() && l >= 0; l--) {
         if (l < nl - 1) {
@@ -370,6 +372,7 @@ int snnmap_partition(snnmap_hgraph* h, void* stream, int32_t* d_rho_out, int64_t
     }
     cudaFreeAsync(tmp, h->stream);
     snn::dense_close(h);
+    snn::carry_close(h);
     if (!s2.ok()) return fail(s2);
     if (cur != d_rho_out) return fail(SNNMAP_ERR_CUDA, "internal: level parity");
     int32_t ne = 0;

@@ -62,6 +62,18 @@ struct ScoreMat {
     int32_t level = -1;   // level the matrix describes
 };
 
+// Proposals, gains and re-evaluation flags of the last histogram-refined
+// level, double-buffered so the next finer level can inherit them through
+// its cid map (cap vertices each).
+struct Carry {
+    int32_t* pto[2] = {nullptr, nullptr};
+    int64_t* pgain[2] = {nullptr, nullptr};
+    int32_t* dirty[2] = {nullptr, nullptr};
+    int cur = 0;
+    int64_t cap = 0;
+    int32_t level = -1;   // level whose final state buffers[cur] hold (-1: none)
+};
+
 // The partition hypergraph G_P of the last snnmap_partition_graph call.
 struct GpOut {
     int64_t* hoff = nullptr;
@@ -101,6 +113,7 @@ struct snnmap_hgraph {
     snn::DenseRows dense;
     snn::ScoreMat mat;
     snn::GpOut gp;
+    snn::Carry carry;
     std::vector<snnmap_round_log> rlog;
     std::vector<snnmap_level_log> llog;
     // profiler
@@ -186,6 +199,10 @@ Status dense_begin(snnmap_hgraph* h, int32_t level);
 Status dense_descend(snnmap_hgraph* h, int32_t level);
 void dense_close(snnmap_hgraph* h);
 int64_t dense_row_budget(const snnmap_hgraph* h);
+
+// proposal carry for snnmap_partition's uncoarsening (vertices of level 0)
+Status carry_open(snnmap_hgraph* h, int64_t cap);
+void carry_close(snnmap_hgraph* h);
 
 Status refine_level(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* rho, int64_t* cost,
                     int64_t* cost_start);

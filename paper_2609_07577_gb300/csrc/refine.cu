@@ -1630,6 +1630,56 @@ Status check_rho(snnmap_hgraph* h, int32_t level, int32_t K, const int32_t* rho)
     return Status{};
 }
 
+// Proposals carried to the next finer level: an unmatched vertex keeps its
+// super-node's proposal, gain and flag (its conn, overlap, save, W and the
+// partition state are unchanged by projection); both members of a pair are
+// evaluated.
+__global__ void k_carry_count(int32_t V, const int32_t* __restrict__ cid, int32_t* mcount)
+{
+    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < V;
+         n += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&mcount[cid[n]], 1);
+}
+
+__global__ void k_carry(int32_t V, const int32_t* __restrict__ cid, const int32_t* __restrict__ mcount,
+                        const int32_t* __restrict__ pto_c, const int64_t* __restrict__ pgain_c,
+                        const int32_t* __restrict__ dirty_c, int32_t* pto, int64_t* pgain,
+                        int32_t* dirty)
+{
+    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < V;
+         n += (int64_t)gridDim.x * blockDim.x) {
+        int32_t c = cid[n];
+        pto[n] = pto_c[c];
+        pgain[n] = pgain_c[c];
+        dirty[n] = (mcount[c] > 1 || dirty_c[c]) ? 1 : 0;
+    }
+}
+
+Status carry_open(snnmap_hgraph* h, int64_t cap)
+{
+    carry_close(h);
+    Carry& C = h->carry;
+    size_t n = (size_t)(cap > 0 ? cap : 1);
+    for (int b = 0; b < 2; b++) {
+        SNN_CUDA(cudaMallocAsync(&C.pto[b], n * 4, h->stream));
+        SNN_CUDA(cudaMallocAsync(&C.pgain[b], n * 8, h->stream));
+        SNN_CUDA(cudaMallocAsync(&C.dirty[b], n * 4, h->stream));
+    }
+    C.cap = cap;
+    C.level = -1;
+    C.cur = 0;
+    return Status{};
+}
+
+void carry_close(snnmap_hgraph* h)
+{
+    Carry& C = h->carry;
+    for (int b = 0; b < 2; b++)
+        for (void* p : {(void*)C.pto[b], (void*)C.pgain[b], (void*)C.dirty[b]})
+            if (p) cudaFreeAsync(p, h->stream);
+    C = Carry{};
+}
+
 Status refine_level(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* rho, int64_t* cost,
                     int64_t* cost_start)
 {
@@ -1638,10 +1688,35 @@ Status refine_level(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* rho, in
     size_t nv = (size_t)(L.V > 0 ? L.V : 1), nk = (size_t)(K > 0 ? K : 1);
     int32_t* moveidx;
     IncState inc;
+    Carry& CA = h->carry;
+    const bool dense_level = h->dense.C && h->dense.level == level;
+    const bool use_carry = CA.pto[0] && L.V <= CA.cap;
+    bool inherited = false;
     SNN_CUDA(cudaMallocAsync(&moveidx, nv * sizeof(int32_t), s));
-    SNN_CUDA(cudaMallocAsync(&inc.pto, nv * 4, s));
-    SNN_CUDA(cudaMallocAsync(&inc.pgain, nv * 8, s));
-    SNN_CUDA(cudaMallocAsync(&inc.dirty, nv * 4, s));
+    if (use_carry) {
+        int nb = 1 - CA.cur;
+        inc.pto = CA.pto[nb];
+        inc.pgain = CA.pgain[nb];
+        inc.dirty = CA.dirty[nb];
+        if (!dense_level && CA.level == level + 1 && L.V > 0) {
+            const Level& Lc = h->levels[level + 1];
+            int32_t* mcount;
+            SNN_TRY(h->scratch.alloc(&mcount, Lc.V));
+            SNN_CUDA(cudaMemsetAsync(mcount, 0, (size_t)(Lc.V > 0 ? Lc.V : 1) * 4, s));
+            SNN_L k_carry_count<<<grid_for(L.V, 256), 256, 0, s>>>(L.V, L.cid, mcount);
+            SNN_L k_carry<<<grid_for(L.V, 256), 256, 0, s>>>(L.V, L.cid, mcount, CA.pto[CA.cur],
+                                                            CA.pgain[CA.cur], CA.dirty[CA.cur],
+                                                            inc.pto, inc.pgain, inc.dirty);
+            SNN_CUDA(cudaGetLastError());
+            inherited = true;
+        }
+        CA.cur = nb;
+        CA.level = -1;
+    } else {
+        SNN_CUDA(cudaMallocAsync(&inc.pto, nv * 4, s));
+        SNN_CUDA(cudaMallocAsync(&inc.pgain, nv * 8, s));
+        SNN_CUDA(cudaMallocAsync(&inc.dirty, nv * 4, s));
+    }
     SNN_CUDA(cudaMallocAsync(&inc.pchg, nk, s));
     SNN_CUDA(cudaMallocAsync(&inc.prel, nk, s));
     SNN_CUDA(cudaMallocAsync(&inc.vmax, 3 * 4, s));
@@ -1663,7 +1738,7 @@ Status refine_level(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* rho, in
     if (L.V > 0) SNN_L k_level_max<<<grid_for(L.V, 256), 256, 0, s>>>(L, inc.vmax);
     SNN_CUDA(cudaGetLastError());
     Status st = fill_i32(moveidx, -1, L.V, s);
-    if (st.ok()) st = fill_i32(inc.dirty, 1, L.V, s);
+    if (st.ok() && !inherited) st = fill_i32(inc.dirty, 1, L.V, s);
     int64_t c = 0;
     bool have_cost = false;
     for (int32_t r = 0; st.ok() && r < h->prm.max_refine_rounds; r++) {
@@ -1680,7 +1755,11 @@ Status refine_level(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* rho, in
         if (applied == 0) break;
     }
     cudaFreeAsync(moveidx, s);
-    for (void* p : {(void*)inc.pto, (void*)inc.pgain, (void*)inc.dirty, (void*)inc.pchg,
+    if (!use_carry)
+        for (void* p : {(void*)inc.pto, (void*)inc.pgain, (void*)inc.dirty}) cudaFreeAsync(p, s);
+    else if (st.ok() && !dense_level)
+        CA.level = level;   // the next finer level may inherit these proposals
+    for (void* p : {(void*)inc.pchg,
                     (void*)inc.prel, (void*)inc.vmax, (void*)inc.pc.p, (void*)inc.pc.cnt,
                     (void*)inc.pc.dcnt, (void*)inc.pc.lam, (void*)inc.ps.size,
                     (void*)inc.ps.inpins, (void*)inc.ps.pincnt, (void*)inc.costv,
