@@ -387,13 +387,9 @@ def _dist_setup():
 
 
 def _max_over_ranks(x, world, local):
-    if world == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], device=torch.device("cuda", local), dtype=torch.float64)
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    """Slowest rank's value (NCCL on the rank's GPU when N > 1)."""
+    from paper_2609_07577_gb300.shard import max_over_ranks
+    return x if world == 1 else max_over_ranks(x, device=f"cuda:{local}")
 
 
 def _barrier(world, local):
@@ -414,8 +410,9 @@ def run_batch(args):
     __graft_entry__.build()
     import paper_2609_07577_gb300 as P
     from paper_2609_07577_gb300 import JobBuffers
+    from paper_2609_07577_gb300.shard import rank_jobs
     n_jobs = args.jobs or 32
-    mine = [j for j in range(n_jobs) if j % world == rank]
+    mine = rank_jobs(n_jobs, rank, world)
     t0 = time.perf_counter()
     hgs = [snngen.batch_jobs_one(j) for j in mine]
     gen_s = time.perf_counter() - t0
@@ -499,7 +496,8 @@ def run_serve(args):
     stream = snngen.serve_stream(n_jobs)
     if args.max_neurons:
         stream = [d for d in stream if d["n"] <= args.max_neurons]
-    mine = [d for i, d in enumerate(stream) if i % world == rank]
+    from paper_2609_07577_gb300.shard import rank_jobs
+    mine = [stream[i] for i in rank_jobs(len(stream), rank, world)]
     t0 = time.perf_counter()
     bufs = [JobBuffers(snngen.serve_job(d), on_host=True) for d in mine]
     gen_s = time.perf_counter() - t0
