@@ -287,7 +287,7 @@ int snnmap_partition_graph_copy(const snnmap_hgraph* h, int64_t* d_offsets, int3
  * eighth of their vertices into pairs, each vertex keeps its
  * connection weight and inbound overlap to every partition, updated as moves
  * are enacted and carried to the next finer level, instead of a histogram
- * per round. -1: the default, 1/8 of the device's memory; 0: none. Results do
+ * per round. -1: the default, 1/4 of the device's memory; 0: none. Results do
  * not depend on it (used only when the summed omega stays below 2^31).
  */
 int snnmap_set_row_budget(snnmap_hgraph* h, int64_t bytes);

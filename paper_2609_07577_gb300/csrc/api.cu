@@ -319,32 +319,32 @@ int snnmap_partition(snnmap_hgraph* h, void* stream, int32_t* d_rho_out, int64_t
     int32_t* oth = cur == d_rho_out ? tmp : d_rho_out;
     snn::mat_close(h);
     snn::Status s2 = snn::iota_i32(cur, K, h->stream);
-    // connection rows for the levels from the coarsest down to the finest one
-    // whose rows fit the row budget (conn is stored in int32: needs the
-    // summed omega below 2^31) and that re-create at most a quarter of their
-    // rows on descent (2 x pairs <= V / 4; levels merging more pairs pay a
-    // histogram per fresh row and gain little over incremental histogram
-    // rounds); the finer levels use histograms
-    int32_t ld = nl;
+    // Connection rows serve the levels from the coarsest down to the finest
+    // one whose rows fit the row budget (conn is stored in int32: needs the
+    // summed omega below 2^31). Going down, a level keeps the rows (descent:
+    // fresh rows for the pairs only) unless it re-creates more than a quarter
+    // of them (2 x pairs > V / 4) while the level above needed few
+    // evaluations; a histogram level hands back to rows (every row fresh)
+    // once the level above needed at least four evaluations per vertex
+    // (rounds times the share of vertices evaluated), as on power-law
+    // graphs whose levels run many rounds with every vertex active.
+    int32_t lb = nl;
     {
         int64_t rb = snn::dense_row_budget(h);
         int64_t per = ((((int64_t)K + 3) & ~(int64_t)3) * 8 + 12);
         if (rb > 0 && !h->wide && h->wsum <= INT32_MAX)
-            for (int32_t l = nl - 1; l >= 0; l--) {
-                int64_t V = h->levels[l].V;
-                int64_t fresh = l + 1 < nl ? 2 * (V - h->levels[l + 1].V) : 0;
-                if (V * per > rb || 4 * fresh > V) break;
-                ld = l;
-            }
-        if (ld < nl && !snn::dense_open(h, K, h->levels[ld].V).ok()) {
+            for (int32_t l = nl - 1; l >= 0 && (int64_t)h->levels[l].V * per <= rb; l--) lb = l;
+        if (lb < nl && !snn::dense_open(h, K, h->levels[lb].V).ok()) {
             snn::dense_close(h);
             cudaGetLastError();
-            ld = nl;
+            lb = nl;
         }
     }
     if (s2.ok()) s2 = snn::carry_open(h, V0);
     int64_t cost = 0;
+    double evals_above = 0;   // evaluations per vertex at the level above
     for (int32_t l = nl - 1; s2.ok() && l >= 0; l--) {
+        bool rows_here = false;
         if (l < nl - 1) {
             // a level rebuilt for its refinement is released again
             if (l + 1 < nl - 1 && (l + 1) % h->keep_stride != 0)
@@ -355,20 +355,36 @@ int snnmap_partition(snnmap_hgraph* h, void* stream, int32_t* d_rho_out, int64_t
             s2 = snn::project(h, l, cur, oth);
             if (!s2.ok()) break;
             std::swap(cur, oth);
-            if (l >= ld) {
+            if (l >= lb) {
+                int64_t V = h->levels[l].V;
+                int64_t fresh = 2 * (V - h->levels[l + 1].V);
+                bool busy = evals_above >= 4.0;
                 snn::ProfScope prof(h, snn::PS_ROWS);
-                s2 = snn::dense_descend(h, l);
+                if (h->dense.level == l + 1 && (4 * fresh <= V || busy)) {
+                    s2 = snn::dense_descend(h, l);
+                    rows_here = true;
+                } else if (h->dense.level != l + 1 && busy) {
+                    s2 = snn::dense_begin(h, l);
+                    rows_here = true;
+                }
+            } else if (h->dense.C) {
+                snn::dense_close(h);
             }
-            else if (h->dense.C) snn::dense_close(h);
             if (!s2.ok()) break;
-        } else if (ld <= l) {
+        } else if (lb <= l) {
             s2 = snn::dense_begin(h, l);
+            rows_here = true;
             if (!s2.ok()) break;
         }
+        if (!rows_here && h->dense.C) h->dense.level = -1;
         int64_t c0 = 0;
+        size_t r0 = h->rlog.size();
         s2 = snn::refine_level(h, l, K, cur, &cost, l == nl - 1 ? &c0 : nullptr);
         if (l == nl - 1) st.cost_initial = c0;
         snn::note_bytes(h);
+        double act = 0;
+        for (size_t r = r0; r < h->rlog.size(); r++) act += h->rlog[r].n_active;
+        evals_above = h->levels[l].V > 0 ? act / h->levels[l].V : 0;
     }
     cudaFreeAsync(tmp, h->stream);
     snn::dense_close(h);

@@ -697,29 +697,72 @@ __global__ void k_inc_parts(int32_t M, Moves mv, const int64_t* __restrict__ sca
     }
 }
 
-// (a) and (b): every pin of a hyperedge holding an enacted moved pin or a
-// partition of prel (round-start pin counts) is marked
+// (a) and (b). A hyperedge holding enacted moved pins changes the other
+// pins' conn, overlap or save only where a partition's count or
+// destination count crosses zero or its count moves between 1 and 2; then
+// all its pins are marked, otherwise only the moved pins. A hyperedge
+// holding a partition of prel (round-start pin counts) marks all its pins.
+// One warp per hyperedge; buf (one word per pin) collects the moves.
 __global__ void __launch_bounds__(256)
-    k_inc_hedges(Level L, PinCounts pc, const int32_t* __restrict__ moveidx,
-                 const int64_t* __restrict__ scal, const uint8_t* __restrict__ prel, int32_t* dirty)
+    k_inc_hedges(Level L, PinCounts pc, const int32_t* __restrict__ moveidx, Moves mv,
+                 const int64_t* __restrict__ scal, const uint8_t* __restrict__ prel, uint32_t* buf,
+                 int32_t* dirty)
 {
     int64_t istar = scal[RS_BEST] > 0 ? scal[RS_ISTAR] : -1;
     if (istar < 0) return;
     int lane = threadIdx.x & 31;
+    unsigned lt = lanemask_lt();
     int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t a = gw; a < L.E; a += nw) {
         int64_t b = L.hoff[a], e = L.hoff[a + 1];
-        bool hit = false;
-        for (int64_t j = b + lane; j < e && !hit; j += 32) {
-            int32_t mi = moveidx[L.hpins[j]];
-            if (mi >= 0 && mi <= istar) hit = true;
+        int sd = L.hsd[a];
+        int m = 0;
+        for (int64_t cb = b; cb < e; cb += 32) {
+            int64_t j = cb + lane;
+            int32_t mi = -1;
+            if (j < e) mi = moveidx[L.hpins[j]];
+            bool ap = mi >= 0 && mi <= istar;
+            unsigned mk = __ballot_sync(FULL, ap);
+            if (ap) buf[b + m + __popc(mk & lt)] = ((uint32_t)mi << 1) | ((j != b || sd) ? 1u : 0u);
+            m += __popc(mk);
         }
+        __syncwarp();
         int32_t lam = pc.lam[a];
-        for (int32_t r = lane; r < lam && !hit; r += 32)
-            if (prel[pc.p[b + r]]) hit = true;
-        if (!__any_sync(FULL, hit)) continue;
-        for (int64_t j = b + lane; j < e; j += 32) dirty[L.hpins[j]] = 1;
+        bool all = false;
+        for (int32_t r = lane; r < lam && !all; r += 32)
+            if (prel[pc.p[b + r]]) all = true;
+        all = __any_sync(FULL, all);   // uniform before the warp-wide loop below
+        for (int ib = 0; ib < m && !all; ib += 32) {
+            int ii = ib + lane;
+            if (ii < m) {
+                int32_t mi = (int32_t)(buf[b + ii] >> 1);
+                int32_t cand[2] = {mv.from[mi], mv.to[mi]};
+                for (int u = 0; u < 2 && !all; u++) {
+                    int32_t p = cand[u];
+                    int nc = 0, nd = 0;
+                    for (int jj = 0; jj < m; jj++) {
+                        uint32_t rj = buf[b + jj];
+                        int32_t mj = (int32_t)(rj >> 1);
+                        int dlt = (mv.to[mj] == p) - (mv.from[mj] == p);
+                        nc += dlt;
+                        if (rj & 1) nd += dlt;
+                    }
+                    int32_t c0, d0;
+                    lookup_count(pc, b, lam, p, c0, d0);
+                    int c1 = c0 + nc, d1 = d0 + nd;
+                    if ((c0 > 0) != (c1 > 0) || (d0 > 0) != (d1 > 0) || (c0 == 1) != (c1 == 1))
+                        all = true;
+                }
+            }
+            all = __any_sync(FULL, all);
+        }
+        all = __any_sync(FULL, all);
+        if (all) {
+            for (int64_t j = b + lane; j < e; j += 32) dirty[L.hpins[j]] = 1;
+        } else {
+            for (int ii = lane; ii < m; ii += 32) dirty[mv.n[buf[b + ii] >> 1]] = 1;
+        }
     }
 }
 
@@ -1115,7 +1158,7 @@ int64_t dense_row_budget(const snnmap_hgraph* h)
     if (h->row_budget >= 0) return h->row_budget;
     size_t fr = 0, tot = 0;
     if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return 0;
-    return (int64_t)(tot / 8);
+    return (int64_t)(tot / 4);
 }
 
 Status dense_open(snnmap_hgraph* h, int32_t K, int64_t rows)
@@ -1563,7 +1606,7 @@ static Status refine_round(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* 
                                              prm.phi, inc.pchg, inc.prel);
         if (L.E > 0)
             SNN_L k_inc_hedges<<<grid_for((int64_t)L.E * 32, 256), 256, 0, s>>>(
-                L, pc, moveidx, h->d_scal, inc.prel, inc.dirty);
+                L, pc, moveidx, mv, h->d_scal, inc.prel, mvbuf, inc.dirty);
         SNN_L k_inc_targets<<<gv, 256, 0, s>>>(V, pto, inc.pchg, inc.dirty);
         SNN_CUDA(cudaGetLastError());
     }
