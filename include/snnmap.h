@@ -342,10 +342,10 @@ int snnmap_connectivity_noalloc(int32_t n_vertices, int32_t n_hedges, const int6
  * already reserved, or at once when nothing is reserved. A footprint stays
  * reserved while the job runs and, for jobs with keep_hierarchy set, until
  * snnmap_serve_release. Each job keeps at most about its level-0 size of
- * intermediate levels in memory (snnmap_set_level_budget) and gets 4 times
- * its level-0 size plus 256 MiB for connection rows and the score matrix
- * (snnmap_set_row_budget), which bounds its footprint; this changes no
- * result.
+ * intermediate levels in memory (snnmap_set_level_budget) and gets the
+ * larger of 4 times its level-0 size plus 256 MiB and mem_budget / (4 x
+ * slots) for connection rows and the score matrix (snnmap_set_row_budget);
+ * both count in its footprint. None of this changes a result.
  */
 typedef struct snnmap_server snnmap_server;
 
@@ -381,8 +381,9 @@ typedef struct {
                                  memory free at creation (dry run: 2^36) */
 } snnmap_serve_opts;
 
-/* Predicted peak device bytes of one job with the given level-0 sizes
- * (host-only arithmetic; no GPU needed). on_host adds the job's input copies.
+/* Predicted peak device bytes of one job with the given level-0 sizes and
+ * the smallest row budget a server grants (host-only arithmetic; no GPU
+ * needed; a server adds any larger grant). on_host adds the input copies.
  * Errors: SNNMAP_ERR_INVALID for negative sizes or a NULL output. */
 int snnmap_job_footprint(int32_t n_vertices, int32_t n_hedges, int64_t n_pins, int32_t on_host,
                          int64_t* bytes);

@@ -68,6 +68,7 @@ struct Ticket {
     int64_t id = 0;
     snnmap_job* job = nullptr;
     int64_t fp = 0;
+    int64_t rows = 0;              // row budget granted to the job
     int state = 0;                 // 0 queued, 1 running, 2 done
     snnmap_hgraph* h = nullptr;    // kept hierarchy
 };
@@ -102,6 +103,14 @@ struct snnmap_server {
         return std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
     }
     bool admissible(const Ticket* t) const { return reserved == 0 || reserved + t->fp <= budget; }
+    // row budget of a job: at least the footprint model's, and a quarter of
+    // the memory budget shared by the slots (power-law jobs refine from
+    // connection rows at most levels with it)
+    int64_t row_grant(int64_t L0) const
+    {
+        int64_t share = budget / (4 * (int64_t)slots);
+        return std::max(job_row_budget(L0), share);
+    }
     void work(int slot);
     void run(Ticket* t, int slot);
 };
@@ -162,7 +171,7 @@ void snnmap_server::run(Ticket* t, int slot)
     if (rc == SNNMAP_OK) {
         int64_t L0 = level_bytes(j->n_vertices, j->n_hedges, h->levels[0].P);
         snnmap_set_level_budget(h, L0);
-        snnmap_set_row_budget(h, job_row_budget(L0));
+        snnmap_set_row_budget(h, t->rows);
         rc = snnmap_partition(h, s, rho, &j->cost, &j->stats);
         if (rc != SNNMAP_OK) msg = snnmap_last_error();
     }
@@ -302,7 +311,13 @@ int snnmap_serve_submit(snnmap_server* s, snnmap_job* job, int64_t* ticket)
         return SNNMAP_ERR_OOM;
     }
     t->job = job;
-    t->fp = footprint(job->n_vertices, job->n_hedges, P < 0 ? 0 : P, job->on_host != 0);
+    {
+        int64_t Pc = P < 0 ? 0 : P;
+        int64_t L0 = level_bytes(job->n_vertices, job->n_hedges, Pc);
+        t->rows = s->row_grant(L0);
+        t->fp = footprint(job->n_vertices, job->n_hedges, Pc, job->on_host != 0) - job_row_budget(L0) +
+                t->rows;
+    }
     job->footprint = t->fp;
     job->cost = 0;
     job->stats = snnmap_stats{};
