@@ -139,7 +139,7 @@ void snnmap_free(snnmap_hgraph* h)
     delete h;
 }
 
-int snnmap_build_hgraph(const snnmap_params* params, int32_t n_vertices, int32_t n_hedges,
+static int snnmap_build_hgraph_impl(const snnmap_params* params, int32_t n_vertices, int32_t n_hedges,
                         const int64_t* d_offsets, const int32_t* d_pins, const int32_t* d_w,
                         void* stream, snnmap_hgraph** out)
 {
@@ -185,7 +185,7 @@ int snnmap_build_hgraph(const snnmap_params* params, int32_t n_vertices, int32_t
     return SNNMAP_OK;
 }
 
-int snnmap_coarsen_level(snnmap_hgraph* h, void* stream, int32_t* n_cand_out, int32_t* n_pairs_out)
+static int snnmap_coarsen_level_impl(snnmap_hgraph* h, void* stream, int32_t* n_cand_out, int32_t* n_pairs_out)
 {
     g_err.clear();
     if (!h || !n_cand_out || !n_pairs_out) return fail(SNNMAP_ERR_INVALID, "NULL argument");
@@ -202,7 +202,7 @@ int snnmap_coarsen_level(snnmap_hgraph* h, void* stream, int32_t* n_cand_out, in
     return SNNMAP_OK;
 }
 
-int snnmap_contract(snnmap_hgraph* h, void* stream, int32_t* V_out, int32_t* E_out, int64_t* P_out)
+static int snnmap_contract_impl(snnmap_hgraph* h, void* stream, int32_t* V_out, int32_t* E_out, int64_t* P_out)
 {
     g_err.clear();
     if (!h) return fail(SNNMAP_ERR_INVALID, "NULL handle");
@@ -249,7 +249,7 @@ int snnmap_project(snnmap_hgraph* h, int32_t level, const int32_t* d_rho_coarse,
     return SNNMAP_OK;
 }
 
-int snnmap_refine(snnmap_hgraph* h, int32_t level, int32_t n_parts, int32_t* d_rho, void* stream,
+static int snnmap_refine_impl(snnmap_hgraph* h, int32_t level, int32_t n_parts, int32_t* d_rho, void* stream,
                   int64_t* cost_out)
 {
     g_err.clear();
@@ -277,7 +277,7 @@ int snnmap_connectivity(snnmap_hgraph* h, int32_t n_parts, const int32_t* d_rho,
     return SNNMAP_OK;
 }
 
-int snnmap_partition(snnmap_hgraph* h, void* stream, int32_t* d_rho_out, int64_t* cost_out,
+static int snnmap_partition_impl(snnmap_hgraph* h, void* stream, int32_t* d_rho_out, int64_t* cost_out,
                      snnmap_stats* stats)
 {
     g_err.clear();
@@ -406,7 +406,7 @@ int snnmap_partition(snnmap_hgraph* h, void* stream, int32_t* d_rho_out, int64_t
     return SNNMAP_OK;
 }
 
-int snnmap_partition_host(const snnmap_params* params, int32_t n_vertices, int32_t n_hedges,
+static int snnmap_partition_host_impl(const snnmap_params* params, int32_t n_vertices, int32_t n_hedges,
                           const int64_t* h_offsets, const int32_t* h_pins, const int32_t* h_w,
                           int32_t* h_rho_out, int64_t* cost_out, snnmap_stats* stats, void* stream)
 {
@@ -638,6 +638,80 @@ int snnmap_set_level_budget(snnmap_hgraph* h, int64_t bytes)
     h->keep_stride = 1;
     snn::thin_levels(h);
     return SNNMAP_OK;
+}
+
+// The entry points above never let a C++ exception (a failed host
+// allocation inside a standard container) cross the C ABI.
+int snnmap_build_hgraph(const snnmap_params* params, int32_t n_vertices, int32_t n_hedges,
+                        const int64_t* d_offsets, const int32_t* d_pins, const int32_t* d_w,
+                        void* stream, snnmap_hgraph** out)
+{
+    try {
+        return snnmap_build_hgraph_impl(params, n_vertices, n_hedges, d_offsets, d_pins, d_w, stream, out);
+    } catch (const std::bad_alloc&) {
+        return fail(SNNMAP_ERR_OOM, "host allocation failed");
+    } catch (...) {
+        return fail(SNNMAP_ERR_CUDA, "internal error");
+    }
+}
+
+int snnmap_coarsen_level(snnmap_hgraph* h, void* stream, int32_t* n_cand_out, int32_t* n_pairs_out)
+{
+    try {
+        return snnmap_coarsen_level_impl(h, stream, n_cand_out, n_pairs_out);
+    } catch (const std::bad_alloc&) {
+        return fail(SNNMAP_ERR_OOM, "host allocation failed");
+    } catch (...) {
+        return fail(SNNMAP_ERR_CUDA, "internal error");
+    }
+}
+
+int snnmap_contract(snnmap_hgraph* h, void* stream, int32_t* V_out, int32_t* E_out, int64_t* P_out)
+{
+    try {
+        return snnmap_contract_impl(h, stream, V_out, E_out, P_out);
+    } catch (const std::bad_alloc&) {
+        return fail(SNNMAP_ERR_OOM, "host allocation failed");
+    } catch (...) {
+        return fail(SNNMAP_ERR_CUDA, "internal error");
+    }
+}
+
+int snnmap_refine(snnmap_hgraph* h, int32_t level, int32_t n_parts, int32_t* d_rho, void* stream,
+                  int64_t* cost_out)
+{
+    try {
+        return snnmap_refine_impl(h, level, n_parts, d_rho, stream, cost_out);
+    } catch (const std::bad_alloc&) {
+        return fail(SNNMAP_ERR_OOM, "host allocation failed");
+    } catch (...) {
+        return fail(SNNMAP_ERR_CUDA, "internal error");
+    }
+}
+
+int snnmap_partition(snnmap_hgraph* h, void* stream, int32_t* d_rho_out, int64_t* cost_out,
+                     snnmap_stats* stats)
+{
+    try {
+        return snnmap_partition_impl(h, stream, d_rho_out, cost_out, stats);
+    } catch (const std::bad_alloc&) {
+        return fail(SNNMAP_ERR_OOM, "host allocation failed");
+    } catch (...) {
+        return fail(SNNMAP_ERR_CUDA, "internal error");
+    }
+}
+
+int snnmap_partition_host(const snnmap_params* params, int32_t n_vertices, int32_t n_hedges,
+                          const int64_t* h_offsets, const int32_t* h_pins, const int32_t* h_w,
+                          int32_t* h_rho_out, int64_t* cost_out, snnmap_stats* stats, void* stream)
+{
+    try {
+        return snnmap_partition_host_impl(params, n_vertices, n_hedges, h_offsets, h_pins, h_w, h_rho_out, cost_out, stats, stream);
+    } catch (const std::bad_alloc&) {
+        return fail(SNNMAP_ERR_OOM, "host allocation failed");
+    } catch (...) {
+        return fail(SNNMAP_ERR_CUDA, "internal error");
+    }
 }
 
 }  // extern "C"

@@ -215,7 +215,14 @@ void snnmap_server::work(int slot)
         t->state = 1;
         t->job->t_start_ms = now_ms();
         lk.unlock();
-        run(t, slot);
+        try {
+            run(t, slot);
+        } catch (...) {
+            // a failed host allocation ends this job, not the process
+            t->h = nullptr;
+            t->job->status = SNNMAP_ERR_OOM;
+            set_err(t->job, "host allocation failed");
+        }
         lk.lock();
         t->job->t_end_ms = now_ms();
         t->state = 2;
