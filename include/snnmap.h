@@ -52,6 +52,12 @@ typedef struct {
     int32_t max_levels;        /* cap on contractions; coarsening otherwise stops
                                   when no vertex has a candidate (Sec. 4.1) */
     int32_t max_refine_rounds; /* cap on refinement rounds per level */
+    int32_t refine_nonpositive; /* 0 (default): a vertex proposes its best move only if
+                                   its gain is positive; 1: every vertex with a feasible
+                                   move to an adjacent partition proposes its best one
+                                   (a variant of Sec. 4.1: moves that only pay after
+                                   earlier moves of the sequence can join an enacted
+                                   prefix, which still needs a positive total gain) */
 } snnmap_params;
 
 /* Summary of one snnmap_partition call. */

@@ -35,7 +35,8 @@ def build(force: bool = False) -> str:
 
 class Params(C.Structure):
     _fields_ = [("omega", C.c_int32), ("delta", C.c_int32), ("phi", C.c_int32),
-                ("max_levels", C.c_int32), ("max_refine_rounds", C.c_int32)]
+                ("max_levels", C.c_int32), ("max_refine_rounds", C.c_int32),
+                ("refine_nonpositive", C.c_int32)]
 
 
 class RoundLog(C.Structure):
@@ -90,8 +91,10 @@ def lib():
         return _lib
 
 
-def params(omega, delta, phi, max_levels=1024, max_refine_rounds=16) -> Params:
-    return Params(int(omega), int(delta), int(phi), int(max_levels), int(max_refine_rounds))
+def params(omega, delta, phi, max_levels=1024, max_refine_rounds=16,
+           refine_nonpositive=0) -> Params:
+    return Params(int(omega), int(delta), int(phi), int(max_levels), int(max_refine_rounds),
+                  int(refine_nonpositive))
 
 
 def params_of(h, **kw) -> Params:

@@ -38,6 +38,11 @@
  *  R13 Validity is evaluated after each whole move.
  *  R14 Refinement also runs on the coarsest level.
  *  R15 Partitions may end up empty; ids are those of the coarsest vertices.
+ *  R19 Variant (refine_nonpositive = 1): every vertex with a feasible move
+ *      to an adjacent partition proposes its best one (max gain, lower
+ *      partition id) whatever the sign of its gain; a non-positive move can
+ *      still belong to an enacted prefix, whose cumulative gain and
+ *      validity are judged with every earlier move applied.
  *  R18 G_P (Sec. 3): the image of an axon keeps its direction: source
  *      partition rho(src), destinations the other partitions of its pins
  *      (a destination inside the source's partition is discarded). Axons
@@ -63,6 +68,7 @@ typedef struct {
     int32_t phi;                /* max inbound synapses per core (Phi) */
     int32_t max_levels;         /* R8 */
     int32_t max_refine_rounds;  /* R12 */
+    int32_t refine_nonpositive; /* R19: 1 = propose the best feasible move whatever its gain */
 } orc_params;
 
 /* One level of the hierarchy (Sec. 4.1: "each level's hgraph is
@@ -882,7 +888,7 @@ static int64_t refine_round(const orc_level *L, int32_t K, int32_t *rho, const o
             if (!feasible) continue;
             if (best < 0 || gain > bg || (gain == bg && p < best)) { best = p; bg = gain; }
         }
-        if (best >= 0 && bg > 0) {
+        if (best >= 0 && (bg > 0 || prm->refine_nonpositive)) {     /* R9, R19 */
             mv[nm].n = n; mv[nm].from = home; mv[nm].to = best; mv[nm].gain = bg;
             nm++;
         }

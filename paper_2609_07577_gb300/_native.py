@@ -16,7 +16,8 @@ OK, ERR_INVALID, ERR_INFEASIBLE, ERR_OOM, ERR_DEVICE_TIMEOUT, ERR_CUDA, ERR_STAT
 
 class Params(C.Structure):
     _fields_ = [("omega", C.c_int32), ("delta", C.c_int32), ("phi", C.c_int32),
-                ("max_levels", C.c_int32), ("max_refine_rounds", C.c_int32)]
+                ("max_levels", C.c_int32), ("max_refine_rounds", C.c_int32),
+                ("refine_nonpositive", C.c_int32)]
 
 
 class Stats(C.Structure):

@@ -8,8 +8,10 @@ import torch
 from . import _native as N
 
 
-def params_for(omega, delta, phi, max_levels=1024, max_refine_rounds=16) -> N.Params:
-    return N.Params(int(omega), int(delta), int(phi), int(max_levels), int(max_refine_rounds))
+def params_for(omega, delta, phi, max_levels=1024, max_refine_rounds=16,
+               refine_nonpositive=0) -> N.Params:
+    return N.Params(int(omega), int(delta), int(phi), int(max_levels), int(max_refine_rounds),
+                    int(refine_nonpositive))
 
 
 def to_device(hg, device="cuda"):

@@ -33,7 +33,7 @@ int fail(int code, const char* msg)
 bool params_ok(const snnmap_params* p)
 {
     return p && p->omega >= 1 && p->delta >= 0 && p->phi >= 0 && p->max_levels >= 0 &&
-           p->max_refine_rounds >= 0;
+           p->max_refine_rounds >= 0 && (p->refine_nonpositive == 0 || p->refine_nonpositive == 1);
 }
 
 // a device (or managed) pointer; host pointers would fault inside kernels
@@ -111,6 +111,7 @@ snnmap_params snnmap_default_params(int32_t omega, int32_t delta, int32_t phi)
     p.phi = phi;
     p.max_levels = 1024;
     p.max_refine_rounds = 16;
+    p.refine_nonpositive = 0;
     return p;
 }
 

@@ -46,7 +46,8 @@ enum : int {
     RS_NEV = SC_F,     // inbound events emitted
     RS_NHV = SC_G,     // hyperedges replayed by the block tier
     RS_DEG = 8,        // incidences of proposing vertices
-    RS_ACT = 10,       // vertices with save > 0
+    RS_ACT = 10,       // vertices evaluated
+    RS_MING = 11,      // smallest proposed gain (<= 0)
 };
 
 constexpr int REPLAY_WARP_MAX = 32;
@@ -308,8 +309,9 @@ struct GainPol {
     int64_t* pgain;
     const int64_t* savev;
     const int32_t* dirty;   // vertices to evaluate; the others keep pto/pgain
+    bool nonpos;            // propose the best feasible move whatever its gain
 
-    __device__ bool skip(int32_t n) const { return savev[n] == 0 || !dirty[n]; }
+    __device__ bool skip(int32_t n) const { return (!nonpos && savev[n] == 0) || !dirty[n]; }
     __device__ int64_t vb(int32_t n) const { return L.voff[n]; }
     __device__ int64_t ve(int32_t n) const { return L.voff[n + 1]; }
     __device__ int64_t seg_len(int64_t i) const
@@ -362,7 +364,7 @@ struct GainPol {
     __device__ void write(int32_t n, int64_t bs, int32_t bk, uint32_t, const Acc&) const
     {
         if (!dirty[n]) return;
-        bool prop = bk >= 0 && bs > 0;
+        bool prop = bk >= 0 && (bs > 0 || nonpos);
         pto[n] = prop ? bk : -1;
         pgain[n] = prop ? bs : 0;
     }
@@ -456,14 +458,14 @@ __global__ void __launch_bounds__(256)
                  const int64_t* __restrict__ savev, const int64_t* __restrict__ Wv,
                  const int32_t* __restrict__ rowid, const int32_t* __restrict__ C,
                  const int32_t* __restrict__ O, int64_t Kp, int32_t K, int32_t omega,
-                 int32_t delta, int32_t phi, int32_t* pto, int64_t* pgain)
+                 int32_t delta, int32_t phi, int nonpos, int32_t* pto, int64_t* pgain)
 {
     int lane = threadIdx.x & 31;
     int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t n = gw; n < L.V; n += nw) {
         int64_t sv = savev[n];
-        if (sv == 0) {
+        if (sv == 0 && !nonpos) {
             if (lane == 0) {
                 pto[n] = -1;
                 pgain[n] = 0;
@@ -484,7 +486,10 @@ __global__ void __launch_bounds__(256)
             for (int u = 0; u < 4; u++) {
                 int32_t p = (int32_t)(4 * q + u);
                 int64_t g = (int64_t)cv[u] - T;
-                if (p < K && g > bs && p != own && ps.size[p] + sz <= omega &&
+                // default: positive gains only (bs starts at 0); variant: any
+                // adjacent partition (conn > 0), the first one found seeds bs
+                if (p < K && (g > bs || (nonpos && bk < 0 && cv[u] > 0)) && cv[u] > 0 &&
+                    p != own && ps.size[p] + sz <= omega &&
                     ps.inpins[p] + ip <= phi && ps.pincnt[p] + ic - (int64_t)O[r0 + p] <= delta) {
                     bs = g;
                     bk = p;
@@ -781,17 +786,19 @@ __global__ void k_inc_targets(int32_t V, const int32_t* __restrict__ pto,
 __global__ void k_prop_stats(Level L, const int32_t* __restrict__ pto,
                              const int64_t* __restrict__ pgain,
                              const int64_t* __restrict__ savev,
-                             const int32_t* __restrict__ dirty, int32_t* flag, int64_t* scal)
+                             const int32_t* __restrict__ dirty, int nonpos, int32_t* flag,
+                             int64_t* scal)
 {
-    int64_t mg = 0, deg = 0;
+    int64_t mg = 0, ng = 0, deg = 0;
     int act = 0;
     for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < L.V;
          n += (int64_t)gridDim.x * blockDim.x) {
-        act += savev[n] > 0 && (!dirty || dirty[n]);
+        act += (nonpos || savev[n] > 0) && (!dirty || dirty[n]);
         int f = pto[n] >= 0;
         flag[n] = f;
         if (f) {
             mg = pgain[n] > mg ? pgain[n] : mg;
+            ng = pgain[n] < ng ? pgain[n] : ng;
             deg += L.voff[n + 1] - L.voff[n];
         }
     }
@@ -799,6 +806,8 @@ __global__ void k_prop_stats(Level L, const int32_t* __restrict__ pto,
     for (int o = 16; o > 0; o >>= 1) {
         int64_t m2 = __shfl_xor_sync(FULL, mg, o);
         mg = m2 > mg ? m2 : mg;
+        int64_t n2 = __shfl_xor_sync(FULL, ng, o);
+        ng = n2 < ng ? n2 : ng;
         deg += __shfl_xor_sync(FULL, deg, o);
     }
     act = warp_sum(act);
@@ -806,6 +815,7 @@ __global__ void k_prop_stats(Level L, const int32_t* __restrict__ pto,
         if (mg) atomicMax((unsigned long long*)&scal[RS_MAXG], (unsigned long long)mg);
         if (deg) atomicAdd((unsigned long long*)&scal[RS_DEG], (unsigned long long)deg);
         if (act) atomicAdd((unsigned long long*)&scal[RS_ACT], (unsigned long long)act);
+        if (ng < 0) atomicMin((long long*)&scal[RS_MING], (long long)ng);
     }
 }
 
@@ -1118,6 +1128,7 @@ static Status gains(snnmap_hgraph* h, Level& L, const PinCounts& pc, const int32
     GainPol<S> pol;
     pol.savev = savev;
     pol.dirty = dirty;
+    pol.nonpos = h->prm.refine_nonpositive != 0;
     pol.L = L;
     pol.pc = pc;
     pol.ps = ps;
@@ -1482,7 +1493,7 @@ static Status refine_round(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* 
         if (V > 0) {
             SNN_L k_dense_best<<<grid_for((int64_t)V * 32, 256), 256, 0, s>>>(
                 L, rho, ps, savev, Wv, D.rowid, D.C, D.O, D.Kp, K, prm.omega, prm.delta, prm.phi,
-                pto, pgain);
+                prm.refine_nonpositive, pto, pgain);
             SNN_CUDA(cudaGetLastError());
         }
     } else if (h->wide) {
@@ -1491,8 +1502,8 @@ static Status refine_round(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* 
         SNN_TRY(gains<uint32_t>(h, L, pc, rho, ps, K, pto, pgain, savev, inc.dirty));
     }
     int gv = grid_for(V, 256);
-    SNN_L k_prop_stats<<<gv, 256, 0, s>>>(L, pto, pgain, savev, dense ? nullptr : inc.dirty, flag,
-                                          h->d_scal);
+    SNN_L k_prop_stats<<<gv, 256, 0, s>>>(L, pto, pgain, savev, dense ? nullptr : inc.dirty,
+                                          prm.refine_nonpositive, flag, h->d_scal);
     SNN_CUDA(cudaGetLastError());
     SNN_TRY(scan_exclusive_i32(flag, pos, V, (int32_t*)(h->d_scal + RS_M), ar, s));
     prof.reset();
@@ -1504,6 +1515,7 @@ static Status refine_round(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* 
         return Status{SNNMAP_ERR_INVALID, "refinement input breaks a per-core limit"};
     int32_t M = (int32_t)(h->h_scal[RS_M] & 0xffffffff);
     int64_t maxg = h->h_scal[RS_MAXG];
+    int64_t ming = h->h_scal[RS_MING];   // <= 0: keys maxg - gain span maxg - ming
     int64_t deg = h->h_scal[RS_DEG];
     *n_props = M;
     if (M == 0) return Status{};
@@ -1518,7 +1530,7 @@ static Status refine_round(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* 
     SNN_TRY(ar.alloc(&vals2, M));
     SNN_L k_prop_keys<<<gv, 256, 0, s>>>(V, pto, pgain, pos, maxg, keys, vals);
     SNN_CUDA(cudaGetLastError());
-    SNN_TRY(radix_sort_pairs(keys, vals, keys2, vals2, M, bits_for((uint64_t)maxg), ar, s));
+    SNN_TRY(radix_sort_pairs(keys, vals, keys2, vals2, M, bits_for((uint64_t)(maxg - ming)), ar, s));
     Moves mv;
     SNN_TRY(ar.alloc(&mv.n, M));
     SNN_TRY(ar.alloc(&mv.from, M));

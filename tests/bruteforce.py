@@ -211,10 +211,15 @@ def refine_round(hg, img, VL, rho, K, prm):
 
     base = conn(hg, proj(rho))
     props = []
+    pr0 = proj(rho)
+    axons = [({s} | d) for s, d, w in hedges(hg) if d]
+    nonpos = getattr(prm, "refine_nonpositive", 0)
     for n in range(VL):
+        # partitions adjacent to n: holding a neuron of an axon that touches n
+        adj = {pr0[q] for e in axons if e & mem[n] for q in e}
         best = None
         for p in range(K):
-            if p == rho[n]:
+            if p == rho[n] or p not in adj:
                 continue
             if not group_ok(hg, part_neurons(rho, p) | mem[n], prm, ins):
                 continue
@@ -223,7 +228,7 @@ def refine_round(hg, img, VL, rho, K, prm):
             g = base - conn(hg, proj(r2))
             if best is None or (g, -p) > best:
                 best = (g, -p)
-        if best is not None and best[0] > 0:
+        if best is not None and (best[0] > 0 or nonpos):
             props.append((n, rho[n], -best[1], best[0]))
     props.sort(key=lambda t: (-t[3], t[0]))
     cur = list(rho)

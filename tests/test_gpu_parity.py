@@ -187,3 +187,37 @@ def test_rebuilt_levels_equal_oracle_levels():
             assert_level_equal(G.level_arrays(lev), olevels[lev].arrays(), f"rebuilt level {lev}")
     finally:
         G.close()
+
+
+@pytest.mark.parametrize("name,rows", [("cfg1s", None), ("cfg2s", None), ("cfg3s", None),
+                                       ("cfg1s", 0), ("cfg2s", 0), ("cfg3s", 0)])
+def test_partition_parity_nonpositive_variant(name, rows):
+    """Reading R19: every vertex proposes its best feasible adjacent move
+    whatever its gain; same partition, cost, stats and round logs as the
+    oracle, on connection rows (rows=None) and on histograms (rows=0)."""
+    hg = snngen.by_name(name)
+    (rho, cost, st, lv, rl), (rho_o, cost_o, st_o, lv_o, rl_o) = _partition_both(
+        hg, None, rows, refine_nonpositive=1)
+    assert cost == cost_o
+    assert np.array_equal(rho, rho_o)
+    for k in ("levels", "n_parts", "nonempty_parts", "rounds", "moves", "cost_initial", "cost"):
+        assert st[k] == st_o[k], k
+    assert [(r["level"], r["round"], r["n_props"], r["istar"], r["gain"]) for r in rl] == \
+        [(r["level"], r["round"], r["n_props"], r["istar"], r["gain"]) for r in rl_o]
+
+
+def test_tiny_random_nonpositive_variant():
+    from paper_2609_07577_gb300 import partition
+    n = 0
+    for seed in range(120):
+        hg = snngen.tiny_random(50_000 + seed)
+        prm = oracle.params_of(hg, refine_nonpositive=1)
+        try:
+            rho_o, cost_o, *_ = oracle.partition(hg, prm)
+        except oracle.OracleError:
+            continue
+        rho, cost, st = partition(hg, refine_nonpositive=1)
+        assert cost == cost_o, seed
+        assert np.array_equal(rho, rho_o), seed
+        n += 1
+    assert n > 40

@@ -161,3 +161,41 @@ def test_invalid_inputs_rejected():
     with pytest.raises(oracle.OracleError) as e:
         oracle.Level.from_hypergraph(inf)
     assert e.value.code == oracle.ERR_INFEASIBLE
+
+
+@pytest.mark.parametrize("chunk", range(2))
+def test_refine_round_variant_matches_bruteforce(chunk):
+    """The variant of reading R19 (every vertex proposes its best feasible
+    adjacent move whatever its gain) against the set-based restatement: the
+    non-positive proposals join the sorted sequence and a prefix is still
+    enacted only with positive cumulative gain and validity."""
+    rng = np.random.default_rng(4321 + chunk)
+    rounds_checked = moved = extra = 0
+    for seed in range(chunk, 2400, 4):
+        hg = snngen.tiny_random(10_000 + seed)
+        prm = oracle.params_of(hg, max_refine_rounds=1, refine_nonpositive=1)
+        base = oracle.params_of(hg, max_refine_rounds=1)
+        try:
+            levels = list(_levels(hg, base))
+        except oracle.OracleError:
+            continue
+        for L, cids, _, _, _ in levels:
+            img, mem = bf.members(cids, hg.V)
+            VL = len(mem)
+            for _ in range(2):
+                K = int(rng.integers(1, VL + 1))
+                rho = rng.integers(0, K, size=VL).astype(np.int32)
+                if not bf.feasible(hg, rho[img], prm):
+                    continue
+                want, props, istar, gain = bf.refine_round(hg, img, VL, rho.tolist(), K, prm)
+                _, props0, _, _ = bf.refine_round(hg, img, VL, rho.tolist(), K, base)
+                got = rho.copy()
+                r, mv, logs = L.refine(K, got, prm)
+                assert got.tolist() == want
+                assert logs[0]["n_props"] == props >= props0
+                assert logs[0]["istar"] == istar
+                assert logs[0]["gain"] == gain
+                rounds_checked += 1
+                moved += istar > 0
+                extra += props > props0
+    assert rounds_checked > 50 and moved > 10 and extra > 10
