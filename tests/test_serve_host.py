@@ -185,3 +185,28 @@ def test_bad_arguments():
             N.snnmap_serve_submit(s, j)
     finally:
         N.snnmap_serve_destroy(s)
+
+
+def test_row_grant_counts_in_footprint():
+    """A job's footprint is the model's plus any larger row grant (a quarter
+    of the memory budget shared by the slots)."""
+    lib_or_skip()
+    base = N.snnmap_job_footprint(100, 99, 198, on_host=True)
+
+    def fp(slots, budget):
+        s = N.snnmap_serve_create(slots, budget, 1000)
+        try:
+            hj = HostJob(100)
+            t = N.snnmap_serve_submit(s, hj.job)
+            assert N.snnmap_serve_wait(s, t, 10_000.0)
+            N.snnmap_serve_release(s, t)
+            return hj.job.footprint
+        finally:
+            N.snnmap_serve_destroy(s)
+
+    B = 1 << 34
+    # both shares (2 GiB, 512 MiB) exceed the model's row budget of a tiny job
+    assert fp(2, B) - fp(8, B) == B // 8 - B // 32
+    assert fp(8, B) > base
+    # a share below the model's row budget leaves the model's footprint
+    assert fp(8, 1 << 20) == base
