@@ -63,7 +63,9 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            _lib = C.CDLL(build())
+            # SNNMAP_ORACLE_LIB: a library built elsewhere from a modified copy of
+            # the source (the planted-mistake tests load mutants this way)
+            _lib = C.CDLL(os.environ.get("SNNMAP_ORACLE_LIB") or build())
             L = _lib
             vp, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
             L.orc_build.argtypes = [vp, i32, i32, vp, vp, vp, C.POINTER(vp)]
