@@ -287,14 +287,16 @@ int snnmap_partition_graph_copy(const snnmap_hgraph* h, int64_t* d_offsets, int3
                                 int64_t* d_eta, int32_t* d_axons, void* stream);
 
 /*
- * Memory for connection rows in the refinement of snnmap_partition: for the
- * levels (from the coarsest down) whose vertices times the partitions fit in
- * `bytes` (8 bytes per vertex and partition) and which merged at most an
- * eighth of their vertices into pairs, each vertex keeps its
- * connection weight and inbound overlap to every partition, updated as moves
- * are enacted and carried to the next finer level, instead of a histogram
- * per round. -1: the default, 1/4 of the device's memory; 0: none. Results do
- * not depend on it (used only when the summed omega stays below 2^31).
+ * Memory for connection rows in the refinement of snnmap_partition, and for
+ * the score matrix of small coarsening levels. On levels (from the coarsest
+ * down) whose vertices times the partitions fit in `bytes` (8 bytes per
+ * vertex and partition), each vertex can keep its connection weight and
+ * inbound overlap to every partition, updated as moves are enacted and
+ * carried to the next finer level, instead of a histogram per round; the
+ * library uses them where the measured work of the level above says they
+ * pay. Coarsening levels with V vertices use a V x V score matrix when
+ * 16 V^2 fits. -1: the default, 1/4 of the device's memory; 0: none. Results
+ * do not depend on it (used only when the summed omega stays below 2^31).
  */
 int snnmap_set_row_budget(snnmap_hgraph* h, int64_t bytes);
 
