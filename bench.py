@@ -148,6 +148,17 @@ def gpu_uuid(torch, dev):
 # algorithmic bytes per stage call (compulsory traffic: every array the
 # stage needs read once, every output written once), from level sizes
 
+def onchip_rate(pair_terms, affinity_ms):
+    """Neighbour-histogram throughput: pair updates (sum over levels of
+    |e|(|e|-1), the histogram's work) per second of the affinity stage; the
+    stage is bound by shared-memory hash updates and L2 latency, so this is
+    its efficiency figure beside the HBM fraction. None without timing."""
+    if not affinity_ms or affinity_ms <= 0:
+        return None
+    return {"pair_updates_per_s": pair_terms / (affinity_ms / 1e3), "pair_updates": pair_terms,
+            "affinity_ms": affinity_ms}
+
+
 def stage_bytes(stage, lv):
     V, E, P = lv["V"], lv["E"], lv["P"]
     if stage == "affinity":
@@ -361,6 +372,7 @@ def run_ours(args):
                        "pair_terms_all_levels": pair_terms},
             "stage_ms_per_step": {k: round(v["ms"], 3) for k, v in per_step.items()},
             "roofline": roof,
+            "onchip": onchip_rate(pair_terms, per_step.get("affinity", {}).get("ms")),
             "cpu_baseline": cb,
             "e2e": None if e2e_s is None else {
                 "value": world * hg.P / e2e_s, "unit": UNIT,

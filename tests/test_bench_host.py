@@ -1,0 +1,20 @@
+"""Host-side helpers of bench.py (no GPU): the histogram throughput figure."""
+import importlib.util
+import os
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def load_bench():
+    spec = importlib.util.spec_from_file_location("bench", os.path.join(ROOT, "bench.py"))
+    m = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(m)
+    return m
+
+
+def test_onchip_rate():
+    b = load_bench()
+    r = b.onchip_rate(2_000_000_000, 400.0)
+    assert r["pair_updates_per_s"] == 5e9
+    assert r["pair_updates"] == 2_000_000_000 and r["affinity_ms"] == 400.0
+    assert b.onchip_rate(10, 0) is None and b.onchip_rate(10, None) is None
