@@ -84,6 +84,11 @@ def lib():
             L.orc_conn.argtypes = [vp, vp]
             L.orc_gp.restype = C.c_int
             L.orc_gp.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
+            L.orc_place_trd.restype = C.c_int64
+            L.orc_place_trd.argtypes = [i32, i32, vp, vp, vp, i32, vp]
+            L.orc_place_refine.restype = C.c_int32
+            L.orc_place_refine.argtypes = [i32, i32, vp, vp, vp, i32, i32, vp, i32, vp, vp, vp,
+                                           vp, i32]
             L.orc_conn.restype = i64
             L.orc_refine.argtypes = [vp, i32, vp, vp, i32, vp, i32, vp, vp]
             L.orc_refine.restype = i32
@@ -254,3 +259,36 @@ def partition(hg, prm: Params | None = None, log_cap=1 << 14):
     levels = [{"V": g.V, "E": g.E, "P": g.P, "n_cand": g.n_cand, "n_pairs": g.n_pairs}
               for g in llog[:nl.value]]
     return rho, cost.value, stats, levels, [_round(r) for r in rlog[:nr.value]]
+
+
+def place_trd(n_nodes, off, pins, eta, width, gamma) -> int:
+    """Total residual distance of a placement (reading RP6)."""
+    lib()
+    off = np.ascontiguousarray(off, np.int64)
+    pins = np.ascontiguousarray(pins, np.int32)
+    eta = np.ascontiguousarray(eta, np.int64)
+    gamma = np.ascontiguousarray(gamma, np.int32)
+    return int(_lib.orc_place_trd(int(n_nodes), int(len(off) - 1), _ptr(off), _ptr(pins),
+                                  _ptr(eta), int(width), _ptr(gamma)))
+
+
+def place_refine(n_nodes, off, pins, eta, width, height, gamma, max_rounds=1000, log_cap=4096):
+    """Swap refinement of a placement of G_P (Sec. 4.2; readings RP1-RP6).
+    Returns (gamma, logs) with one dict per round."""
+    lib()
+    off = np.ascontiguousarray(off, np.int64)
+    pins = np.ascontiguousarray(pins, np.int32)
+    eta = np.ascontiguousarray(eta, np.int64)
+    g = np.array(gamma, dtype=np.int32, copy=True)
+    lp = np.zeros(log_cap, np.int32)
+    ls = np.zeros(log_cap, np.int32)
+    la = np.zeros(log_cap, np.int32)
+    lg = np.zeros(log_cap, np.int64)
+    r = _lib.orc_place_refine(int(n_nodes), int(len(off) - 1), _ptr(off), _ptr(pins), _ptr(eta),
+                              int(width), int(height), _ptr(g), int(max_rounds), _ptr(lp),
+                              _ptr(ls), _ptr(la), _ptr(lg), int(log_cap))
+    if r < 0:
+        raise OracleError(-r)
+    logs = [{"props": int(lp[i]), "swaps": int(ls[i]), "applied": int(la[i]),
+             "gain": int(lg[i])} for i in range(min(r, log_cap))]
+    return g, logs

@@ -423,7 +423,10 @@ int orc_cand_one(const orc_level *L, const orc_params *prm, int32_t n, int32_t *
 
 /* ------------------------------------------------------------------------ */
 /* Matching (Eq. matching). The candidate graph is a pseudo-forest rooted at
- * two-cycles. Evaluated top-down in synchronous rounds by depth: the two
+ * two-cycles, or at nodes without a candidate that others point to (never in
+ * coarsening, where validity is symmetric; empty cores in placement). By the
+ * second case of the equation such a root takes its best child. Evaluated
+ * top-down in synchronous rounds by depth: the two
  * nodes of each root two-cycle match each other; then every node of depth d
  * that is still free (not taken by its parent) takes its best child, the
  * child m with cand(m) = n of highest score(n, m) = cscore(m), ties to the
@@ -460,6 +463,9 @@ int32_t orc_match(int32_t V, const int32_t *cand, const int64_t *cscore, int32_t
             reached[n] = 1;
             front[nf++] = n;
             if (n < cand[n]) pairs++;
+        } else if (cand[n] < 0 && coff[n + 1] > coff[n]) {
+            reached[n] = 1;            /* a free root */
+            front[nf++] = n;
         }
     }
     while (nf > 0) {
@@ -1055,4 +1061,195 @@ done:
     if (cids) for (int32_t i = 0; i < cap; i++) free(cids[i]);
     free(lv); free(cids); free(cand); free(cov); free(match); free(cscore); free(rho); free(rho2);
     return err;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Placement refinement (Sec. 4.2, "Swap Proposals" and "Placement
+ * Refinement") of the partition hypergraph G_P on a width x height lattice
+ * (core id = y * width + x, Manhattan distance).
+ *
+ *  RP1 The cores adjacent to h are its 4-neighbours on the lattice.
+ *  RP2 force(p, k) = sum over hyperedges a incident to p of eta(a) times the
+ *      sum over the other pins q of a of dist(h, g(q)) - max(dist(k, g(q)), 1),
+ *      h = g(p) (Eq. force); tension(h, k) = force(pi(h), k) + force(pi(k), h)
+ *      over occupied cores (Eq. tension).
+ *  RP3 A node at h proposes the adjacent core with the largest tension, ties
+ *      to the lower core id, if that tension is positive.
+ *  RP4 Proposals over cores are matched by Eq. matching with tension as the
+ *      score (orc_match); matched pairs are disjoint swaps.
+ *  RP5 Swaps are ordered by decreasing tension, ties by the lower smaller
+ *      core id; each swap's tension is evaluated again with every earlier
+ *      swap of the sequence applied; the prefix with the largest positive
+ *      sum (shortest on ties) is applied. Rounds repeat until none is
+ *      applied, at most max_rounds.
+ *  RP6 The total residual distance is the sum over hyperedges of eta(a)
+ *      times the Manhattan distances of all unordered pairs of its pins; a
+ *      swap's tension is exactly its decrease, so every applied prefix
+ *      lowers it by its sum. */
+
+typedef struct { int32_t h, k; int64_t t; } swp;
+
+static int cmp_swp(const void *x, const void *y)
+{
+    const swp *a = (const swp *)x, *b = (const swp *)y;
+    if (a->t != b->t) return a->t > b->t ? -1 : 1;
+    return (a->h > b->h) - (a->h < b->h);
+}
+
+static int32_t mdist(int32_t width, int32_t u, int32_t v)
+{
+    int32_t dx = u % width - v % width, dy = u / width - v / width;
+    return (dx < 0 ? -dx : dx) + (dy < 0 ? -dy : dy);
+}
+
+/* force of node p (at g[p]) towards core k */
+static int64_t place_force(int32_t np, const int64_t *voff, const int32_t *vinc, const int64_t *off,
+                           const int32_t *pins, const int64_t *eta, int32_t width,
+                           const int32_t *g, int32_t p, int32_t k)
+{
+    int64_t f = 0;
+    int32_t h = g[p];
+    (void)np;
+    for (int64_t i = voff[p]; i < voff[p + 1]; i++) {
+        int32_t a = vinc[i];
+        int64_t s = 0;
+        for (int64_t j = off[a]; j < off[a + 1]; j++) {
+            int32_t q = pins[j];
+            if (q == p) continue;
+            int32_t dk = mdist(width, k, g[q]);
+            s += mdist(width, h, g[q]) - (dk > 1 ? dk : 1);
+        }
+        f += eta[a] * s;
+    }
+    return f;
+}
+
+static int64_t place_tension(int32_t np, const int64_t *voff, const int32_t *vinc,
+                             const int64_t *off, const int32_t *pins, const int64_t *eta,
+                             int32_t width, const int32_t *g, const int32_t *pi, int32_t h,
+                             int32_t k)
+{
+    int64_t t = 0;
+    if (pi[h] >= 0) t += place_force(np, voff, vinc, off, pins, eta, width, g, pi[h], k);
+    if (pi[k] >= 0) t += place_force(np, voff, vinc, off, pins, eta, width, g, pi[k], h);
+    return t;
+}
+
+int64_t orc_place_trd(int32_t np, int32_t ne, const int64_t *off, const int32_t *pins,
+                      const int64_t *eta, int32_t width, const int32_t *g)
+{
+    int64_t d = 0;
+    (void)np;
+    for (int32_t a = 0; a < ne; a++)
+        for (int64_t i = off[a]; i < off[a + 1]; i++)
+            for (int64_t j = i + 1; j < off[a + 1]; j++)
+                d += eta[a] * mdist(width, g[pins[i]], g[pins[j]]);
+    return d;
+}
+
+/* Refines the placement g (int32[np], distinct cores in [0, width*height)).
+ * Per round logs (capacity log_cap): proposals, swaps matched, swaps applied
+ * and the residual distance removed. Returns the rounds run, or a negative
+ * error code. */
+int32_t orc_place_refine(int32_t np, int32_t ne, const int64_t *off, const int32_t *pins,
+                         const int64_t *eta, int32_t width, int32_t height, int32_t *g,
+                         int32_t max_rounds, int32_t *log_props, int32_t *log_swaps,
+                         int32_t *log_applied, int64_t *log_gain, int32_t log_cap)
+{
+    int32_t nh = width * height, rounds = 0, err = 0;
+    int64_t *voff = (int64_t *)calloc((size_t)np + 1, sizeof(int64_t));
+    int64_t P = off[ne];
+    int32_t *vinc = (int32_t *)malloc(((size_t)P + 1) * sizeof(int32_t));
+    int32_t *fill = (int32_t *)calloc((size_t)np + 1, sizeof(int32_t));
+    int32_t *pi = (int32_t *)malloc(((size_t)nh + 1) * sizeof(int32_t));
+    int32_t *cand = (int32_t *)malloc(((size_t)nh + 1) * sizeof(int32_t));
+    int64_t *cscore = (int64_t *)malloc(((size_t)nh + 1) * sizeof(int64_t));
+    int32_t *match = (int32_t *)malloc(((size_t)nh + 1) * sizeof(int32_t));
+    int32_t *g2 = (int32_t *)malloc(((size_t)np + 1) * sizeof(int32_t));
+    int32_t *pi2 = (int32_t *)malloc(((size_t)nh + 1) * sizeof(int32_t));
+    swp *sw = (swp *)malloc(((size_t)nh + 1) * sizeof(swp));
+    if (!voff || !vinc || !fill || !pi || !cand || !cscore || !match || !g2 || !pi2 || !sw) {
+        err = -ORC_ERR_OOM;
+        goto done;
+    }
+    /* incident hyperedges of every node (each once) */
+    for (int32_t a = 0; a < ne; a++)
+        for (int64_t j = off[a]; j < off[a + 1]; j++) voff[pins[j] + 1]++;
+    for (int32_t p = 0; p < np; p++) voff[p + 1] += voff[p];
+    for (int32_t a = 0; a < ne; a++)
+        for (int64_t j = off[a]; j < off[a + 1]; j++) vinc[voff[pins[j]] + fill[pins[j]]++] = a;
+    for (int32_t h = 0; h < nh; h++) pi[h] = -1;
+    for (int32_t p = 0; p < np; p++) {
+        if (g[p] < 0 || g[p] >= nh || pi[g[p]] >= 0) { err = -ORC_ERR_INVALID; goto done; }
+        pi[g[p]] = p;
+    }
+    while (rounds < max_rounds) {
+        int32_t props = 0, ns = 0, istar = 0;
+        int64_t G = 0, bestG = 0;
+        /* RP3: proposals over occupied cores */
+        for (int32_t h = 0; h < nh; h++) {
+            cand[h] = -1;
+            cscore[h] = 0;
+            if (pi[h] < 0) continue;
+            int32_t x = h % width, y = h / width;
+            int32_t nb[4] = {y > 0 ? h - width : -1, x > 0 ? h - 1 : -1,
+                             x + 1 < width ? h + 1 : -1, y + 1 < height ? h + width : -1};
+            int32_t best = -1;
+            int64_t bt = 0;
+            for (int u = 0; u < 4; u++) {   /* ascending core ids */
+                int32_t k = nb[u];
+                if (k < 0) continue;
+                int64_t t = place_tension(np, voff, vinc, off, pins, eta, width, g, pi, h, k);
+                if (best < 0 || t > bt) { best = k; bt = t; }   /* ties: lower id */
+            }
+            if (best >= 0 && bt > 0) {
+                cand[h] = best;
+                cscore[h] = bt;
+                props++;
+            }
+        }
+        /* RP4 */
+        orc_match(nh, cand, cscore, match);
+        for (int32_t h = 0; h < nh; h++)
+            if (match[h] > h) {
+                sw[ns].h = h;
+                sw[ns].k = match[h];
+                sw[ns].t = place_tension(np, voff, vinc, off, pins, eta, width, g, pi, h, match[h]);
+                ns++;
+            }
+        /* RP5 */
+        qsort(sw, (size_t)ns, sizeof(swp), cmp_swp);
+        memcpy(g2, g, (size_t)np * sizeof(int32_t));
+        memcpy(pi2, pi, (size_t)nh * sizeof(int32_t));
+        for (int32_t i = 0; i < ns; i++) {
+            int32_t h = sw[i].h, k = sw[i].k;
+            G += place_tension(np, voff, vinc, off, pins, eta, width, g2, pi2, h, k);
+            int32_t a = pi2[h], b = pi2[k];
+            pi2[h] = b;
+            pi2[k] = a;
+            if (a >= 0) g2[a] = k;
+            if (b >= 0) g2[b] = h;
+            if (G > 0 && G > bestG) { bestG = G; istar = i + 1; }
+        }
+        for (int32_t i = 0; i < istar; i++) {
+            int32_t h = sw[i].h, k = sw[i].k;
+            int32_t a = pi[h], b = pi[k];
+            pi[h] = b;
+            pi[k] = a;
+            if (a >= 0) g[a] = k;
+            if (b >= 0) g[b] = h;
+        }
+        if (rounds < log_cap) {
+            if (log_props) log_props[rounds] = props;
+            if (log_swaps) log_swaps[rounds] = ns;
+            if (log_applied) log_applied[rounds] = istar;
+            if (log_gain) log_gain[rounds] = bestG;
+        }
+        rounds++;
+        if (istar == 0) break;
+    }
+done:
+    free(voff); free(vinc); free(fill); free(pi); free(cand); free(cscore); free(match);
+    free(g2); free(pi2); free(sw);
+    return err ? err : rounds;
 }

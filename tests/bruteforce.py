@@ -294,3 +294,74 @@ def components_fit(hg, prm):
 
 
 __all__ = [n for n in dir() if not n.startswith("_") and n not in ("functools", "itertools", "np")]
+
+
+# --- placement (Sec. 4.2) -------------------------------------------------
+
+def place_trd(hedges_, eta, width, gamma):
+    """Total residual distance: eta-weighted Manhattan distances of all
+    unordered pin pairs of every hyperedge."""
+    d = 0
+    for pins, w in zip(hedges_, eta):
+        for i in range(len(pins)):
+            for j in range(i + 1, len(pins)):
+                a, b = gamma[pins[i]], gamma[pins[j]]
+                d += w * (abs(a % width - b % width) + abs(a // width - b // width))
+    return d
+
+
+def place_round(hedges_, eta, width, height, gamma):
+    """One swap-refinement round restated with tension := the residual
+    distance a swap removes (recomputed from scratch), Eq. matching by the
+    memoised restatement, and the prefix by sequential recomputation.
+    Returns (new gamma, props, swaps, applied, gain)."""
+    nh = width * height
+    gamma = list(gamma)
+    pi = [-1] * nh
+    for p, h in enumerate(gamma):
+        pi[h] = p
+
+    def swapped(g, pi_, h, k):
+        g2, pi2 = list(g), list(pi_)
+        a, b = pi2[h], pi2[k]
+        pi2[h], pi2[k] = b, a
+        if a >= 0:
+            g2[a] = k
+        if b >= 0:
+            g2[b] = h
+        return g2, pi2
+
+    def tension(g, pi_, h, k):
+        g2, _ = swapped(g, pi_, h, k)
+        return place_trd(hedges_, eta, width, g) - place_trd(hedges_, eta, width, g2)
+
+    cand, cs = [-1] * nh, [0] * nh
+    props = 0
+    for h in range(nh):
+        if pi[h] < 0:
+            continue
+        x, y = h % width, h // width
+        nb = [k for k, ok in ((h - width, y > 0), (h - 1, x > 0), (h + 1, x + 1 < width),
+                              (h + width, y + 1 < height)) if ok]
+        best = None
+        for k in sorted(nb):
+            t = tension(gamma, pi, h, k)
+            if best is None or t > best[0]:
+                best = (t, k)
+        if best is not None and best[0] > 0:
+            cand[h], cs[h] = best[1], best[0]
+            props += 1
+    m = matching(cand, cs)
+    sw = sorted(((tension(gamma, pi, h, m[h]), h, m[h]) for h in range(nh) if m[h] > h),
+                key=lambda t: (-t[0], t[1]))
+    g, p_ = list(gamma), list(pi)
+    G = bestG = istar = 0
+    for i, (_, h, k) in enumerate(sw):
+        G += tension(g, p_, h, k)
+        g, p_ = swapped(g, p_, h, k)
+        if G > 0 and G > bestG:
+            bestG, istar = G, i + 1
+    g, p_ = list(gamma), list(pi)
+    for _, h, k in sw[:istar]:
+        g, p_ = swapped(g, p_, h, k)
+    return g, props, len(sw), istar, bestG

@@ -42,14 +42,23 @@ MUTANTS = [
      "g += L->w[a] * ((cf == 1 ? 1 : 0) - (ct == 0 ? 1 : 0));",
      "g += L->w[a] * ((cf == 1 ? 1 : 0) - (ct == 1 ? 1 : 0));"),
     ("prefix ties to the longest",
-     "G > 0 && G > bestG)", "G > 0 && G >= bestG)"),
+     "nviol == 0 && G > 0 && G > bestG)", "nviol == 0 && G > 0 && G >= bestG)"),
     ("G_P keeps self-cycles",
      "if (tmp[i] == s2) continue;            /* self-cycle broken */", ""),
     ("G_P loses internal weight", "inw += L->w[a];", "inw += 0;"),
+    ("force without the max(., 1) term",
+     "s += mdist(width, h, g[q]) - (dk > 1 ? dk : 1);", "s += mdist(width, h, g[q]) - dk;"),
+    ("swap proposals tie to the higher core",
+     "if (best < 0 || t > bt) { best = k; bt = t; }", "if (best < 0 || t >= bt) { best = k; bt = t; }"),
+    ("swap prefix ties to the longest",
+     "if (G > 0 && G > bestG) { bestG = G; istar = i + 1; }\n        }\n        for (int32_t i = 0; i < istar; i++) {",
+     "if (G > 0 && G >= bestG) { bestG = G; istar = i + 1; }\n        }\n        for (int32_t i = 0; i < istar; i++) {"),
+    ("matching ignores roots without a candidate",
+     "reached[n] = 1;            /* a free root */", "continue;"),
 ]
 
 BATTERY = ["tests/test_golden.py", "tests/test_gp.py", "tests/test_oracle_bruteforce.py",
-           "tests/test_oracle_invariants.py"]
+           "tests/test_oracle_invariants.py", "tests/test_placement.py"]
 
 
 @pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
