@@ -404,7 +404,9 @@ int snnmap_serve_create(const snnmap_serve_opts* opts, snnmap_server** out);
  * reported in job->status. */
 int snnmap_serve_submit(snnmap_server* s, snnmap_job* job, int64_t* ticket);
 /* Blocks until the job is done or timeout_ms passes (< 0: no limit); *done
- * (may be NULL) receives 1 if it is done. */
+ * (may be NULL) receives 1 if it is done. Any number of threads may submit
+ * and wait; a ticket must not be released while another thread waits on
+ * it. */
 int snnmap_serve_wait(snnmap_server* s, int64_t ticket, double timeout_ms, int32_t* done);
 /* The resident hierarchy of a done job submitted with keep_hierarchy (owned
  * by the server; valid until snnmap_serve_release). SNNMAP_ERR_STATE if the
