@@ -84,6 +84,10 @@ def lib():
             L.orc_conn.argtypes = [vp, vp]
             L.orc_gp.restype = C.c_int
             L.orc_gp.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
+            L.orc_hilbert_order.restype = C.c_int
+            L.orc_hilbert_order.argtypes = [i32, i32, vp]
+            L.orc_initial_sequence.restype = C.c_int
+            L.orc_initial_sequence.argtypes = [i32, i32, vp, vp, vp, vp]
             L.orc_place_trd.restype = C.c_int64
             L.orc_place_trd.argtypes = [i32, i32, vp, vp, vp, i32, vp]
             L.orc_place_refine.restype = C.c_int32
@@ -292,3 +296,38 @@ def place_refine(n_nodes, off, pins, eta, width, height, gamma, max_rounds=1000,
     logs = [{"props": int(lp[i]), "swaps": int(ls[i]), "applied": int(la[i]),
              "gain": int(lg[i])} for i in range(min(r, log_cap))]
     return g, logs
+
+
+def hilbert_order(width, height):
+    """Cores of a width x height lattice in Hilbert order (reading RI1)."""
+    lib()
+    out = np.zeros(max(width * height, 1), np.int32)
+    rc = _lib.orc_hilbert_order(int(width), int(height), _ptr(out))
+    if rc:
+        raise OracleError(rc)
+    return out[:width * height]
+
+
+def initial_sequence(n_nodes, off, pins, eta, seq0):
+    """Node order of one start of the initial placement (readings RI2-RI4)
+    from the initial order seq0."""
+    lib()
+    off = np.ascontiguousarray(off, np.int64)
+    pins = np.ascontiguousarray(pins, np.int32)
+    eta = np.ascontiguousarray(eta, np.int64)
+    seq = np.array(seq0, dtype=np.int32, copy=True)
+    rc = _lib.orc_initial_sequence(int(n_nodes), int(len(off) - 1), _ptr(off), _ptr(pins),
+                                   _ptr(eta), _ptr(seq))
+    if rc:
+        raise OracleError(rc)
+    return seq
+
+
+def initial_placement(n_nodes, off, pins, eta, width, height, seq0):
+    """gamma of one start: the i-th node of the sequence on the i-th core in
+    Hilbert order."""
+    seq = initial_sequence(n_nodes, off, pins, eta, seq0)
+    order = hilbert_order(width, height)
+    gamma = np.zeros(n_nodes, np.int32)
+    gamma[seq] = order[:n_nodes]
+    return gamma

@@ -1253,3 +1253,221 @@ done:
     free(g2); free(pi2); free(sw);
     return err ? err : rounds;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Initial placement (Sec. 4.2, "Initial Placement") of G_P on a width x
+ * height lattice, for one start (the multi-start runs several initial
+ * orders).
+ *
+ *  RI1 Cores are ordered by their index on the Hilbert curve of the
+ *      smallest power-of-two square covering the lattice (cells outside the
+ *      lattice skipped); node i of the final sequence goes to the i-th core.
+ *  RI2 Section s_0 holds every node in the given initial (random) order.
+ *      Each section of more than one node splits into its first ceil(n/2)
+ *      and its remaining nodes; recursion stops at single nodes.
+ *  RI3 Label propagation between two sibling sections L and R: the cut is
+ *      the summed eta of hyperedges with pins in both L and R (pins outside
+ *      L and R ignored). Swaps of one node of L with one of R are applied
+ *      one at a time, each time the swap lowering the cut the most (ties:
+ *      the lower node of L, then of R), while some swap lowers it, at most
+ *      4 * min(|L|, |R|) swaps; swapped nodes take each other's positions.
+ *  RI4 Folding, bottom-up: a section whose sibling S' exists is reversed
+ *      if its child more strongly connected to S' (summed eta of hyperedges
+ *      with pins in both) does not face S' -- the last child when S' lies
+ *      to its right, the first when to its left; ties keep the order.
+ *      Reversing a section reverses the order of its children and of the
+ *      nodes inside them. */
+
+static uint32_t hilbert_d(uint32_t n, uint32_t x, uint32_t y)
+{
+    uint32_t d = 0;
+    for (uint32_t s = n / 2; s > 0; s /= 2) {
+        uint32_t rx = (x & s) > 0, ry = (y & s) > 0;
+        d += s * s * ((3 * rx) ^ ry);
+        if (ry == 0) {                    /* rotate the quadrant */
+            if (rx == 1) { x = s - 1 - x; y = s - 1 - y; }
+            uint32_t t = x; x = y; y = t;
+        }
+    }
+    return d;
+}
+
+typedef struct { uint32_t d; int32_t core; } hcell;
+
+static int cmp_hcell(const void *x, const void *y)
+{
+    const hcell *a = (const hcell *)x, *b = (const hcell *)y;
+    return (a->d > b->d) - (a->d < b->d);
+}
+
+/* cores in Hilbert order (RI1) */
+int orc_hilbert_order(int32_t width, int32_t height, int32_t *order)
+{
+    uint32_t n = 1;
+    int32_t nh = width * height;
+    while (n < (uint32_t)width || n < (uint32_t)height) n <<= 1;
+    hcell *c = (hcell *)malloc(((size_t)nh + 1) * sizeof(hcell));
+    if (!c) return ORC_ERR_OOM;
+    for (int32_t k = 0; k < nh; k++) {
+        c[k].d = hilbert_d(n, (uint32_t)(k % width), (uint32_t)(k / width));
+        c[k].core = k;
+    }
+    qsort(c, (size_t)nh, sizeof(hcell), cmp_hcell);
+    for (int32_t i = 0; i < nh; i++) order[i] = c[i].core;
+    free(c);
+    return ORC_OK;
+}
+
+typedef struct {
+    int32_t np, ne;
+    const int64_t *off;
+    const int32_t *pins;
+    const int64_t *eta;
+    int32_t *side;    /* per node: 0 outside, 1 in L (or X), 2 in R (or S') */
+} ip_ctx;
+
+/* summed eta of hyperedges with pins on both sides 1 and 2 */
+static int64_t ip_cut(const ip_ctx *c)
+{
+    int64_t cut = 0;
+    for (int32_t a = 0; a < c->ne; a++) {
+        int in1 = 0, in2 = 0;
+        for (int64_t j = c->off[a]; j < c->off[a + 1]; j++) {
+            int32_t s = c->side[c->pins[j]];
+            if (s == 1) in1 = 1;
+            if (s == 2) in2 = 1;
+        }
+        if (in1 && in2) cut += c->eta[a];
+    }
+    return cut;
+}
+
+/* RI3 on seq[lo..mid) and seq[mid..hi): steepest-descent swaps */
+static int ip_label_propagation(ip_ctx *c, int32_t *seq, int32_t lo, int32_t mid, int32_t hi,
+                                int32_t *pos)
+{
+    int32_t nl = mid - lo, nr = hi - mid;
+    int32_t cap = 4 * (nl < nr ? nl : nr);
+    for (int32_t i = lo; i < hi; i++) {
+        c->side[seq[i]] = i < mid ? 1 : 2;
+        pos[seq[i]] = i;
+    }
+    int64_t cur = ip_cut(c);
+    for (int32_t it = 0; it < cap && cur > 0; it++) {
+        int32_t ba = -1, bb = -1;
+        int64_t bd = 0;
+        for (int32_t i = lo; i < mid; i++) {
+            for (int32_t j = mid; j < hi; j++) {
+                int32_t x = seq[i], y = seq[j];
+                c->side[x] = 2;
+                c->side[y] = 1;
+                int64_t d = cur - ip_cut(c);
+                c->side[x] = 1;
+                c->side[y] = 2;
+                if (d > bd || (d == bd && d > 0 && (x < ba || (x == ba && y < bb)))) {
+                    bd = d;
+                    ba = x;
+                    bb = y;
+                }
+            }
+        }
+        if (bd <= 0) break;
+        int32_t pa = pos[ba], pb = pos[bb];
+        seq[pa] = bb; seq[pb] = ba;
+        pos[ba] = pb; pos[bb] = pa;
+        c->side[ba] = 2;
+        c->side[bb] = 1;
+        cur -= bd;
+    }
+    for (int32_t i = lo; i < hi; i++) c->side[seq[i]] = 0;
+    return ORC_OK;
+}
+
+/* connection of seq[a0..a1) to seq[b0..b1) (RI4) */
+static int64_t ip_conn(ip_ctx *c, const int32_t *seq, int32_t a0, int32_t a1, int32_t b0,
+                       int32_t b1)
+{
+    for (int32_t i = a0; i < a1; i++) c->side[seq[i]] = 1;
+    for (int32_t i = b0; i < b1; i++) c->side[seq[i]] = 2;
+    int64_t x = ip_cut(c);
+    for (int32_t i = a0; i < a1; i++) c->side[seq[i]] = 0;
+    for (int32_t i = b0; i < b1; i++) c->side[seq[i]] = 0;
+    return x;
+}
+
+static void ip_reverse(int32_t *seq, int32_t lo, int32_t hi)
+{
+    for (int32_t i = lo, j = hi - 1; i < j; i++, j--) {
+        int32_t t = seq[i]; seq[i] = seq[j]; seq[j] = t;
+    }
+}
+
+/* node sequence of one start (RI2-RI4), in place on seq (initial order in,
+ * final order out) */
+int orc_initial_sequence(int32_t np, int32_t ne, const int64_t *off, const int32_t *pins,
+                         const int64_t *eta, int32_t *seq)
+{
+    int32_t *side = (int32_t *)calloc((size_t)np + 1, sizeof(int32_t));
+    int32_t *pos = (int32_t *)malloc(((size_t)np + 1) * sizeof(int32_t));
+    /* the bisection tree as intervals of seq, level by level */
+    int32_t cap = 2 * (np > 0 ? np : 1) + 2;
+    int32_t *lo = (int32_t *)malloc((size_t)cap * sizeof(int32_t));
+    int32_t *hi = (int32_t *)malloc((size_t)cap * sizeof(int32_t));
+    int32_t *par = (int32_t *)malloc((size_t)cap * sizeof(int32_t));
+    int32_t *depth = (int32_t *)malloc((size_t)cap * sizeof(int32_t));
+    int32_t *kid = (int32_t *)malloc((size_t)cap * sizeof(int32_t));   /* first child or -1 */
+    int err = ORC_OK;
+    ip_ctx c = {np, ne, off, pins, eta, side};
+    if (!side || !pos || !lo || !hi || !par || !depth || !kid) { err = ORC_ERR_OOM; goto done; }
+    if (np <= 1) goto done;
+    {
+        int32_t nn = 1, maxd = 0;
+        lo[0] = 0; hi[0] = np; par[0] = -1; depth[0] = 0; kid[0] = -1;
+        /* RI2 + RI3: split breadth-first, propagate labels between siblings */
+        for (int32_t s = 0; s < nn; s++) {
+            int32_t n = hi[s] - lo[s];
+            if (n <= 1) continue;
+            int32_t mid = lo[s] + (n + 1) / 2;
+            err = ip_label_propagation(&c, seq, lo[s], mid, hi[s], pos);
+            if (err) goto done;
+            kid[s] = nn;
+            for (int t = 0; t < 2; t++) {
+                lo[nn] = t ? mid : lo[s];
+                hi[nn] = t ? hi[s] : mid;
+                par[nn] = s;
+                depth[nn] = depth[s] + 1;
+                kid[nn] = -1;
+                if (depth[nn] > maxd) maxd = depth[nn];
+                nn++;
+            }
+        }
+        /* RI4: deepest sections first; a section's sibling is the other
+         * child of its parent (the root has none) */
+        for (int32_t d = maxd; d >= 1; d--) {
+            for (int32_t s = 0; s < nn; s++) {
+                if (depth[s] != d || kid[s] < 0) continue;   /* leaves need no orientation */
+                int32_t p = par[s];
+                int32_t sib = kid[p] == s ? kid[p] + 1 : kid[p];
+                int32_t a = kid[s], b = kid[s] + 1;         /* first and last child */
+                int64_t ca = ip_conn(&c, seq, lo[a], hi[a], lo[sib], hi[sib]);
+                int64_t cb = ip_conn(&c, seq, lo[b], hi[b], lo[sib], hi[sib]);
+                int right = lo[sib] > lo[s];              /* sibling to the right */
+                int flip = right ? (ca > cb) : (cb > ca);
+                if (flip) {
+                    ip_reverse(seq, lo[s], hi[s]);
+                    /* children swap places; their intervals follow */
+                    int32_t na = hi[a] - lo[a];
+                    int32_t nb2 = hi[b] - lo[b];
+                    (void)na;
+                    lo[b] = lo[s]; hi[b] = lo[s] + nb2;
+                    lo[a] = hi[b]; hi[a] = hi[s];
+                    /* deeper descendants were final already; their intervals
+                     * are not read again */
+                }
+            }
+        }
+    }
+done:
+    free(side); free(pos); free(lo); free(hi); free(par); free(depth); free(kid);
+    return err;
+}

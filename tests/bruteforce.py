@@ -365,3 +365,50 @@ def place_round(hedges_, eta, width, height, gamma):
     for _, h, k in sw[:istar]:
         g, p_ = swapped(g, p_, h, k)
     return g, props, len(sw), istar, bestG
+
+
+def initial_sequence(hedges_, eta, seq0):
+    """Readings RI2-RI4 restated recursively on node sets: halving, steepest
+    swaps between the halves, then bottom-up orientation against each
+    section's sibling."""
+    def cut(A, B):
+        return sum(w for e, w in zip(hedges_, eta) if set(e) & A and set(e) & B)
+
+    def build(seq):
+        if len(seq) <= 1:
+            return {"seq": list(seq), "kids": None}
+        mid = (len(seq) + 1) // 2
+        L, R = list(seq[:mid]), list(seq[mid:])
+        cur = cut(set(L), set(R))
+        for _ in range(4 * min(len(L), len(R))):
+            best = None
+            for x in L:
+                for y in R:
+                    L2 = [y if v == x else v for v in L]
+                    R2 = [x if v == y else v for v in R]
+                    d = cur - cut(set(L2), set(R2))
+                    if d > 0 and (best is None or (-d, x, y) < (-best[0], best[1], best[2])):
+                        best = (d, x, y, L2, R2)
+            if best is None:
+                break
+            cur -= best[0]
+            L, R = best[3], best[4]
+        return {"seq": None, "kids": [build(L), build(R)]}
+
+    def flat(t):
+        return t["seq"] if t["kids"] is None else flat(t["kids"][0]) + flat(t["kids"][1])
+
+    def orient(t, sib=None, sib_right=None):
+        if t["kids"] is None:
+            return t["seq"]
+        a, b = t["kids"]
+        sa = orient(a, set(flat(b)), True)
+        sb = orient(b, set(flat(a)), False)
+        seq = sa + sb
+        if sib is not None:
+            ca, cb = cut(set(sa), sib), cut(set(sb), sib)
+            if (ca > cb) if sib_right else (cb > ca):
+                seq = seq[::-1]
+        return seq
+
+    return orient(build(list(seq0)))

@@ -55,10 +55,34 @@ MUTANTS = [
      "if (G > 0 && G >= bestG) { bestG = G; istar = i + 1; }\n        }\n        for (int32_t i = 0; i < istar; i++) {"),
     ("matching ignores roots without a candidate",
      "reached[n] = 1;            /* a free root */", "continue;"),
+    ("folding faces the weaker child to the sibling",
+     "int flip = right ? (ca > cb) : (cb > ca);", "int flip = right ? (cb > ca) : (ca > cb);"),
+    ("bisection halves at the floor",
+     "int32_t mid = lo[s] + (n + 1) / 2;", "int32_t mid = lo[s] + n / 2;"),
+    ("bisection swaps tie to the higher node",
+     "(d == bd && d > 0 && (x < ba || (x == ba && y < bb)))",
+     "(d == bd && d > 0 && (x > ba || (x == ba && y > bb)))"),
+    ("Hilbert quadrant not mirrored",
+     "if (rx == 1) { x = s - 1 - x; y = s - 1 - y; }", "if (0) { x = s - 1 - x; y = s - 1 - y; }"),
 ]
 
 BATTERY = ["tests/test_golden.py", "tests/test_gp.py", "tests/test_oracle_bruteforce.py",
-           "tests/test_oracle_invariants.py", "tests/test_placement.py"]
+           "tests/test_oracle_invariants.py", "tests/test_placement.py",
+           "tests/test_initial_placement.py"]
+
+
+# the pin file closest to each mutant runs first (-x stops at the first
+# failure; the mutant must fail the battery either way)
+FIRST = {"force without the max(., 1) term": "tests/test_placement.py",
+         "swap proposals tie to the higher core": "tests/test_placement.py",
+         "swap prefix ties to the longest": "tests/test_placement.py",
+         "matching ignores roots without a candidate": "tests/test_placement.py",
+         "folding faces the weaker child to the sibling": "tests/test_initial_placement.py",
+         "bisection halves at the floor": "tests/test_initial_placement.py",
+         "bisection swaps tie to the higher node": "tests/test_initial_placement.py",
+         "Hilbert quadrant not mirrored": "tests/test_initial_placement.py",
+         "G_P keeps self-cycles": "tests/test_gp.py",
+         "G_P loses internal weight": "tests/test_gp.py"}
 
 
 @pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
@@ -71,7 +95,9 @@ def test_planted_mistake_fails_a_pin(name, old, new, tmp_path):
     subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-w", "-o", str(lib),
                            str(mut)])
     env = dict(os.environ, SNNMAP_ORACLE_LIB=str(lib))
+    first = FIRST.get(name)
+    battery = ([first] if first else []) + [f for f in BATTERY if f != first]
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        "-k", "not cfg2s", *BATTERY], cwd=ROOT, env=env,
+                        "-k", "not cfg2s", *battery], cwd=ROOT, env=env,
                        capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"mutant survived the pins: {name}"
