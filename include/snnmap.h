@@ -427,6 +427,72 @@ int snnmap_serve_destroy(snnmap_server* s);
  * keep_hierarchy is ignored. */
 int snnmap_batch_partition(snnmap_job* jobs, int32_t n_jobs, const snnmap_serve_opts* opts);
 
+/*
+ * Placement swap refinement (Sec. 4.2, "Swap Proposals" and "Placement
+ * Refinement") of the partition hypergraph G_P = (P, A, eta) on a width x
+ * height lattice of cores, core h = y * width + x, distances Manhattan.
+ *
+ * Per round, each node p on core h = gamma(p) has a force towards every
+ * adjacent core k (Eq. force: the sum over its hyperedges a of eta(a) times
+ * the sum over the other pins q of dist(h, gamma(q)) - max(dist(k,
+ * gamma(q)), 1)); the tension of two adjacent cores is the sum of the forces
+ * of their occupants towards each other (Eq. tension; an empty core adds
+ * nothing). Each occupied core proposes the adjacent core of largest
+ * tension (the lowest core id on ties) when that tension is positive; the
+ * proposals are matched by Eq. matching with tension as the score (an empty
+ * core proposes nothing but may take its best proposer); the matched swaps,
+ * ordered by decreasing tension (ties: lower core id first), are each
+ * re-evaluated with every earlier swap applied, and the prefix with the
+ * largest positive sum (the shortest on ties) is applied. Rounds repeat
+ * until one applies nothing, or max_rounds have run. A swap's re-evaluated
+ * tension is exactly the drop of the total residual distance (see
+ * snnmap_place_trd), so every round lowers it by its logged gain.
+ *
+ * Multi-start: n_starts placements are refined together (the paper refines
+ * its Pi starts concurrently); each one's result equals its refinement
+ * alone. d_gamma: device int32[n_starts * n_nodes], start-major, gamma of
+ * start s at d_gamma[s * n_nodes ..], refined in place; every start's cores
+ * must be distinct and in [0, width * height).
+ *
+ * G_P: d_offsets int64[n_hedges + 1] (from 0, non-decreasing), d_pins int32
+ * (node ids in [0, n_nodes); a repeated pin counts as often as it appears),
+ * d_eta int64[n_hedges]; all device memory, owned by the caller, read only.
+ * Sums are int64 and exact while sum_a eta(a) |a|^2 (width + height) < 2^63.
+ *
+ * Outputs on the host: h_rounds_out[n_starts] (may be NULL) receives each
+ * start's rounds, the last one applying nothing unless max_rounds stopped
+ * it; h_log (may be NULL) receives round r of start s at h_log[s * log_cap
+ * + r] for r < min(rounds, log_cap).
+ *
+ * Errors: SNNMAP_ERR_INVALID (negative sizes or max_rounds, width or height
+ * < 1, n_starts < 1, n_starts * width * height >= 2^31, n_nodes > width *
+ * height, host pointers, malformed offsets, a pin or core out of range, two
+ * nodes of one start on one core; d_gamma is then unchanged),
+ * SNNMAP_ERR_OOM, SNNMAP_ERR_CUDA.
+ */
+typedef struct {
+    int32_t props;    /* occupied cores that proposed a swap */
+    int32_t swaps;    /* swaps in the matching */
+    int32_t applied;  /* length of the applied prefix (0: none) */
+    int32_t reserved;
+    int64_t gain;     /* summed re-evaluated tension of the applied prefix */
+} snnmap_place_log;
+
+int snnmap_place_refine(int32_t n_nodes, int32_t n_hedges, const int64_t* d_offsets,
+                        const int32_t* d_pins, const int64_t* d_eta, int32_t width,
+                        int32_t height, int32_t n_starts, int32_t* d_gamma, int32_t max_rounds,
+                        void* stream, int32_t* h_rounds_out, snnmap_place_log* h_log,
+                        int32_t log_cap);
+
+/* Total residual distance of each start's placement (the measure by which
+ * Sec. 4.2 picks the best of its multi-start results): sum over hyperedges
+ * a of eta(a) times the Manhattan distances between the cores of every
+ * unordered pair of its pins. Arguments as in snnmap_place_refine; d_gamma
+ * is read only; h_trd_out: host int64[n_starts]. Same errors. */
+int snnmap_place_trd(int32_t n_nodes, int32_t n_hedges, const int64_t* d_offsets,
+                     const int32_t* d_pins, const int64_t* d_eta, int32_t width, int32_t height,
+                     int32_t n_starts, const int32_t* d_gamma, void* stream, int64_t* h_trd_out);
+
 /* Kernels launched by the library in this process so far. */
 int64_t snnmap_launch_count(void);
 

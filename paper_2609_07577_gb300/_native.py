@@ -60,6 +60,12 @@ class ServeOpts(C.Structure):
     _fields_ = [("slots", C.c_int32), ("dry_run_us", C.c_int32), ("mem_budget", C.c_int64)]
 
 
+class PlaceLog(C.Structure):
+    """snnmap_place_log: one round of placement swap refinement."""
+    _fields_ = [("props", C.c_int32), ("swaps", C.c_int32), ("applied", C.c_int32),
+                ("reserved", C.c_int32), ("gain", C.c_int64)]
+
+
 class SnnmapError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"snnmap error {code}: {msg}")
@@ -110,6 +116,9 @@ _SIGS = {
     "snnmap_serve_info": (C.c_int, [_vp, C.POINTER(_i32), C.POINTER(_i32), C.POINTER(_i64)]),
     "snnmap_serve_destroy": (C.c_int, [_vp]),
     "snnmap_batch_partition": (C.c_int, [C.POINTER(Job), _i32, C.POINTER(ServeOpts)]),
+    "snnmap_place_refine": (C.c_int, [_i32, _i32, _vp, _vp, _vp, _i32, _i32, _i32, _vp, _i32,
+                                      _vp, _vp, _vp, _i32]),
+    "snnmap_place_trd": (C.c_int, [_i32, _i32, _vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp, _vp]),
     "snnmap_free": (None, [_vp]),
     "snnmap_last_error": (C.c_char_p, []),
 }
@@ -367,6 +376,38 @@ def snnmap_partition_graph_copy(h, d_offsets=None, d_pins=None, d_eta=None, d_ax
                                 stream=None):
     check(lib().snnmap_partition_graph_copy(h, _p(d_offsets), _p(d_pins), _p(d_eta), _p(d_axons),
                                             _stream(stream)))
+
+
+def snnmap_place_refine(n_nodes, n_hedges, d_offsets, d_pins, d_eta, width, height, n_starts,
+                        d_gamma, max_rounds, stream=None, log_cap=0):
+    """Refines n_starts placements of G_P in d_gamma (device int32[n_starts *
+    n_nodes]) in place; returns (rounds per start, logs per start as lists
+    of dicts, up to log_cap rounds each)."""
+    S = int(n_starts)
+    rounds = (C.c_int32 * max(S, 1))()
+    cap = max(int(log_cap), 0)
+    logs = (PlaceLog * max(S * cap, 1))()
+    check(lib().snnmap_place_refine(int(n_nodes), int(n_hedges), _p(d_offsets), _p(d_pins),
+                                    _p(d_eta), int(width), int(height), S, _p(d_gamma),
+                                    int(max_rounds), _stream(stream), rounds,
+                                    logs if cap else None, cap))
+    out = []
+    for i in range(S):
+        n = min(rounds[i], cap)
+        out.append([{"props": L.props, "swaps": L.swaps, "applied": L.applied, "gain": L.gain}
+                    for L in logs[i * cap:i * cap + n]])
+    return [rounds[i] for i in range(S)], out
+
+
+def snnmap_place_trd(n_nodes, n_hedges, d_offsets, d_pins, d_eta, width, height, n_starts,
+                     d_gamma, stream=None):
+    """Total residual distance of each start's placement (list of ints)."""
+    S = int(n_starts)
+    out = (C.c_int64 * max(S, 1))()
+    check(lib().snnmap_place_trd(int(n_nodes), int(n_hedges), _p(d_offsets), _p(d_pins),
+                                 _p(d_eta), int(width), int(height), S, _p(d_gamma),
+                                 _stream(stream), out))
+    return [out[i] for i in range(S)]
 
 
 def snnmap_set_row_budget(h, nbytes):

@@ -392,4 +392,62 @@ Status coarsen_level(snnmap_hgraph* h, int32_t* n_cand, int32_t* n_pairs)
     return Status{};
 }
 
+// Eq. matching over any candidate pseudo-forest, for callers outside
+// coarsening: the same kernels as coarsen_level, with its own scalars. A
+// vertex without a candidate may still have children (never so in
+// coarsening, where validity is symmetric); it then tops its chain at even
+// distance and takes its best child, as the equation's second case says.
+Status match_forest(int32_t V, const int32_t* cand, const int64_t* cscore, int32_t* match,
+                    int64_t* d_scal, Arena& ar, cudaStream_t s, int64_t* n_pairs)
+{
+    *n_pairs = 0;
+    if (V <= 0) return Status{};
+    int g = grid_for(V, 256);
+    int64_t h_scal[SC_COUNT];
+    int64_t* bestsc;
+    int32_t *bc, *link, *nxt, *nxt2;
+    uint8_t *par, *pj, *pj2;
+    SNN_TRY(ar.alloc(&bestsc, V));
+    SNN_TRY(ar.alloc(&bc, V));
+    SNN_TRY(ar.alloc(&link, V));
+    SNN_TRY(ar.alloc(&par, V));
+    SNN_CUDA(cudaMemsetAsync(d_scal, 0, SC_COUNT * sizeof(int64_t), s));
+    SNN_TRY(fill_i64(bestsc, INT64_MIN, V, s));
+    SNN_TRY(fill_i32(bc, 0x7fffffff, V, s));
+    SNN_L k_child_best_score<<<g, 256, 0, s>>>(V, cand, cscore, bestsc);
+    SNN_L k_child_best_id<<<g, 256, 0, s>>>(V, cand, cscore, bestsc, bc);
+    SNN_L k_link<<<g, 256, 0, s>>>(V, cand, bc, link);
+    SNN_L k_walk<<<g, 256, 0, s>>>(V, link, par, d_scal);
+    SNN_CUDA(cudaGetLastError());
+    SNN_CUDA(cudaMemcpyAsync(h_scal, d_scal, sizeof(h_scal), cudaMemcpyDeviceToHost, s));
+    SNN_CUDA(cudaStreamSynchronize(s));
+    if (h_scal[SC_B] > 0) {
+        SNN_TRY(ar.alloc(&nxt, V));
+        SNN_TRY(ar.alloc(&nxt2, V));
+        SNN_TRY(ar.alloc(&pj, V));
+        SNN_TRY(ar.alloc(&pj2, V));
+        SNN_L k_jump_init<<<g, 256, 0, s>>>(V, link, nxt, pj);
+        SNN_CUDA(cudaGetLastError());
+        for (int it = 0; it < 40; it++) {
+            SNN_CUDA(cudaMemsetAsync(d_scal, 0, SC_COUNT * sizeof(int64_t), s));
+            SNN_L k_jump<<<g, 256, 0, s>>>(V, nxt, pj, nxt2, pj2, d_scal);
+            SNN_CUDA(cudaGetLastError());
+            std::swap(nxt, nxt2);
+            std::swap(pj, pj2);
+            SNN_CUDA(cudaMemcpyAsync(h_scal, d_scal, sizeof(h_scal), cudaMemcpyDeviceToHost, s));
+            SNN_CUDA(cudaStreamSynchronize(s));
+            if (h_scal[SC_B] == 0) break;
+        }
+        SNN_L k_jump_done<<<g, 256, 0, s>>>(V, pj, par);
+        SNN_CUDA(cudaGetLastError());
+    }
+    SNN_CUDA(cudaMemsetAsync(d_scal, 0, SC_COUNT * sizeof(int64_t), s));
+    SNN_L k_match_finish<<<g, 256, 0, s>>>(V, cand, bc, par, match, d_scal);
+    SNN_CUDA(cudaGetLastError());
+    SNN_CUDA(cudaMemcpyAsync(h_scal, d_scal, sizeof(h_scal), cudaMemcpyDeviceToHost, s));
+    SNN_CUDA(cudaStreamSynchronize(s));
+    *n_pairs = h_scal[SC_C];
+    return Status{};
+}
+
 }  // namespace snn

@@ -168,6 +168,10 @@ Status build_incidence(snnmap_hgraph* h, Level& L);
 
 // S1 + S2 on the coarsest level: fills h->cand/cscore/cov/match
 Status coarsen_level(snnmap_hgraph* h, int32_t* n_cand, int32_t* n_pairs);
+// Eq. matching of a candidate pseudo-forest (cand[v] = -1: none) into match
+// (-1: unmatched); d_scal: device int64[SC_COUNT] scratch; *n_pairs: pairs.
+Status match_forest(int32_t V, const int32_t* cand, const int64_t* cscore, int32_t* match,
+                    int64_t* d_scal, Arena& ar, cudaStream_t s, int64_t* n_pairs);
 // S3: next level from h->match
 Status contract_level(snnmap_hgraph* h);
 // materializes levels[dst] from resident levels[src] through map (V(src) ids)

@@ -1,0 +1,148 @@
+"""The placement refinement kernels' steps (csrc/place_items.cuh) run on the
+host in the kernels' phase order (tests/place_emul.cpp) and compared with
+the oracle (Sec. 4.2; readings RP1-RP6): per start, the same placement, the
+same rounds and the same per-round logs, for single starts and for several
+starts refined together; the total residual distance agrees too. This pins
+the GPU path's decomposition (forces per pin entry, tensions from
+directional forces, re-evaluation through ranks, per-start prefixes) on the
+CPU; the GPU parity tests run the kernels themselves."""
+import ctypes as C
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+import snngen
+from test_placement import csr, random_case
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(os.path.dirname(HERE), "paper_2609_07577_gb300", "csrc")
+
+
+@pytest.fixture(scope="module")
+def emul(tmp_path_factory):
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if not cxx:
+        pytest.skip("no C++ compiler")
+    out = str(tmp_path_factory.mktemp("emul") / "libplace_emul.so")
+    subprocess.run([cxx, "-O2", "-std=c++17", "-shared", "-fPIC", "-I", CSRC,
+                    os.path.join(HERE, "place_emul.cpp"), "-o", out], check=True)
+    L = C.CDLL(out)
+    vp, i32 = C.c_void_p, C.c_int32
+    L.emul_place_refine.restype = C.c_int
+    L.emul_place_refine.argtypes = [i32, i32, vp, vp, vp, i32, i32, i32, vp, i32, vp, vp, vp,
+                                    vp, vp, i32]
+    L.emul_place_trd.restype = None
+    L.emul_place_trd.argtypes = [i32, i32, vp, vp, vp, i32, i32, vp, vp]
+    return L
+
+
+def ptr(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def run_emul(L, n, off, pins, eta, width, height, gammas, max_rounds=1000, cap=4096):
+    S = len(gammas)
+    off = np.ascontiguousarray(off, np.int64)
+    pins = np.ascontiguousarray(pins, np.int32)
+    eta = np.ascontiguousarray(eta, np.int64)
+    g = np.ascontiguousarray(np.concatenate([np.asarray(x, np.int32) for x in gammas])
+                             if n else np.zeros(0, np.int32))
+    rounds = np.zeros(S, np.int32)
+    lp = np.zeros(S * cap, np.int32)
+    ls = np.zeros(S * cap, np.int32)
+    la = np.zeros(S * cap, np.int32)
+    lg = np.zeros(S * cap, np.int64)
+    rc = L.emul_place_refine(n, len(off) - 1, ptr(off), ptr(pins), ptr(eta), width, height, S,
+                             ptr(g), max_rounds, ptr(rounds), ptr(lp), ptr(ls), ptr(la), ptr(lg),
+                             cap)
+    if rc:
+        return rc, None, None
+    outs, logs = [], []
+    for s in range(S):
+        outs.append(g[s * n:(s + 1) * n].tolist())
+        logs.append([{"props": int(lp[s * cap + r]), "swaps": int(ls[s * cap + r]),
+                      "applied": int(la[s * cap + r]), "gain": int(lg[s * cap + r])}
+                     for r in range(min(int(rounds[s]), cap))])
+    return 0, outs, logs
+
+
+def trd_emul(L, n, off, pins, eta, width, gammas):
+    S = len(gammas)
+    off = np.ascontiguousarray(off, np.int64)
+    pins = np.ascontiguousarray(pins, np.int32)
+    eta = np.ascontiguousarray(eta, np.int64)
+    g = np.ascontiguousarray(np.concatenate([np.asarray(x, np.int32) for x in gammas]))
+    out = np.zeros(S, np.int64)
+    L.emul_place_trd(n, len(off) - 1, ptr(off), ptr(pins), ptr(eta), width, S, ptr(g), ptr(out))
+    return out.tolist()
+
+
+def test_single_start_matches_oracle(emul):
+    compared = moved = 0
+    for seed in range(600):
+        width, height, n, hedges_, eta, gamma = random_case(seed)
+        off, pins = csr(hedges_)
+        want_g, want_logs = oracle.place_refine(n, off, pins, eta, width, height, gamma)
+        rc, got, logs = run_emul(emul, n, off, pins, eta, width, height, [gamma])
+        assert rc == 0, seed
+        assert got[0] == want_g.tolist(), seed
+        assert logs[0] == want_logs, seed
+        compared += 1
+        moved += any(r["applied"] for r in want_logs)
+    assert compared == 600 and moved > 150
+
+
+def gp_case(seed, n_starts):
+    """G_P of a small SNN under the oracle's partition, on the smallest
+    near-square lattice that holds it, with n_starts random placements."""
+    hg = snngen.tiny_random(seed) if seed % 2 else snngen.by_name("cfg1s")
+    rho, _, st, *_ = oracle.partition(hg, oracle.params_of(hg))
+    K = int(st["n_parts"])
+    L = oracle.Level.from_hypergraph(hg, oracle.params_of(hg))
+    gp = L.partition_graph(rho)
+    off, pins, eta = gp["off"], gp["pins"], gp["eta"]
+    width = int(np.ceil(np.sqrt(K)))
+    height = int(np.ceil(K / width)) + (seed % 3 == 0)   # some lattices with empty rows
+    rng = np.random.Generator(np.random.PCG64(seed))
+    gammas = [rng.choice(width * height, size=K, replace=False) for _ in range(n_starts)]
+    return K, off, pins, eta, width, height, gammas
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3, 5])
+def test_multi_start_equals_each_start_alone(emul, seed):
+    K, off, pins, eta, width, height, gammas = gp_case(seed, 5)
+    rc, got, logs = run_emul(emul, K, off, pins, eta, width, height, gammas)
+    assert rc == 0
+    for s, gamma in enumerate(gammas):
+        want_g, want_logs = oracle.place_refine(K, off, pins, eta, width, height, gamma)
+        assert got[s] == want_g.tolist(), s
+        assert logs[s] == want_logs, s
+    trds = trd_emul(emul, K, off, pins, eta, width, got)
+    assert trds == [oracle.place_trd(K, off, pins, eta, width, g) for g in got]
+
+
+def test_multi_start_random_cases(emul):
+    rng = np.random.Generator(np.random.PCG64(77))
+    for seed in range(200):
+        width, height, n, hedges_, eta, gamma = random_case(5000 + seed)
+        off, pins = csr(hedges_)
+        gammas = [gamma] + [rng.choice(width * height, size=n, replace=False).tolist()
+                            for _ in range(int(rng.integers(1, 4)))]
+        mr = int(rng.integers(1, 6))
+        rc, got, logs = run_emul(emul, n, off, pins, eta, width, height, gammas, max_rounds=mr)
+        assert rc == 0
+        for s, gm in enumerate(gammas):
+            want_g, want_logs = oracle.place_refine(n, off, pins, eta, width, height, gm,
+                                                    max_rounds=mr)
+            assert got[s] == want_g.tolist(), (seed, s)
+            assert logs[s] == want_logs, (seed, s)
+
+
+def test_invalid_placement_rejected(emul):
+    off, pins = csr([[0, 1]])
+    assert run_emul(emul, 2, off, pins, [1], 2, 1, [[0, 0]])[0] == 1
+    assert run_emul(emul, 2, off, pins, [1], 2, 1, [[0, 2]])[0] == 1
