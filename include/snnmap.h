@@ -493,6 +493,51 @@ int snnmap_place_trd(int32_t n_nodes, int32_t n_hedges, const int64_t* d_offsets
                      const int32_t* d_pins, const int64_t* d_eta, int32_t width, int32_t height,
                      int32_t n_starts, const int32_t* d_gamma, void* stream, int64_t* h_trd_out);
 
+/*
+ * Initial placement of G_P (Sec. 4.2, "Initial Placement") for n_starts
+ * starts at once. Each start's node sequence begins as its given order
+ * (d_seq0: device int32[n_starts * n_nodes], start-major, each a
+ * permutation of [0, n_nodes); the paper draws them at random). The
+ * sequence is bisected recursively (a section of n nodes into its first
+ * ceil(n/2) and its remaining ones, down to single nodes); between the two
+ * halves of every section, label propagation applies, one at a time, the
+ * swap of a node of each half that lowers their cut the most (the summed
+ * eta of hyperedges with pins in both halves, pins elsewhere ignored; ties
+ * to the lower node of the first half, then of the second) while one lowers
+ * it, at most 4 * min(size of the halves) swaps. Folding, bottom-up,
+ * reverses a section (with everything inside it) when its child more
+ * strongly connected to the section's sibling does not face that sibling
+ * (ties keep the order). The i-th node of the final sequence goes to the
+ * i-th core in Hilbert order (snnmap_hilbert_order).
+ *
+ * G_P as in snnmap_place_refine; the pins of a hyperedge must be distinct.
+ * Outputs (device, start-major): d_seq_out int32[n_starts * n_nodes] the
+ * final sequences (may be NULL), d_gamma_out int32[n_starts * n_nodes] the
+ * placements (node -> core), ready for snnmap_place_refine.
+ *
+ * Work: per label-propagation round of a pair of halves of sizes nL, nR, an
+ * nL x nR matrix of int64 (device memory grows with n_starts * n_nodes^2 /
+ * 4 for the top split).
+ *
+ * Errors: SNNMAP_ERR_INVALID (negative sizes, width or height < 1,
+ * n_starts outside [1, 65535], width * height or n_starts * n_nodes >= 2^31,
+ * n_nodes > width * height, host pointers, malformed offsets, a pin out of
+ * range or repeated within its hyperedge, an initial order that is not a
+ * permutation), SNNMAP_ERR_OOM, SNNMAP_ERR_CUDA.
+ */
+int snnmap_place_initial(int32_t n_nodes, int32_t n_hedges, const int64_t* d_offsets,
+                         const int32_t* d_pins, const int64_t* d_eta, int32_t width,
+                         int32_t height, int32_t n_starts, const int32_t* d_seq0,
+                         int32_t* d_seq_out, int32_t* d_gamma_out, void* stream);
+
+/* The cores of a width x height lattice (core = y * width + x) in Hilbert
+ * order: ordered by their index along the Hilbert curve of the smallest
+ * power-of-two square covering the lattice, cells outside the lattice
+ * skipped. d_order_out: device int32[width * height]. Errors:
+ * SNNMAP_ERR_INVALID (width or height < 1, width * height >= 2^31, a host
+ * pointer), SNNMAP_ERR_OOM, SNNMAP_ERR_CUDA. */
+int snnmap_hilbert_order(int32_t width, int32_t height, int32_t* d_order_out, void* stream);
+
 /* Kernels launched by the library in this process so far. */
 int64_t snnmap_launch_count(void);
 

@@ -119,6 +119,9 @@ _SIGS = {
     "snnmap_place_refine": (C.c_int, [_i32, _i32, _vp, _vp, _vp, _i32, _i32, _i32, _vp, _i32,
                                       _vp, _vp, _vp, _i32]),
     "snnmap_place_trd": (C.c_int, [_i32, _i32, _vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp, _vp]),
+    "snnmap_place_initial": (C.c_int, [_i32, _i32, _vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp,
+                                       _vp, _vp]),
+    "snnmap_hilbert_order": (C.c_int, [_i32, _i32, _vp, _vp]),
     "snnmap_free": (None, [_vp]),
     "snnmap_last_error": (C.c_char_p, []),
 }
@@ -408,6 +411,22 @@ def snnmap_place_trd(n_nodes, n_hedges, d_offsets, d_pins, d_eta, width, height,
                                  _p(d_eta), int(width), int(height), S, _p(d_gamma),
                                  _stream(stream), out))
     return [out[i] for i in range(S)]
+
+
+def snnmap_place_initial(n_nodes, n_hedges, d_offsets, d_pins, d_eta, width, height, n_starts,
+                         d_seq0, d_gamma_out, d_seq_out=None, stream=None):
+    """Initial placements of n_starts starts from their initial orders
+    d_seq0 (device int32[n_starts * n_nodes]) into d_gamma_out (and the
+    final sequences into d_seq_out if given)."""
+    check(lib().snnmap_place_initial(int(n_nodes), int(n_hedges), _p(d_offsets), _p(d_pins),
+                                     _p(d_eta), int(width), int(height), int(n_starts),
+                                     _p(d_seq0), _p(d_seq_out), _p(d_gamma_out),
+                                     _stream(stream)))
+
+
+def snnmap_hilbert_order(width, height, d_order_out, stream=None):
+    """Cores of a width x height lattice in Hilbert order (device int32)."""
+    check(lib().snnmap_hilbert_order(int(width), int(height), _p(d_order_out), _stream(stream)))
 
 
 def snnmap_set_row_budget(h, nbytes):

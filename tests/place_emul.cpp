@@ -1,10 +1,15 @@
-// Host run of the placement refinement kernels' steps: the per-item
+// Host run of the placement kernels' steps. Refinement: the per-item
 // functions of csrc/place_items.cuh, called one item at a time in the phase
 // order of the kernels in csrc/place.cu (forces summed per pin entry,
 // proposals per core over all starts, Eq. matching in the matching kernels'
 // formulation, swaps sorted by tension then by start, re-evaluation through
-// ranks, per-start best prefix, apply). It checks that decomposition against
-// the oracle without a GPU. Test infrastructure only; built by the tests.
+// ranks, per-start best prefix, apply). Initial placement: those of
+// csrc/initial_items.cuh in the order of csrc/initial.cu (label propagation
+// of all jobs of a depth in lockstep rounds through single-move gains and a
+// correction matrix, folding from the post-propagation section sets, Hilbert
+// order). It checks those decompositions against the oracle without a GPU.
+// Test infrastructure only; built by the tests.
+#include "initial_items.cuh"
 #include "place_items.cuh"
 
 #include <algorithm>
@@ -208,6 +213,176 @@ void emul_place_trd(int32_t np, int32_t ne, const int64_t* off, const int32_t* p
                 acc += eta[a] * trd_terms(pins, j, off[a + 1], g + (int64_t)s * np, width);
         out[s] = acc;
     }
+}
+
+
+// Same contract as snnmap_place_initial on host arrays (seq_out and gamma:
+// int32[S * np]). Returns 0 or 1 (invalid input).
+int emul_place_initial(int32_t np, int32_t ne, const int64_t* off, const int32_t* pins,
+                       const int64_t* eta, int32_t width, int32_t height, int32_t S,
+                       const int32_t* seq0, int32_t* seq_out, int32_t* gamma)
+{
+    namespace ip = snn::initial;
+    const int64_t P = off[ne];
+    std::vector<int32_t> hid((size_t)P), deg(np, 0);
+    for (int32_t a = 0; a < ne; a++)
+        for (int64_t j = off[a]; j < off[a + 1]; j++) {
+            hid[j] = a;
+            for (int64_t t = j + 1; t < off[a + 1]; t++)
+                if (pins[t] == pins[j]) return 1;
+            deg[pins[j]]++;
+        }
+    std::vector<int64_t> voff(np + 1, 0);
+    for (int32_t q = 0; q < np; q++) voff[q + 1] = voff[q] + deg[q];
+    std::vector<int32_t> vinc((size_t)P), cur(np, 0);
+    for (int64_t j = P - 1; j >= 0; j--) vinc[voff[pins[j]] + cur[pins[j]]++] = hid[j];   // any order
+    std::vector<int32_t> seq((size_t)S * np), pos((size_t)S * np, -1);
+    for (int64_t t = 0; t < (int64_t)S * np; t++) {
+        int32_t q = seq0[t];
+        int64_t s = t / np;
+        if (q < 0 || q >= np || pos[s * np + q] >= 0) return 1;
+        seq[t] = q;
+        pos[s * np + q] = (int32_t)(t - s * np);
+    }
+    // the bisection tree
+    std::vector<int32_t> lo{0}, hi{np}, par{-1}, kid{-1}, depth{0};
+    for (size_t v = 0; v < lo.size(); v++) {
+        int32_t len = hi[v] - lo[v];
+        if (len <= 1) continue;
+        int32_t mid = lo[v] + (len + 1) / 2;
+        kid[v] = (int32_t)lo.size();
+        lo.push_back(lo[v]); hi.push_back(mid); par.push_back((int32_t)v); kid.push_back(-1);
+        depth.push_back(depth[v] + 1);
+        lo.push_back(mid); hi.push_back(hi[v]); par.push_back((int32_t)v); kid.push_back(-1);
+        depth.push_back(depth[v] + 1);
+    }
+    const int32_t nn = (int32_t)lo.size();
+    int32_t maxd = 0;
+    for (int32_t v = 0; v < nn; v++) maxd = std::max(maxd, depth[v]);
+    std::vector<int64_t> G((size_t)S * np, 0);
+    for (int32_t d = 0; d <= maxd; d++) {
+        std::vector<int32_t> js;
+        for (int32_t v = 0; v < nn; v++)
+            if (depth[v] == d && kid[v] >= 0) js.push_back(v);
+        const int32_t J = (int32_t)js.size();
+        if (!J) continue;
+        std::vector<int32_t> jlo(J), jmid(J), jhi(J), jcap(J), jobof(np, -1);
+        std::vector<int64_t> po(J + 1, 0);
+        for (int32_t k = 0; k < J; k++) {
+            int32_t v = js[k], len = hi[v] - lo[v], nl = (len + 1) / 2, nr = len - nl;
+            jlo[k] = lo[v]; jmid[k] = lo[v] + nl; jhi[k] = hi[v];
+            jcap[k] = 4 * std::min(nl, nr);
+            po[k + 1] = po[k] + (int64_t)nl * nr;
+            for (int32_t i = lo[v]; i < hi[v]; i++) jobof[i] = k;
+        }
+        const int64_t pairs = po[J];
+        std::vector<int32_t> done((size_t)S * J, 0), it((size_t)S * J, 0), bx((size_t)S * J),
+            by((size_t)S * J);
+        std::vector<int64_t> bd((size_t)S * J), M((size_t)S * pairs);
+        for (;;) {
+            for (size_t t = 0; t < done.size(); t++)
+                if (!done[t]) { bd[t] = 0; bx[t] = INT32_MAX; by[t] = INT32_MAX; }
+            // k_ip_gain
+            for (int32_t s = 0; s < S; s++)
+                for (int32_t i = 0; i < np; i++) {
+                    int32_t k = jobof[i];
+                    if (k < 0 || done[(size_t)s * J + k]) continue;
+                    int32_t x = seq[(size_t)s * np + i];
+                    G[(size_t)s * np + x] = ip::single_gain(
+                        vinc.data(), voff[x], voff[x + 1], off, pins, eta, &pos[(size_t)s * np],
+                        ip::side_of(i, jlo[k], jmid[k], jhi[k]), jlo[k], jmid[k], jhi[k]);
+                }
+            // k_ip_corr
+            std::fill(M.begin(), M.end(), 0);
+            for (int32_t s = 0; s < S; s++)
+                for (int32_t i = 0; i < np; i++) {
+                    int32_t k = jobof[i];
+                    if (k < 0 || done[(size_t)s * J + k] || i >= jmid[k]) continue;
+                    int32_t x = seq[(size_t)s * np + i], nr = jhi[k] - jmid[k];
+                    int64_t* row = &M[(size_t)s * pairs + po[k] + (int64_t)(i - jlo[k]) * nr];
+                    ip::corr_row(vinc.data(), voff[x], voff[x + 1], off, pins, eta,
+                                 &pos[(size_t)s * np], jlo[k], jmid[k], jhi[k],
+                                 [row](int32_t j, int64_t w) { row[j] += w; });
+                }
+            // k_ip_best, three passes
+            for (int pass = 0; pass < 3; pass++)
+                for (int32_t s = 0; s < S; s++)
+                    for (int32_t k = 0; k < J; k++) {
+                        size_t t = (size_t)s * J + k;
+                        if (done[t]) continue;
+                        int32_t nr = jhi[k] - jmid[k];
+                        for (int64_t q = 0; q < po[k + 1] - po[k]; q++) {
+                            int32_t x = seq[(size_t)s * np + jlo[k] + q / nr];
+                            int32_t y = seq[(size_t)s * np + jmid[k] + q % nr];
+                            int64_t dd = G[(size_t)s * np + x] + G[(size_t)s * np + y] -
+                                         M[(size_t)s * pairs + po[k] + q];
+                            if (dd <= 0) continue;
+                            if (pass == 0) bd[t] = std::max(bd[t], dd);
+                            else if (pass == 1 && dd == bd[t]) bx[t] = std::min(bx[t], x);
+                            else if (pass == 2 && dd == bd[t] && x == bx[t]) by[t] = std::min(by[t], y);
+                        }
+                    }
+            // k_ip_apply
+            int active = 0;
+            for (int32_t s = 0; s < S; s++)
+                for (int32_t k = 0; k < J; k++) {
+                    size_t t = (size_t)s * J + k;
+                    if (done[t]) continue;
+                    if (bd[t] <= 0) { done[t] = 1; continue; }
+                    int32_t* ps = &pos[(size_t)s * np];
+                    int32_t* qs = &seq[(size_t)s * np];
+                    int32_t x = bx[t], y = by[t], px = ps[x], py = ps[y];
+                    qs[px] = y; qs[py] = x; ps[x] = py; ps[y] = px;
+                    if (++it[t] >= jcap[k]) done[t] = 1;
+                    else active++;
+                }
+            if (!active) break;
+        }
+    }
+    // k_ip_conn, k_ip_flip, k_ip_fold
+    std::vector<int64_t> conn((size_t)S * nn, 0);
+    std::vector<uint8_t> flip((size_t)S * nn, 0);
+    for (int32_t s = 0; s < S; s++) {
+        const int32_t* ps = &pos[(size_t)s * np];
+        for (int64_t j = 0; j < P; j++) {
+            int32_t a = hid[j], i = ps[pins[j]], v = 0;
+            while (kid[v] >= 0) {
+                int32_t c = ip::child_holding(lo.data(), hi.data(), kid.data(), v, i);
+                int32_t p = par[v];
+                if (p >= 0) {
+                    int32_t sib = kid[p] == v ? kid[p] + 1 : kid[p];
+                    bool first, meets;
+                    ip::fold_checks(pins, off[a], off[a + 1], ps, j, lo[c], hi[c], lo[sib], hi[sib],
+                                    &first, &meets);
+                    if (first && meets) conn[(size_t)s * nn + c] += eta[a];
+                }
+                v = c;
+            }
+        }
+        for (int32_t v = 0; v < nn; v++) {
+            int32_t p = par[v];
+            if (kid[v] < 0 || p < 0) continue;
+            int64_t ca = conn[(size_t)s * nn + kid[v]], cb = conn[(size_t)s * nn + kid[v] + 1];
+            flip[(size_t)s * nn + v] = kid[p] == v ? (ca > cb) : (cb > ca);
+        }
+        for (int32_t i = 0; i < np; i++)
+            seq_out[(size_t)s * np +
+                    ip::folded_position(lo.data(), hi.data(), kid.data(), &flip[(size_t)s * nn], i)] =
+                seq[(size_t)s * np + i];
+    }
+    // k_ip_hkeys + sort, k_ip_gamma
+    uint32_t n2 = 1;
+    while (n2 < (uint32_t)width || n2 < (uint32_t)height) n2 <<= 1;
+    std::vector<std::pair<uint64_t, int32_t>> cells;
+    for (int32_t h = 0; h < width * height; h++)
+        cells.push_back({ip::hilbert_index(n2, (uint32_t)(h % width), (uint32_t)(h / width)), h});
+    std::stable_sort(cells.begin(), cells.end(),
+                     [](const std::pair<uint64_t, int32_t>& a, const std::pair<uint64_t, int32_t>& b) {
+                         return a.first < b.first;
+                     });
+    for (int32_t s = 0; s < S; s++)
+        for (int32_t i = 0; i < np; i++) gamma[(size_t)s * np + seq_out[(size_t)s * np + i]] = cells[i].second;
+    return 0;
 }
 
 }  // extern "C"

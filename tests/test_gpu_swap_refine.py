@@ -7,13 +7,21 @@ SNN refined from 64 random starts together (the paper's Pi), where sampled
 starts are checked one by one and every start by invariants (an injective
 placement, a total residual distance lowered by exactly the summed gains).
 The total residual distance (snnmap_place_trd) equals the oracle's; invalid
-input is rejected and leaves gamma unchanged."""
+input is rejected and leaves gamma unchanged.
+
+The initial placement the refinement starts from (snnmap_place_initial,
+snnmap_hilbert_order; readings RI1-RI4) is checked the same way: final
+sequences and placements equal the oracle's start by start (random
+hypergraphs, the G_P of cfg2s, larger random cases, several starts at once),
+the Hilbert order equals the oracle's, and 64 starts on the G_P of cfg1s
+(too large for the oracle's label propagation) are checked by invariants
+and then refined."""
 import numpy as np
 import pytest
 import torch
 
 import oracle
-from test_place_emul import gp_case
+from test_place_emul import gp_case, gp_of, larger_initial_case, random_initial_case
 from test_placement import csr, random_case
 
 pytestmark = pytest.mark.gpu
@@ -174,3 +182,99 @@ def test_runs_native_kernels():
     off, pins = csr([[0, 1, 2]])
     gpu_refine(3, off, pins, [4], 3, 3, [[0, 4, 8]])
     assert P.snnmap_launch_count() > before
+
+
+# --- initial placement ---
+
+def gpu_initial(n, off, pins, eta, width, height, seq0s):
+    import paper_2609_07577_gb300 as P
+    d_off, d_pins, d_eta = upload(off, pins, eta)
+    S = len(seq0s)
+    s0 = dev(np.concatenate([np.asarray(x, np.int32) for x in seq0s]), torch.int32)
+    seq = torch.zeros(S * n, dtype=torch.int32, device="cuda")
+    gamma = torch.zeros(S * n, dtype=torch.int32, device="cuda")
+    P.snnmap_place_initial(n, len(off) - 1, d_off, d_pins, d_eta, width, height, S, s0, gamma,
+                           d_seq_out=seq)
+    seq = seq.cpu().numpy().reshape(S, n)
+    gamma = gamma.cpu().numpy().reshape(S, n)
+    return [seq[s].tolist() for s in range(S)], [gamma[s].tolist() for s in range(S)]
+
+
+def test_initial_random_cases_match_oracle():
+    for seed in range(150):
+        n, hedges_, eta, width, height, seq0s = random_initial_case(seed)
+        off, pins = csr(hedges_)
+        seqs, gammas = gpu_initial(n, off, pins, eta, width, height, seq0s)
+        for s, s0 in enumerate(seq0s):
+            assert seqs[s] == oracle.initial_sequence(n, off, pins, eta, s0).tolist(), (seed, s)
+            assert gammas[s] == oracle.initial_placement(n, off, pins, eta, width, height,
+                                                         s0).tolist(), (seed, s)
+
+
+def test_initial_gp_and_larger_cases_match_oracle():
+    K, off, pins, eta, width, height = gp_of("cfg2s")
+    rng = np.random.Generator(np.random.PCG64(3))
+    seq0s = [rng.permutation(K).tolist() for _ in range(8)]
+    seqs, gammas = gpu_initial(K, off, pins, eta, width, height, seq0s)
+    for s, s0 in enumerate(seq0s):
+        assert seqs[s] == oracle.initial_sequence(K, off, pins, eta, s0).tolist(), s
+        assert gammas[s] == oracle.initial_placement(K, off, pins, eta, width, height,
+                                                     s0).tolist(), s
+    for seed in range(3):
+        n, hedges_, eta, width, height, seq0s = larger_initial_case(seed)
+        off, pins = csr(hedges_)
+        _, gammas = gpu_initial(n, off, pins, eta, width, height, seq0s)
+        for s, s0 in enumerate(seq0s):
+            assert gammas[s] == oracle.initial_placement(n, off, pins, eta, width, height,
+                                                         s0).tolist(), (seed, s)
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (1, 9), (9, 1), (3, 5), (22, 22), (37, 5), (64, 64)])
+def test_hilbert_order_matches_oracle(shape):
+    import paper_2609_07577_gb300 as P
+    w, h = shape
+    out = torch.zeros(w * h, dtype=torch.int32, device="cuda")
+    P.snnmap_hilbert_order(w, h, out)
+    assert out.cpu().numpy().tolist() == oracle.hilbert_order(w, h).tolist()
+
+
+def test_initial_then_refine_sixty_four_starts():
+    import paper_2609_07577_gb300 as P
+    K, off, pins, eta, width, height, _ = gp_case(2, 1)
+    rng = np.random.Generator(np.random.PCG64(64))
+    seq0s = [rng.permutation(K).tolist() for _ in range(64)]
+    seqs, gammas = gpu_initial(K, off, pins, eta, width, height, seq0s)
+    first = set(oracle.hilbert_order(width, height)[:K].tolist())
+    for s in range(64):
+        assert sorted(seqs[s]) == list(range(K))
+        assert set(gammas[s]) == first and len(set(gammas[s])) == K
+    trd0 = gpu_trd(K, off, pins, eta, width, height, gammas)
+    assert trd0 == [oracle.place_trd(K, off, pins, eta, width, g) for g in gammas]
+    got, rounds, logs = gpu_refine(K, off, pins, eta, width, height, gammas)
+    trd1 = gpu_trd(K, off, pins, eta, width, height, got)
+    for s in range(64):
+        assert trd0[s] - trd1[s] == sum(r["gain"] for r in logs[s])
+        assert len(set(got[s])) == K
+    # the initial placement already beats random ones on this G_P
+    rand = [rng.choice(width * height, size=K, replace=False) for _ in range(8)]
+    assert min(trd0) < min(gpu_trd(K, off, pins, eta, width, height, rand))
+
+
+def test_initial_invalid_input_rejected():
+    import paper_2609_07577_gb300 as P
+    off, pins = csr([[0, 1, 0]])
+    d_off, d_pins, d_eta = upload(off, pins, [1])
+    g = torch.full((2,), 7, dtype=torch.int32, device="cuda")
+    with pytest.raises(P.SnnmapError):
+        P.snnmap_place_initial(2, 1, d_off, d_pins, d_eta, 2, 1, 1, dev([0, 1], torch.int32), g)
+    off, pins = csr([[0, 1]])
+    d_off, d_pins, d_eta = upload(off, pins, [1])
+    for s0 in ([0, 0], [0, 2], [1, -1]):
+        with pytest.raises(P.SnnmapError):
+            P.snnmap_place_initial(2, 1, d_off, d_pins, d_eta, 2, 1, 1, dev(s0, torch.int32), g)
+    with pytest.raises(P.SnnmapError):
+        P.snnmap_place_initial(3, 1, d_off, d_pins, d_eta, 2, 1, 1,
+                               dev([0, 1, 2], torch.int32), g)   # 3 nodes, 2 cores
+    with pytest.raises(P.SnnmapError):
+        P.snnmap_hilbert_order(0, 3, g)
+    assert g.cpu().numpy().tolist() == [7, 7]

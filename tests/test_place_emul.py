@@ -146,3 +146,105 @@ def test_invalid_placement_rejected(emul):
     off, pins = csr([[0, 1]])
     assert run_emul(emul, 2, off, pins, [1], 2, 1, [[0, 0]])[0] == 1
     assert run_emul(emul, 2, off, pins, [1], 2, 1, [[0, 2]])[0] == 1
+
+
+# --- initial placement (Sec. 4.2, "Initial Placement"; readings RI1-RI4) ---
+
+def initial_emul(L, n, off, pins, eta, width, height, seq0s):
+    S = len(seq0s)
+    off = np.ascontiguousarray(off, np.int64)
+    pins = np.ascontiguousarray(pins, np.int32)
+    eta = np.ascontiguousarray(eta, np.int64)
+    s0 = np.ascontiguousarray(np.concatenate([np.asarray(x, np.int32) for x in seq0s]))
+    seq = np.zeros(S * n, np.int32)
+    gamma = np.zeros(S * n, np.int32)
+    rc = L.emul_place_initial(n, len(off) - 1, ptr(off), ptr(pins), ptr(eta), width, height, S,
+                              ptr(s0), ptr(seq), ptr(gamma))
+    if rc:
+        return rc, None, None
+    return 0, [seq[s * n:(s + 1) * n].tolist() for s in range(S)], \
+        [gamma[s * n:(s + 1) * n].tolist() for s in range(S)]
+
+
+def random_initial_case(seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n = int(rng.integers(1, 40))
+    hedges_ = [rng.choice(n, size=int(rng.integers(2, min(n, 6) + 1)), replace=False).tolist()
+               for _ in range(int(rng.integers(0, 3 * n)))] if n >= 2 else []
+    eta = rng.integers(1, 9, size=len(hedges_)).tolist()
+    width = int(rng.integers(1, 8))
+    height = -(-n // width) + int(rng.integers(0, 2))
+    seq0s = [rng.permutation(n).tolist() for _ in range(int(rng.integers(1, 4)))]
+    return n, hedges_, eta, width, height, seq0s
+
+
+@pytest.fixture(scope="module")
+def emul_initial(emul):
+    emul.emul_place_initial.restype = C.c_int
+    emul.emul_place_initial.argtypes = [C.c_int32, C.c_int32] + [C.c_void_p] * 3 + \
+        [C.c_int32] * 3 + [C.c_void_p] * 3
+    return emul
+
+
+def test_initial_matches_oracle(emul_initial):
+    for seed in range(300):
+        n, hedges_, eta, width, height, seq0s = random_initial_case(seed)
+        off, pins = csr(hedges_)
+        rc, seqs, gammas = initial_emul(emul_initial, n, off, pins, eta, width, height, seq0s)
+        assert rc == 0
+        for s, s0 in enumerate(seq0s):
+            assert seqs[s] == oracle.initial_sequence(n, off, pins, eta, s0).tolist(), (seed, s)
+            assert gammas[s] == oracle.initial_placement(n, off, pins, eta, width, height,
+                                                         s0).tolist(), (seed, s)
+
+
+def gp_of(name):
+    """G_P of a named SNN under the oracle's partition, on the smallest
+    near-square lattice that holds it."""
+    hg = snngen.by_name(name)
+    rho, _, st, *_ = oracle.partition(hg, oracle.params_of(hg))
+    K = int(st["n_parts"])
+    gp = oracle.Level.from_hypergraph(hg, oracle.params_of(hg)).partition_graph(rho)
+    width = int(np.ceil(np.sqrt(K)))
+    return K, gp["off"], gp["pins"], gp["eta"], width, int(np.ceil(K / width))
+
+
+def test_initial_on_gp_matches_oracle(emul_initial):
+    K, off, pins, eta, width, height = gp_of("cfg2s")
+    rng = np.random.Generator(np.random.PCG64(3))
+    seq0s = [rng.permutation(K).tolist() for _ in range(4)]
+    rc, seqs, gammas = initial_emul(emul_initial, K, off, pins, eta, width, height, seq0s)
+    assert rc == 0
+    for s, s0 in enumerate(seq0s):
+        assert seqs[s] == oracle.initial_sequence(K, off, pins, eta, s0).tolist(), s
+        assert gammas[s] == oracle.initial_placement(K, off, pins, eta, width, height,
+                                                     s0).tolist(), s
+
+
+def larger_initial_case(seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n = int(rng.integers(48, 97))
+    hedges_ = [rng.choice(n, size=int(rng.integers(2, 9)), replace=False).tolist()
+               for _ in range(3 * n)]
+    eta = rng.integers(1, 20, size=len(hedges_)).tolist()
+    width = int(np.ceil(np.sqrt(n)))
+    height = -(-n // width)
+    return n, hedges_, eta, width, height, [rng.permutation(n).tolist() for _ in range(2)]
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_initial_larger_cases_match_oracle(emul_initial, seed):
+    n, hedges_, eta, width, height, seq0s = larger_initial_case(seed)
+    off, pins = csr(hedges_)
+    rc, seqs, gammas = initial_emul(emul_initial, n, off, pins, eta, width, height, seq0s)
+    assert rc == 0
+    for s, s0 in enumerate(seq0s):
+        assert gammas[s] == oracle.initial_placement(n, off, pins, eta, width, height,
+                                                     s0).tolist(), s
+
+
+def test_initial_rejects_repeated_pins_and_bad_orders(emul_initial):
+    off, pins = csr([[0, 1, 0]])
+    assert initial_emul(emul_initial, 2, off, pins, [1], 2, 1, [[0, 1]])[0] == 1
+    off, pins = csr([[0, 1]])
+    assert initial_emul(emul_initial, 2, off, pins, [1], 2, 1, [[0, 0]])[0] == 1
