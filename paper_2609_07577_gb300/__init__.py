@@ -18,5 +18,5 @@ from ._native import (  # noqa: F401
     snnmap_serve_wait, snnmap_serve_hgraph, snnmap_serve_release, snnmap_serve_info,
     snnmap_serve_destroy, snnmap_batch_partition,
 )
-from .api import HGraph, params_for, partition  # noqa: F401
+from .api import HGraph, lattice_for, params_for, partition, place  # noqa: F401
 from .serve import JobBuffers, Server, batch_partition  # noqa: F401

@@ -157,3 +157,51 @@ def partition(hg, device="cuda", **kw):
         return rho.cpu().numpy(), cost, stats
     finally:
         g.close()
+
+
+def lattice_for(n_nodes):
+    """The smallest near-square lattice (width, height) with at least
+    n_nodes cores: width = ceil(sqrt(n)), height = ceil(n / width)."""
+    width = max(1, int(np.ceil(np.sqrt(max(n_nodes, 1)))))
+    return width, max(1, -(-int(n_nodes) // width))
+
+
+def place(n_nodes, off, pins, eta, width=None, height=None, n_starts=64, seed=0,
+          max_rounds=1000, stream=None):
+    """Placement of G_P on a width x height lattice (Sec. 4.2): n_starts
+    initial placements from random node orders (numpy PCG64 seeded by
+    `seed`, one permutation per start, drawn here and passed to the
+    library), all refined by swaps in the same launches, and the start with
+    the smallest total residual distance kept (the lowest start on ties).
+    off, pins, eta: G_P as numpy arrays or device tensors (e.g. from
+    HGraph.partition_graph). Returns dict(gamma: numpy int32[n_nodes],
+    trd, start, trds: per start after refinement, trds_initial, rounds,
+    logs)."""
+    K = int(n_nodes)
+    if width is None or height is None:
+        width, height = lattice_for(K)
+    S = int(n_starts)
+
+    def dev(a, dt):
+        if isinstance(a, torch.Tensor):
+            return a.to(device="cuda", dtype=dt).contiguous()
+        return torch.from_numpy(np.ascontiguousarray(a).astype(
+            np.int64 if dt == torch.int64 else np.int32)).cuda()
+
+    d_off, d_pins, d_eta = dev(off, torch.int64), dev(pins, torch.int32), dev(eta, torch.int64)
+    E = int(d_off.numel()) - 1
+    rng = np.random.Generator(np.random.PCG64(seed))
+    seq0 = np.concatenate([rng.permutation(K).astype(np.int32) for _ in range(S)]) if K else \
+        np.zeros(0, np.int32)
+    d_seq0 = torch.from_numpy(seq0).cuda()
+    gamma = torch.zeros(S * K, dtype=torch.int32, device="cuda")
+    N.snnmap_place_initial(K, E, d_off, d_pins, d_eta, width, height, S, d_seq0, gamma,
+                           stream=stream)
+    trds0 = N.snnmap_place_trd(K, E, d_off, d_pins, d_eta, width, height, S, gamma, stream)
+    rounds, logs = N.snnmap_place_refine(K, E, d_off, d_pins, d_eta, width, height, S, gamma,
+                                         max_rounds, stream, log_cap=max_rounds)
+    trds = N.snnmap_place_trd(K, E, d_off, d_pins, d_eta, width, height, S, gamma, stream)
+    best = min(range(S), key=lambda s: (trds[s], s))
+    g = gamma.view(S, K)[best].cpu().numpy() if K else np.zeros(0, np.int32)
+    return {"gamma": g, "trd": trds[best], "start": best, "trds": trds, "trds_initial": trds0,
+            "rounds": rounds, "logs": logs, "width": width, "height": height}

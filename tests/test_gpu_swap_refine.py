@@ -278,3 +278,26 @@ def test_initial_invalid_input_rejected():
     with pytest.raises(P.SnnmapError):
         P.snnmap_hilbert_order(0, 3, g)
     assert g.cpu().numpy().tolist() == [7, 7]
+
+
+def test_place_flow_matches_oracle_composition():
+    """paper_2609_07577_gb300.place: initial placements from seeded random
+    orders, refinement, the start of smallest total residual distance --
+    equal to the oracle's steps composed the same way."""
+    import paper_2609_07577_gb300 as P
+    K, off, pins, eta, width, height = gp_of("cfg2s")
+    res = P.place(K, off, pins, eta, n_starts=8, seed=5)
+    assert (res["width"], res["height"]) == (width, height)
+    rng = np.random.Generator(np.random.PCG64(5))
+    finals, trds, trds0 = [], [], []
+    for _ in range(8):
+        s0 = rng.permutation(K)
+        g0 = oracle.initial_placement(K, off, pins, eta, width, height, s0)
+        trds0.append(oracle.place_trd(K, off, pins, eta, width, g0))
+        g1, _ = oracle.place_refine(K, off, pins, eta, width, height, g0)
+        finals.append(g1)
+        trds.append(oracle.place_trd(K, off, pins, eta, width, g1))
+    best = min(range(8), key=lambda s: (trds[s], s))
+    assert res["trds_initial"] == trds0 and res["trds"] == trds
+    assert res["start"] == best and res["trd"] == trds[best]
+    assert res["gamma"].tolist() == finals[best].tolist()

@@ -248,3 +248,10 @@ def test_initial_rejects_repeated_pins_and_bad_orders(emul_initial):
     assert initial_emul(emul_initial, 2, off, pins, [1], 2, 1, [[0, 1]])[0] == 1
     off, pins = csr([[0, 1]])
     assert initial_emul(emul_initial, 2, off, pins, [1], 2, 1, [[0, 0]])[0] == 1
+
+
+def test_lattice_for():
+    from paper_2609_07577_gb300.api import lattice_for
+    for n in range(1, 300):
+        w, h = lattice_for(n)
+        assert w * h >= n and w * (h - 1) < n and abs(w - h) <= 1
