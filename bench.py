@@ -56,9 +56,15 @@ CONFIGS = {
              None),
     "cfg5": ("Served: Poisson arrivals (200 jobs/s) of jobs of 10k-2M neurons (log-uniform), "
              "conv-like or power-law, admitted by HBM footprint", None),
+    "place": ("Placement (Sec. 4.2) of the partition hypergraph G_P of cfg2's partition on the "
+              "smallest near-square lattice: 64 starts, initial placement + swap refinement, "
+              "best start by total residual distance", None),
 }
 BATCH_METRIC = "batched jobs/s (1 GB300)"
 SERVE_METRIC = "served jobs/s with p50/p99 latency (1 GB300)"
+PLACE_METRIC = "multi-start placements/s of G_P (64 starts, initial placement + swap refinement)"
+PLACE_UNIT = "placements/s"
+PLACE_STARTS = 64
 
 
 def parse():
@@ -207,9 +213,52 @@ def cpu_baseline(warm=0, steps=1):
             "s_per_pass": t, "pins": hg.P}
 
 
+def place_baseline(budget_s=10.0):
+    """The oracle on a bounded sample of the placement workload: whole
+    starts (initial placement + swap refinement) on the G_P of the
+    scaled-down conv workload's partition, as many as fit budget_s; value =
+    64-start placements/s at that rate."""
+    import oracle
+    hg = snngen.by_name("cfg2s")
+    oracle.build()
+    rho, _, st, *_ = oracle.partition(hg, oracle.params_of(hg))
+    K = int(st["n_parts"])
+    gp = oracle.Level.from_hypergraph(hg, oracle.params_of(hg)).partition_graph(rho)
+    width = int(math.ceil(math.sqrt(K)))
+    height = -(-K // width)
+    rng = np.random.Generator(np.random.PCG64(0))
+    n, t0 = 0, time.perf_counter()
+    while n < PLACE_STARTS and (n == 0 or time.perf_counter() - t0 < budget_s):
+        g0 = oracle.initial_placement(K, gp["off"], gp["pins"], gp["eta"], width, height,
+                                      rng.permutation(K))
+        oracle.place_refine(K, gp["off"], gp["pins"], gp["eta"], width, height, g0)
+        n += 1
+    per_start = (time.perf_counter() - t0) / n
+    return {"value": 1.0 / (per_start * PLACE_STARTS), "unit": PLACE_UNIT, "cores": 1,
+            "kind": "oracle",
+            "sample": (f"{n} whole starts on the G_P of the 8192-neuron conv workload's partition "
+                       f"(K={K}, {len(gp['pins'])} pins; cfg2's G_P is beyond the oracle's label "
+                       f"propagation); {per_start:.2f} s per start, scaled to 64 starts"),
+            "s_per_placement": per_start * PLACE_STARTS}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
+        return
+    if args.config == "place":
+        cb = place_baseline()
+        line = {"impl": "reference", "metric": PLACE_METRIC, "value": cb["value"],
+                "unit": PLACE_UNIT, "n_gpus": args.gpus, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": cb["s_per_placement"] * 1e3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "int64", "data": "synthetic",
+                "config": {"workload": "place", "description": CONFIGS["place"][0],
+                           "sample": cb["sample"]},
+                "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+                "e2e": {"value": cb["value"], "unit": PLACE_UNIT, "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
         return
     cfg_desc = CONFIGS[args.config][0]
     cb = cpu_baseline(warm=args.warmup, steps=args.steps)
@@ -580,10 +629,119 @@ def run_serve(args):
         dist.destroy_process_group()
 
 
+def run_place(args):
+    """Placement of cfg2's G_P: the partition runs once (untimed setup);
+    each step is one 64-start placement (paper_2609_07577_gb300.place) on
+    device-resident G_P arrays; e2e repeats it from host arrays."""
+    import torch
+    import torch.distributed as dist
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2609_07577_gb300 as P
+    from paper_2609_07577_gb300 import HGraph
+
+    hg = snngen.cfg2()
+    G = HGraph.from_hypergraph(hg, device=dev)
+    try:
+        rho, _, st = G.partition()
+        K = int(st["n_parts"])
+        gp = G.partition_graph(rho, K)
+    finally:
+        G.close()
+    E, Pgp = len(gp["eta"]), len(gp["pins"])
+    d = {k: torch.from_numpy(np.ascontiguousarray(gp[k])).to(dev) for k in ("off", "pins", "eta")}
+    width, height = P.lattice_for(K)
+
+    def step(i, arrays):
+        return P.place(K, arrays["off"], arrays["pins"], arrays["eta"], width, height,
+                       n_starts=PLACE_STARTS, seed=i)
+
+    for i in range(args.warmup):
+        res = step(i, d)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    sampler = None if args.no_clocks else ClockSampler(gpu_uuid(torch, local))
+    time.sleep(0.3)
+    barrier()
+    l0 = P.snnmap_launch_count()
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(args.steps):
+        res = step(args.warmup + i, d)
+    e1.record(stream)
+    barrier()
+    launches = P.snnmap_launch_count() - l0
+    clocks = sampler.stop() if sampler else {"sm_mhz": None, "sm_max_mhz": None,
+                                             "reasons": ["not sampled"]}
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    e2e_s = None
+    if args.e2e_steps > 0:
+        barrier()
+        t0 = time.perf_counter()
+        for i in range(args.e2e_steps):
+            step(i, gp)
+        barrier()
+        e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+        if world > 1:
+            t = torch.tensor([e2e_s], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+
+    cb = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = place_baseline()
+        cb = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    if rank == 0:
+        line = {
+            "metric": PLACE_METRIC, "value": world / (ms / 1e3), "unit": PLACE_UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic",
+            "config": {"workload": "place", "description": CONFIGS["place"][0], "K": K,
+                       "hyperedges": E, "pins": Pgp, "width": width, "height": height,
+                       "starts": PLACE_STARTS, "parallelism": f"replicas{world}",
+                       "l2": "G_P fits L2: placement kernels run from L1/L2",
+                       "trd_best": res["trd"],
+                       "trd_initial_best": min(res["trds_initial"])},
+            "roofline": None,
+            "roofline_note": "placement kernels not yet captured with ncu",
+            "cpu_baseline": cb,
+            "e2e": None if e2e_s is None else {
+                "value": world / e2e_s, "unit": PLACE_UNIT,
+                "h2d_bytes_per_step": 8 * (E + 1) + 4 * Pgp + 8 * E + 4 * PLACE_STARTS * K,
+                "d2h_bytes_per_step": 4 * K, "s_per_step": e2e_s},
+            "gpu_launches": launches,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.config == "place":
+        run_place(args)
     elif args.config == "cfg4":
         run_batch(args)
     elif args.config == "cfg5":
