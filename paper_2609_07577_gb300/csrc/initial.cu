@@ -33,26 +33,6 @@ namespace ip = snn::initial;
 
 constexpr int kMaxStarts = 65535;   // gridDim.y
 
-__global__ void k_ip_check(int32_t ne, int64_t P, int32_t np, const int64_t* __restrict__ off,
-                           const int32_t* __restrict__ pins, int32_t* err)
-{
-    int bad = 0;
-    int64_t n = (int64_t)ne > P ? (int64_t)ne : P;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        if (i < ne && off[i] > off[i + 1]) bad = 1;
-        if (i < P && (pins[i] < 0 || pins[i] >= np)) bad = 1;
-    }
-    if (bad) atomicOr(err, 1);
-}
-
-__global__ void k_ip_hid(int32_t ne, const int64_t* __restrict__ off, int32_t* hid)
-{
-    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < ne;
-         a += (int64_t)gridDim.x * blockDim.x)
-        for (int64_t j = off[a]; j < off[a + 1]; j++) hid[j] = (int32_t)a;
-}
-
 // a pin repeated within its hyperedge; degrees of the nodes
 __global__ void k_ip_distinct(int64_t P, const int64_t* __restrict__ off,
                               const int32_t* __restrict__ pins, const int32_t* __restrict__ hid,
@@ -318,17 +298,6 @@ dim3 grid2(int64_t n, int32_t S)
     return dim3((unsigned)grid_for(n, 256, cap > 0 ? cap : 1), (unsigned)S);
 }
 
-bool device_ptr(const void* p)
-{
-    if (!p) return false;
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
 Status invalid(const char* msg) { return Status{SNNMAP_ERR_INVALID, msg}; }
 
 // cores in Hilbert order into order (device uint32[nh])
@@ -395,8 +364,8 @@ Status initial_impl(int32_t np, int32_t ne, const int64_t* off, const int32_t* p
     if (nh >= ((int64_t)1 << 31) || (int64_t)np * S >= ((int64_t)1 << 31))
         return invalid("width * height or n_starts * n_nodes >= 2^31");
     if (np > nh) return invalid("more nodes than cores");
-    if (!device_ptr(off) || (np > 0 && (!device_ptr(seq0) || !device_ptr(gamma))) ||
-        (seq_out_user && !device_ptr(seq_out_user)))
+    if ((np > 0 && (!device_pointer(seq0) || !device_pointer(gamma))) ||
+        (seq_out_user && !device_pointer(seq_out_user)))
         return invalid("buffers must be device memory");
     Arena ar;
     ar.stream = s;
@@ -404,19 +373,14 @@ Status initial_impl(int32_t np, int32_t ne, const int64_t* off, const int32_t* p
         Arena& a;
         ~Guard() { a.release(); }
     } guard{ar};
-    int64_t ends[2] = {0, 0};
-    SNN_CUDA(cudaMemcpyAsync(&ends[0], off, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    SNN_CUDA(cudaMemcpyAsync(&ends[1], off + ne, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    SNN_CUDA(cudaStreamSynchronize(s));
-    if (ends[0] != 0 || ends[1] < 0) return invalid("offsets must start at 0 and not decrease");
-    const int64_t P = ends[1];
-    if (P > 0 && (!device_ptr(pins) || !device_ptr(eta))) return invalid("buffers must be device memory");
+    int32_t *err, *hid;
+    int64_t P = 0;
+    SNN_TRY(ar.alloc(&err, 1));
+    SNN_TRY(gp_input(np, ne, off, pins, eta, ar, s, err, &P, &hid));
     if (np == 0) return Status{};
 
-    int32_t *err, *hid, *deg, *cursor, *vinc, *seq, *pos, *seq2;
+    int32_t *deg, *cursor, *vinc, *seq, *pos, *seq2;
     int64_t* voff;
-    SNN_TRY(ar.alloc(&err, 1));
-    SNN_TRY(ar.alloc(&hid, P));
     SNN_TRY(ar.alloc(&deg, np));
     SNN_TRY(ar.alloc(&cursor, np));
     SNN_TRY(ar.alloc(&vinc, P));
@@ -425,23 +389,15 @@ Status initial_impl(int32_t np, int32_t ne, const int64_t* off, const int32_t* p
     SNN_TRY(ar.alloc(&seq2, (int64_t)S * np));
     SNN_TRY(ar.alloc(&pos, (int64_t)S * np));
     SNN_CUDA(cudaMemsetAsync(err, 0, sizeof(int32_t), s));
-    if (ne > 0 || P > 0) {
-        SNN_L k_ip_check<<<grid_for(ne > P ? ne : P, 256), 256, 0, s>>>(ne, P, np, off, pins, err);
-        SNN_CUDA(cudaGetLastError());
-    }
     SNN_TRY(fill_i32(pos, -1, (int64_t)S * np, s));
     SNN_L k_ip_seq<<<grid2(np, S), 256, 0, s>>>(np, seq0, seq, pos, err);
     SNN_CUDA(cudaGetLastError());
     int32_t herr = 0;
     SNN_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     SNN_CUDA(cudaStreamSynchronize(s));
-    if (herr) return invalid("malformed offsets, a pin out of range, or an initial order that is not a permutation");
+    if (herr) return invalid("an initial order that is not a permutation of the nodes");
     SNN_CUDA(cudaMemsetAsync(deg, 0, sizeof(int32_t) * np, s));
     SNN_CUDA(cudaMemsetAsync(cursor, 0, sizeof(int32_t) * np, s));
-    if (ne > 0) {
-        SNN_L k_ip_hid<<<grid_for(ne, 256), 256, 0, s>>>(ne, off, hid);
-        SNN_CUDA(cudaGetLastError());
-    }
     if (P > 0) {
         SNN_L k_ip_distinct<<<grid_for(P, 256), 256, 0, s>>>(P, off, pins, hid, deg, err);
         SNN_CUDA(cudaGetLastError());
@@ -606,7 +562,7 @@ int snnmap_hilbert_order(int32_t width, int32_t height, int32_t* d_order_out, vo
     try {
         if (width < 1 || height < 1 || (int64_t)width * height >= ((int64_t)1 << 31))
             return finish(invalid("width and height must be >= 1 and width * height < 2^31"));
-        if (!device_ptr(d_order_out)) return finish(invalid("d_order_out must be device memory"));
+        if (!device_pointer(d_order_out)) return finish(invalid("d_order_out must be device memory"));
         cudaStream_t s = (cudaStream_t)stream;
         Arena ar;
         ar.stream = s;

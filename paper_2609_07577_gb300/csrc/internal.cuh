@@ -172,6 +172,14 @@ Status coarsen_level(snnmap_hgraph* h, int32_t* n_cand, int32_t* n_pairs);
 // (-1: unmatched); d_scal: device int64[SC_COUNT] scratch; *n_pairs: pairs.
 Status match_forest(int32_t V, const int32_t* cand, const int64_t* cscore, int32_t* match,
                     int64_t* d_scal, Arena& ar, cudaStream_t s, int64_t* n_pairs);
+// a device (or managed) pointer; host pointers would fault inside kernels
+bool device_pointer(const void* p);
+// Input G_P of the placement calls (place.cu): device pointers, offsets from
+// 0 and non-decreasing, pins in [0, np); *P_out = offsets[ne]; *hid_out
+// (arena) = the hyperedge of every pin entry. err: device int32 scratch.
+Status gp_input(int32_t np, int32_t ne, const int64_t* off, const int32_t* pins,
+                const int64_t* eta, Arena& ar, cudaStream_t s, int32_t* err, int64_t* P_out,
+                int32_t** hid_out);
 // S3: next level from h->match
 Status contract_level(snnmap_hgraph* h);
 // materializes levels[dst] from resident levels[src] through map (V(src) ids)

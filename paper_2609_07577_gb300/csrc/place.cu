@@ -32,15 +32,8 @@
 
 namespace {
 
-using namespace snn;
-using place::NO_RANK;
-
-// stats slots, each int64[S]
-enum { PS_PROPS = 0, PS_SWAPS = 1, PS_BEST = 2, PS_FIRST = 3, PS_N = 4 };
-constexpr int kMaxStarts = 65535;   // gridDim.y
-
 // offsets non-decreasing, pins in [0, np)
-__global__ void k_pl_check(int32_t ne, int64_t P, int32_t np, const int64_t* __restrict__ off,
+__global__ void k_gp_check(int32_t ne, int64_t P, int32_t np, const int64_t* __restrict__ off,
                            const int32_t* __restrict__ pins, int32_t* err)
 {
     int bad = 0;
@@ -54,12 +47,72 @@ __global__ void k_pl_check(int32_t ne, int64_t P, int32_t np, const int64_t* __r
 }
 
 // hyperedge of every pin entry (offsets already checked)
-__global__ void k_pl_hid(int32_t ne, const int64_t* __restrict__ off, int32_t* hid)
+__global__ void k_gp_hid(int32_t ne, const int64_t* __restrict__ off, int32_t* hid)
 {
     for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < ne;
          a += (int64_t)gridDim.x * blockDim.x)
         for (int64_t j = off[a]; j < off[a + 1]; j++) hid[j] = (int32_t)a;
 }
+
+}  // namespace
+
+namespace snn {
+
+bool device_pointer(const void* p)
+{
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+Status gp_input(int32_t np, int32_t ne, const int64_t* off, const int32_t* pins,
+                const int64_t* eta, Arena& ar, cudaStream_t s, int32_t* err, int64_t* P_out,
+                int32_t** hid_out)
+{
+    if (!device_pointer(off)) return Status{SNNMAP_ERR_INVALID, "buffers must be device memory"};
+    int64_t ends[2] = {0, 0};
+    SNN_CUDA(cudaMemcpyAsync(&ends[0], off, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    SNN_CUDA(cudaMemcpyAsync(&ends[1], off + ne, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    SNN_CUDA(cudaStreamSynchronize(s));
+    if (ends[0] != 0 || ends[1] < 0)
+        return Status{SNNMAP_ERR_INVALID, "offsets must start at 0 and not decrease"};
+    const int64_t P = ends[1];
+    if (P > 0 && (!device_pointer(pins) || !device_pointer(eta)))
+        return Status{SNNMAP_ERR_INVALID, "buffers must be device memory"};
+    int32_t* hid;
+    SNN_TRY(ar.alloc(&hid, P));
+    SNN_CUDA(cudaMemsetAsync(err, 0, sizeof(int32_t), s));
+    if (ne > 0 || P > 0) {
+        SNN_L k_gp_check<<<grid_for(ne > P ? ne : P, 256), 256, 0, s>>>(ne, P, np, off, pins, err);
+        SNN_CUDA(cudaGetLastError());
+    }
+    int32_t herr = 0;
+    SNN_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    SNN_CUDA(cudaStreamSynchronize(s));
+    if (herr) return Status{SNNMAP_ERR_INVALID, "malformed offsets or a pin out of range"};
+    if (ne > 0) {
+        SNN_L k_gp_hid<<<grid_for(ne, 256), 256, 0, s>>>(ne, off, hid);
+        SNN_CUDA(cudaGetLastError());
+    }
+    *P_out = P;
+    *hid_out = hid;
+    return Status{};
+}
+
+}  // namespace snn
+
+namespace {
+
+using namespace snn;
+using place::NO_RANK;
+
+// stats slots, each int64[S]
+enum { PS_PROPS = 0, PS_SWAPS = 1, PS_BEST = 2, PS_FIRST = 3, PS_N = 4 };
+constexpr int kMaxStarts = 65535;   // gridDim.y
 
 // pi from gamma (pi filled with -1): a core out of range or taken twice
 // within a start is an error
@@ -302,21 +355,10 @@ struct Input {
     const int64_t* eta;
 };
 
-bool device_ptr(const void* p)
-{
-    if (!p) return false;
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
 Status invalid(const char* msg) { return Status{SNNMAP_ERR_INVALID, msg}; }
 
-// Argument checks, then the hyperedge of every pin entry (hid) and the
-// inverse placement pi of every start (both from the arena).
+// Argument checks, G_P (gp_input: its pin count and the hyperedge of every
+// pin entry) and the inverse placement pi of every start (from the arena).
 Status prepare(Input& in, const int32_t* g, Arena& ar, cudaStream_t s, int32_t** hid_out,
                int32_t** pi_out, int32_t* err)
 {
@@ -325,25 +367,11 @@ Status prepare(Input& in, const int32_t* g, Arena& ar, cudaStream_t s, int32_t**
     in.nh = (int64_t)in.width * in.height;
     if (in.nh * in.S >= ((int64_t)1 << 31)) return invalid("n_starts * width * height >= 2^31");
     if (in.np > in.nh) return invalid("more nodes than cores");
-    if (!device_ptr(in.off) || (in.np > 0 && !device_ptr(g)))
-        return invalid("buffers must be device memory");
-    int64_t ends[2] = {0, 0};
-    SNN_CUDA(cudaMemcpyAsync(&ends[0], in.off, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    SNN_CUDA(cudaMemcpyAsync(&ends[1], in.off + in.ne, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    SNN_CUDA(cudaStreamSynchronize(s));
-    if (ends[0] != 0 || ends[1] < 0) return invalid("offsets must start at 0 and not decrease");
-    in.P = ends[1];
-    if (in.P > 0 && (!device_ptr(in.pins) || !device_ptr(in.eta)))
-        return invalid("buffers must be device memory");
-    int32_t *hid, *pi;
-    SNN_TRY(ar.alloc(&hid, in.P));
+    if (in.np > 0 && !device_pointer(g)) return invalid("buffers must be device memory");
+    SNN_TRY(gp_input(in.np, in.ne, in.off, in.pins, in.eta, ar, s, err, &in.P, hid_out));
+    int32_t* pi;
     SNN_TRY(ar.alloc(&pi, in.nh * in.S));
     SNN_CUDA(cudaMemsetAsync(err, 0, sizeof(int32_t), s));
-    if (in.ne > 0 || in.P > 0) {
-        SNN_L k_pl_check<<<grid_for(in.ne > in.P ? in.ne : in.P, 256), 256, 0, s>>>(
-            in.ne, in.P, in.np, in.off, in.pins, err);
-        SNN_CUDA(cudaGetLastError());
-    }
     SNN_TRY(fill_i32(pi, -1, in.nh * in.S, s));
     if (in.np > 0) {
         SNN_L k_pl_occupy<<<grid2(in.np, in.S), 256, 0, s>>>(in.np, (int32_t)in.nh, g, pi, err);
@@ -352,12 +380,7 @@ Status prepare(Input& in, const int32_t* g, Arena& ar, cudaStream_t s, int32_t**
     int32_t herr = 0;
     SNN_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     SNN_CUDA(cudaStreamSynchronize(s));
-    if (herr) return invalid("malformed offsets, a pin out of range, or a core out of range or taken twice");
-    if (in.ne > 0) {
-        SNN_L k_pl_hid<<<grid_for(in.ne, 256), 256, 0, s>>>(in.ne, in.off, hid);
-        SNN_CUDA(cudaGetLastError());
-    }
-    *hid_out = hid;
+    if (herr) return invalid("a core out of range or taken twice");
     *pi_out = pi;
     return Status{};
 }
