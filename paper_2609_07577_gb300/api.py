@@ -106,6 +106,14 @@ class HGraph:
         N.snnmap_level_cid(self._h, level, t, self.stream)
         return t.cpu().numpy()[:V]
 
+    def dump_hierarchy(self, path):
+        """Writes every level's arrays (level_arrays) and the cid maps between
+        them to one .npz (save_hierarchy), for triage of a mismatch against
+        the oracle offline."""
+        n = self.num_levels()
+        save_hierarchy(path, [self.level_arrays(l) for l in range(n)],
+                       [self.level_cid(l) for l in range(n - 1)])
+
     def refine(self, level, n_parts, rho):
         return N.snnmap_refine(self._h, level, n_parts, rho, self.stream)
 
@@ -146,6 +154,35 @@ class HGraph:
 
     def device_bytes(self):
         return N.snnmap_device_bytes(self._h)
+
+
+def save_hierarchy(path, levels, cids):
+    """One .npz holding level dicts (as from HGraph.level_arrays) under keys
+    L<l>_<name> and the cid map of level l (onto level l+1) as L<l>_cid."""
+    arrays = {"n_levels": np.int64(len(levels))}
+    for l, lv in enumerate(levels):
+        for k, v in lv.items():
+            arrays[f"L{l}_{k}"] = np.asarray(v)
+    for l, c in enumerate(cids):
+        arrays[f"L{l}_cid"] = np.asarray(c)
+    np.savez_compressed(path, **arrays)
+
+
+def load_hierarchy(path):
+    """Inverse of save_hierarchy: (levels as dicts, cid maps)."""
+    with np.load(path) as z:
+        n = int(z["n_levels"])
+        levels, cids = [], []
+        for l in range(n):
+            pre = f"L{l}_"
+            d = {k[len(pre):]: z[k] for k in z.files if k.startswith(pre) and k != pre + "cid"}
+            for k in ("V", "E", "P"):
+                if k in d:
+                    d[k] = int(d[k])
+            levels.append(d)
+            if pre + "cid" in z.files:
+                cids.append(z[pre + "cid"])
+    return levels, cids
 
 
 def partition(hg, device="cuda", **kw):

@@ -2,6 +2,8 @@
 // helpers every stage shares: size buckets, incidence lists, level memory.
 #include "internal.cuh"
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace snn {
 
 // ---------------------------------------------------------------------------
@@ -36,8 +38,13 @@ static cudaEvent_t prof_event(snnmap_hgraph* h)
     return e;
 }
 
+// Every stage scope is also an NVTX range named after the stage (a start/end
+// pair, so scopes that replace one another need not nest), which timeline
+// and kernel profilers show around the stage's launches; with no tool
+// attached the calls return at once.
 ProfScope::ProfScope(snnmap_hgraph* h_, int stage_) : h(h_), stage(stage_)
 {
+    range = nvtxRangeStartA(kStageNames[stage]);
     if (!h->prof_on) return;
     a = prof_event(h);
     b = prof_event(h);
@@ -46,6 +53,7 @@ ProfScope::ProfScope(snnmap_hgraph* h_, int stage_) : h(h_), stage(stage_)
 
 ProfScope::~ProfScope()
 {
+    nvtxRangeEnd(range);
     if (!h->prof_on || !a || !b) return;
     cudaEventRecord(b, h->stream);
     h->prof_pend.push_back({stage, a, b});

@@ -135,6 +135,7 @@ struct ProfScope {
     snnmap_hgraph* h;
     int stage;
     cudaEvent_t a = nullptr, b = nullptr;
+    uint64_t range = 0;   // NVTX range id
     ProfScope(snnmap_hgraph* h_, int stage_);
     ~ProfScope();
 };
