@@ -56,9 +56,10 @@ CONFIGS = {
              None),
     "cfg5": ("Served: Poisson arrivals (200 jobs/s) of jobs of 10k-2M neurons (log-uniform), "
              "conv-like or power-law, admitted by HBM footprint", None),
-    "place": ("Placement (Sec. 4.2) of the partition hypergraph G_P of cfg2's partition on the "
-              "smallest near-square lattice: 64 starts, initial placement + swap refinement, "
-              "best start by total residual distance", None),
+    "place": ("Placement (Sec. 4.2) of the partition hypergraph G_P of the quarter-width conv "
+              "workload's partition (8 layers of 64x64x8) on the smallest near-square lattice: "
+              "64 starts, initial placement + swap refinement, best start by total residual "
+              "distance", None),
 }
 BATCH_METRIC = "batched jobs/s (1 GB300)"
 SERVE_METRIC = "served jobs/s with p50/p99 latency (1 GB300)"
@@ -237,8 +238,9 @@ def place_baseline(budget_s=10.0):
     return {"value": 1.0 / (per_start * PLACE_STARTS), "unit": PLACE_UNIT, "cores": 1,
             "kind": "oracle",
             "sample": (f"{n} whole starts on the G_P of the 8192-neuron conv workload's partition "
-                       f"(K={K}, {len(gp['pins'])} pins; cfg2's G_P is beyond the oracle's label "
-                       f"propagation); {per_start:.2f} s per start, scaled to 64 starts"),
+                       f"(K={K}, {len(gp['pins'])} pins; the timed workload's G_P is beyond the "
+                       f"oracle's label propagation); {per_start:.2f} s per start, scaled to 64 "
+                       f"starts"),
             "s_per_placement": per_start * PLACE_STARTS}
 
 
@@ -630,7 +632,9 @@ def run_serve(args):
 
 
 def run_place(args):
-    """Placement of cfg2's G_P: the partition runs once (untimed setup);
+    """Placement of a G_P in the size range of the paper's (16 to 1.7k
+    nodes; cfg2's own has about 4.5k): the quarter-width conv workload is
+    partitioned once (untimed setup);
     each step is one 64-start placement (paper_2609_07577_gb300.place) on
     device-resident G_P arrays; e2e repeats it from host arrays."""
     import torch
@@ -648,7 +652,7 @@ def run_place(args):
     import paper_2609_07577_gb300 as P
     from paper_2609_07577_gb300 import HGraph
 
-    hg = snngen.cfg2()
+    hg = snngen.by_name("cfg2q")
     G = HGraph.from_hypergraph(hg, device=dev)
     try:
         rho, _, st = G.partition()
