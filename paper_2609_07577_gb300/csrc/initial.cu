@@ -6,14 +6,18 @@
 // once (breadth-first, the host's bookkeeping of interval bounds) and
 // shared by every start. Sections of one depth are disjoint, so the label
 // propagation of every sibling pair of a depth, in every start, runs as one
-// set of jobs; each job stops on its own. One round of all active jobs:
+// set of jobs; each job stops on its own. At the start of a depth:
 //   k_ip_gain     one thread per position: the single-move cut drop G of
 //                 the node there (counts of its hyperedges on each side)
 //   k_ip_corr     one thread per L position: its row of the job's nL x nR
 //                 correction matrix (the thread is the row's only writer)
+// Then one round of all active jobs:
 //   k_ip_best_*   one thread per (x, y) pair: the steepest swap, ties to
 //                 the lowest x then y, in three passes of integer atomics
-//   k_ip_apply    one thread per job: swap, or stop
+//   k_ip_update   one block per job: stop, or swap and bring G and the
+//                 matrix up to date through the hyperedges of x and y only
+//                 (G deltas, weight changes of pairs of non-moving pins,
+//                 and the rebuilt row and column of the two moved nodes)
 // Folding reads only the node sets of the sections, fixed once the label
 // propagation is done: k_ip_conn sums each child's connection to its
 // parent's sibling, k_ip_flip decides each orientation, and k_ip_fold gives
@@ -185,34 +189,111 @@ __global__ void k_ip_best(int32_t np, int64_t pairs, Jobs jb, const int32_t* __r
     }
 }
 
-__global__ void k_ip_apply(int32_t S, int32_t np, Jobs jb, int32_t* done, int32_t* it,
-                           const int64_t* __restrict__ bd, const int32_t* __restrict__ bx,
-                           const int32_t* __restrict__ by, int32_t* seq, int32_t* pos,
-                           int32_t* active)
+struct GAddAtomic {
+    int64_t* G;
+    __device__ void operator()(int32_t v, int64_t d) const
+    {
+        atomicAdd((unsigned long long*)&G[v], (unsigned long long)d);
+    }
+};
+
+struct MAddAtomic {
+    int64_t* M;
+    int32_t nr;
+    __device__ void operator()(int32_t i, int32_t j, int64_t d) const
+    {
+        atomicAdd((unsigned long long*)&M[(int64_t)i * nr + j], (unsigned long long)d);
+    }
+};
+
+struct RowAddAtomic {
+    int64_t* row;
+    __device__ void operator()(int32_t j, int64_t w) const
+    {
+        atomicAdd((unsigned long long*)&row[j], (unsigned long long)w);
+    }
+};
+
+struct ColAddAtomic {
+    int64_t* col;
+    int32_t nr;
+    __device__ void operator()(int32_t i, int64_t w) const
+    {
+        atomicAdd((unsigned long long*)&col[(int64_t)i * nr], (unsigned long long)w);
+    }
+};
+
+// One block per (job, start): stop when no swap lowers the cut, else swap
+// x and y and update G and the job's matrix incrementally.
+__global__ void k_ip_update(int32_t np, int64_t pairs, Jobs jb, int32_t* done, int32_t* it,
+                            const int64_t* __restrict__ bd, const int32_t* __restrict__ bx,
+                            const int32_t* __restrict__ by, const int64_t* __restrict__ voff,
+                            const int32_t* __restrict__ vinc, const int64_t* __restrict__ off,
+                            const int32_t* __restrict__ pins, const int64_t* __restrict__ eta,
+                            int32_t* seq, int32_t* pos, int64_t* G, int64_t* M, int32_t* active)
 {
-    int c = 0;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)S * jb.J;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        if (done[t]) continue;
-        int64_t s = t / jb.J;
-        int32_t k = (int32_t)(t - s * jb.J);
-        if (bd[t] <= 0) {
-            done[t] = 1;
-            continue;
+    __shared__ int s_mode;   // 0 skip, 1 swap then stop, 2 swap and go on
+    const int64_t s = blockIdx.y;
+    const int32_t k = blockIdx.x;
+    const int64_t t = s * jb.J + k;
+    if (threadIdx.x == 0) {
+        int mode = 0;
+        if (!done[t]) {
+            if (bd[t] <= 0) done[t] = 1;
+            else mode = it[t] + 1 >= jb.cap[k] ? 1 : 2;
         }
-        int32_t x = bx[t], y = by[t];
-        int32_t* ps = pos + s * np;
+        s_mode = mode;
+    }
+    __syncthreads();
+    const int mode = s_mode;
+    if (mode == 0) return;
+    const int32_t lo = jb.lo[k], mid = jb.mid[k], hi = jb.hi[k], nr = hi - mid;
+    const int32_t x = bx[t], y = by[t];
+    int32_t* ps = pos + s * np;
+    int64_t* Gs = G + s * np;
+    int64_t* Mk = M + s * pairs + jb.pairoff[k];
+    const int32_t px = ps[x], py = ps[y];
+    if (mode == 2) {
+        // hyperedges of x, then those of y not holding x, before the swap
+        const int64_t nx = voff[x + 1] - voff[x], ny = voff[y + 1] - voff[y];
+        GAddAtomic gadd{Gs};
+        MAddAtomic madd{Mk, nr};
+        for (int64_t u = threadIdx.x; u < nx + ny; u += blockDim.x) {
+            bool from_y = u >= nx;
+            int32_t a = from_y ? vinc[voff[y] + (u - nx)] : vinc[voff[x] + u];
+            ip::swap_hedge_update(pins, off[a], off[a + 1], ps, lo, mid, hi, x, y, eta[a], from_y,
+                                  gadd, madd);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
         int32_t* qs = seq + s * np;
-        int32_t px = ps[x], py = ps[y];
         qs[px] = y;
         qs[py] = x;
         ps[x] = py;
         ps[y] = px;
-        if (++it[t] >= jb.cap[k]) done[t] = 1;
-        else c++;
+        it[t] += 1;
+        if (mode == 1) done[t] = 1;
+        else atomicAdd(active, 1);
     }
-    c = warp_sum(c);
-    if ((threadIdx.x & 31) == 0 && c) atomicAdd(active, c);
+    if (mode == 1) return;
+    __syncthreads();
+    // the moved nodes' row (y now at px in L) and column (x now at py in R)
+    int64_t* row = Mk + (int64_t)(px - lo) * nr;
+    int64_t* col = Mk + (py - mid);
+    for (int32_t j = threadIdx.x; j < nr; j += blockDim.x) row[j] = 0;
+    for (int32_t i = threadIdx.x; i < mid - lo; i += blockDim.x) col[(int64_t)i * nr] = 0;
+    __syncthreads();
+    const int64_t nyi = voff[y + 1] - voff[y], nxi = voff[x + 1] - voff[x];
+    for (int64_t u = threadIdx.x; u < nyi + nxi; u += blockDim.x) {
+        if (u < nyi) {
+            ip::corr_row(vinc, voff[y] + u, voff[y] + u + 1, off, pins, eta, ps, lo, mid, hi,
+                         RowAddAtomic{row});
+        } else {
+            int64_t v = voff[x] + (u - nyi);
+            ip::corr_col(vinc, v, v + 1, off, pins, eta, ps, lo, mid, hi, y, ColAddAtomic{col, nr});
+        }
+    }
 }
 
 struct Tree {
@@ -490,17 +571,20 @@ Status initial_impl(int32_t np, int32_t ne, const int64_t* off, const int32_t* p
         SNN_CUDA(cudaGetLastError());
         const dim3 gpair = grid2(pairs, S);
         const int gjob = grid_for((int64_t)S * J, 256);
+        SNN_L k_ip_gain<<<gpos, 256, 0, s>>>(np, jb, done, voff, vinc, off, pins, eta, seq, pos, G);
+        SNN_CUDA(cudaMemsetAsync(M, 0, sizeof(int64_t) * S * pairs, s));
+        SNN_L k_ip_corr<<<gpos, 256, 0, s>>>(np, pairs, jb, done, voff, vinc, off, pins, eta, seq,
+                                             pos, M);
+        SNN_CUDA(cudaGetLastError());
+        const dim3 gupd((unsigned)J, (unsigned)S);
         for (;;) {
             SNN_L k_ip_reset<<<gjob, 256, 0, s>>>(S, J, done, bd, bx, by);
-            SNN_L k_ip_gain<<<gpos, 256, 0, s>>>(np, jb, done, voff, vinc, off, pins, eta, seq, pos, G);
-            SNN_CUDA(cudaMemsetAsync(M, 0, sizeof(int64_t) * S * pairs, s));
-            SNN_L k_ip_corr<<<gpos, 256, 0, s>>>(np, pairs, jb, done, voff, vinc, off, pins, eta, seq,
-                                                 pos, M);
             SNN_L k_ip_best<0><<<gpair, 256, 0, s>>>(np, pairs, jb, done, seq, G, M, bd, bx, by);
             SNN_L k_ip_best<1><<<gpair, 256, 0, s>>>(np, pairs, jb, done, seq, G, M, bd, bx, by);
             SNN_L k_ip_best<2><<<gpair, 256, 0, s>>>(np, pairs, jb, done, seq, G, M, bd, bx, by);
             SNN_CUDA(cudaMemsetAsync(active, 0, sizeof(int32_t), s));
-            SNN_L k_ip_apply<<<gjob, 256, 0, s>>>(S, np, jb, done, it, bd, bx, by, seq, pos, active);
+            SNN_L k_ip_update<<<gupd, 128, 0, s>>>(np, pairs, jb, done, it, bd, bx, by, voff, vinc, off,
+                                                   pins, eta, seq, pos, G, M, active);
             SNN_CUDA(cudaGetLastError());
             int32_t hact = 0;
             SNN_CUDA(cudaMemcpyAsync(&hact, active, sizeof(int32_t), cudaMemcpyDeviceToHost, s));

@@ -119,6 +119,81 @@ IP_HD void corr_row(const int32_t* inc, int64_t ib, int64_t ie, const int64_t* o
     }
 }
 
+// corr(., x) of node x in R over its incidences, the mirror of corr_row:
+// add(i, w) receives contributions for the node at position lo + i of L,
+// except the node skip (whose row is rebuilt by corr_row).
+template <typename Add>
+IP_HD void corr_col(const int32_t* inc, int64_t ib, int64_t ie, const int64_t* off,
+                    const int32_t* pins, const int64_t* eta, const int32_t* pos, int32_t lo,
+                    int32_t mid, int32_t hi, int32_t skip, Add add)
+{
+    for (int64_t t = ib; t < ie; t++) {
+        int32_t a = inc[t], cL, cR;
+        side_counts(pins, off[a], off[a + 1], pos, lo, mid, hi, &cL, &cR);
+        if (cL == 0 || (cL != 1 && cR != 1)) continue;
+        int64_t w = cR == 1 ? eta[a] * (1 + (cL == 1)) : eta[a];
+        for (int64_t j = off[a]; j < off[a + 1]; j++) {
+            int32_t u = pins[j];
+            int32_t i = pos[u];
+            if (u != skip && side_of(i, lo, mid, hi) == 1) add(i - lo, w);
+        }
+    }
+}
+
+// What the swap of x (in L) with y (in R) changes through one hyperedge
+// (pins[b..e), weight w_eta), with pos the positions before the swap:
+// gadd(v, d) for every pin v whose single-move gain G(v) changes (the
+// hyperedge's side counts change, or v is x or y and changes side), and
+// madd(i, j, d) for the correction entries of pairs of non-moving pins
+// (L position lo + i, R position mid + j), whose weight eta ([cL = 1] +
+// [cR = 1]) changes with the counts. Such a change needs a side count to
+// cross 1, which leaves at most one non-moving pin on that side, so the
+// pairs are O(|a|). Pairs with x or y are left to the rebuild of their row
+// and column. skip_if_x: the hyperedge came from y's incidence list and is
+// handled from x's if it holds x too.
+template <typename GAdd, typename MAdd>
+IP_HD void swap_hedge_update(const int32_t* pins, int64_t b, int64_t e, const int32_t* pos,
+                             int32_t lo, int32_t mid, int32_t hi, int32_t x, int32_t y,
+                             int64_t w_eta, bool skip_if_x, GAdd gadd, MAdd madd)
+{
+    int32_t cL = 0, cR = 0;
+    bool hx = false, hy = false;
+    for (int64_t j = b; j < e; j++) {
+        int32_t q = pins[j];
+        int sd = side_of(pos[q], lo, mid, hi);
+        cL += sd == 1;
+        cR += sd == 2;
+        hx = hx || q == x;
+        hy = hy || q == y;
+    }
+    if (skip_if_x && hx) return;
+    int32_t nL = cL - hx + hy, nR = cR + hx - hy;   // counts after the swap
+    for (int64_t j = b; j < e; j++) {
+        int32_t q = pins[j];
+        int so = side_of(pos[q], lo, mid, hi);
+        if (so == 0) continue;
+        int sn = q == x ? 2 : q == y ? 1 : so;
+        int32_t d = move_delta(sn, nL, nR) - move_delta(so, cL, cR);
+        if (d != 0) gadd(q, w_eta * d);
+    }
+    int32_t dw = ((nL == 1) + (nR == 1)) - ((cL == 1) + (cR == 1));
+    int32_t mL = cL - hx, mR = cR - hy;   // non-moving pins on each side
+    if (dw == 0 || mL == 0 || mR == 0) return;
+    int outer = mL <= mR ? 1 : 2;
+    for (int64_t j = b; j < e; j++) {
+        int32_t u = pins[j];
+        int32_t iu = pos[u];
+        if (u == x || u == y || side_of(iu, lo, mid, hi) != outer) continue;
+        for (int64_t t = b; t < e; t++) {
+            int32_t v = pins[t];
+            int32_t iv = pos[v];
+            if (v == x || v == y || side_of(iv, lo, mid, hi) != 3 - outer) continue;
+            if (outer == 1) madd(iu - lo, iv - mid, w_eta * dw);
+            else madd(iv - lo, iu - mid, w_eta * dw);
+        }
+    }
+}
+
 // Bisection tree of a sequence of n nodes, breadth-first: node 0 = [0, n);
 // a node of more than one position splits into its first ceil(len/2)
 // positions and the rest, children numbered consecutively. Descending

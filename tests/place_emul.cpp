@@ -6,8 +6,8 @@
 // ranks, per-start best prefix, apply). Initial placement: those of
 // csrc/initial_items.cuh in the order of csrc/initial.cu (label propagation
 // of all jobs of a depth in lockstep rounds through single-move gains and a
-// correction matrix, folding from the post-propagation section sets, Hilbert
-// order). It checks those decompositions against the oracle without a GPU.
+// correction matrix built once per depth and updated swap by swap, folding
+// from the post-propagation section sets, Hilbert order). It checks those decompositions against the oracle without a GPU.
 // Test infrastructure only; built by the tests.
 #include "initial_items.cuh"
 #include "place_items.cuh"
@@ -279,31 +279,30 @@ int emul_place_initial(int32_t np, int32_t ne, const int64_t* off, const int32_t
         std::vector<int32_t> done((size_t)S * J, 0), it((size_t)S * J, 0), bx((size_t)S * J),
             by((size_t)S * J);
         std::vector<int64_t> bd((size_t)S * J), M((size_t)S * pairs);
+        // k_ip_gain, k_ip_corr: once per depth
+        for (int32_t s = 0; s < S; s++)
+            for (int32_t i = 0; i < np; i++) {
+                int32_t k = jobof[i];
+                if (k < 0) continue;
+                int32_t x = seq[(size_t)s * np + i];
+                G[(size_t)s * np + x] = ip::single_gain(
+                    vinc.data(), voff[x], voff[x + 1], off, pins, eta, &pos[(size_t)s * np],
+                    ip::side_of(i, jlo[k], jmid[k], jhi[k]), jlo[k], jmid[k], jhi[k]);
+            }
+        std::fill(M.begin(), M.end(), 0);
+        for (int32_t s = 0; s < S; s++)
+            for (int32_t i = 0; i < np; i++) {
+                int32_t k = jobof[i];
+                if (k < 0 || i >= jmid[k]) continue;
+                int32_t x = seq[(size_t)s * np + i], nr = jhi[k] - jmid[k];
+                int64_t* row = &M[(size_t)s * pairs + po[k] + (int64_t)(i - jlo[k]) * nr];
+                ip::corr_row(vinc.data(), voff[x], voff[x + 1], off, pins, eta,
+                             &pos[(size_t)s * np], jlo[k], jmid[k], jhi[k],
+                             [row](int32_t j, int64_t w) { row[j] += w; });
+            }
         for (;;) {
             for (size_t t = 0; t < done.size(); t++)
                 if (!done[t]) { bd[t] = 0; bx[t] = INT32_MAX; by[t] = INT32_MAX; }
-            // k_ip_gain
-            for (int32_t s = 0; s < S; s++)
-                for (int32_t i = 0; i < np; i++) {
-                    int32_t k = jobof[i];
-                    if (k < 0 || done[(size_t)s * J + k]) continue;
-                    int32_t x = seq[(size_t)s * np + i];
-                    G[(size_t)s * np + x] = ip::single_gain(
-                        vinc.data(), voff[x], voff[x + 1], off, pins, eta, &pos[(size_t)s * np],
-                        ip::side_of(i, jlo[k], jmid[k], jhi[k]), jlo[k], jmid[k], jhi[k]);
-                }
-            // k_ip_corr
-            std::fill(M.begin(), M.end(), 0);
-            for (int32_t s = 0; s < S; s++)
-                for (int32_t i = 0; i < np; i++) {
-                    int32_t k = jobof[i];
-                    if (k < 0 || done[(size_t)s * J + k] || i >= jmid[k]) continue;
-                    int32_t x = seq[(size_t)s * np + i], nr = jhi[k] - jmid[k];
-                    int64_t* row = &M[(size_t)s * pairs + po[k] + (int64_t)(i - jlo[k]) * nr];
-                    ip::corr_row(vinc.data(), voff[x], voff[x + 1], off, pins, eta,
-                                 &pos[(size_t)s * np], jlo[k], jmid[k], jhi[k],
-                                 [row](int32_t j, int64_t w) { row[j] += w; });
-                }
             // k_ip_best, three passes
             for (int pass = 0; pass < 3; pass++)
                 for (int32_t s = 0; s < S; s++)
@@ -322,19 +321,48 @@ int emul_place_initial(int32_t np, int32_t ne, const int64_t* off, const int32_t
                             else if (pass == 2 && dd == bd[t] && x == bx[t]) by[t] = std::min(by[t], y);
                         }
                     }
-            // k_ip_apply
+            // k_ip_update
             int active = 0;
             for (int32_t s = 0; s < S; s++)
                 for (int32_t k = 0; k < J; k++) {
                     size_t t = (size_t)s * J + k;
                     if (done[t]) continue;
                     if (bd[t] <= 0) { done[t] = 1; continue; }
+                    bool last = it[t] + 1 >= jcap[k];
+                    const int32_t lo = jlo[k], mid = jmid[k], hi = jhi[k], nr = hi - mid;
                     int32_t* ps = &pos[(size_t)s * np];
                     int32_t* qs = &seq[(size_t)s * np];
+                    int64_t* Gs = &G[(size_t)s * np];
+                    int64_t* Mk = &M[(size_t)s * pairs + po[k]];
                     int32_t x = bx[t], y = by[t], px = ps[x], py = ps[y];
+                    if (!last) {
+                        auto gadd = [Gs](int32_t v, int64_t d) { Gs[v] += d; };
+                        auto madd = [Mk, nr](int32_t i, int32_t j, int64_t d) {
+                            Mk[(int64_t)i * nr + j] += d;
+                        };
+                        for (int64_t u = voff[x]; u < voff[x + 1]; u++) {
+                            int32_t a = vinc[u];
+                            ip::swap_hedge_update(pins, off[a], off[a + 1], ps, lo, mid, hi, x, y,
+                                                  eta[a], false, gadd, madd);
+                        }
+                        for (int64_t u = voff[y]; u < voff[y + 1]; u++) {
+                            int32_t a = vinc[u];
+                            ip::swap_hedge_update(pins, off[a], off[a + 1], ps, lo, mid, hi, x, y,
+                                                  eta[a], true, gadd, madd);
+                        }
+                    }
                     qs[px] = y; qs[py] = x; ps[x] = py; ps[y] = px;
-                    if (++it[t] >= jcap[k]) done[t] = 1;
-                    else active++;
+                    it[t]++;
+                    if (last) { done[t] = 1; continue; }
+                    active++;
+                    int64_t* row = Mk + (int64_t)(px - lo) * nr;
+                    int64_t* col = Mk + (py - mid);
+                    for (int32_t j = 0; j < nr; j++) row[j] = 0;
+                    for (int32_t i = 0; i < mid - lo; i++) col[(int64_t)i * nr] = 0;
+                    ip::corr_row(vinc.data(), voff[y], voff[y + 1], off, pins, eta, ps, lo, mid, hi,
+                                 [row](int32_t j, int64_t w) { row[j] += w; });
+                    ip::corr_col(vinc.data(), voff[x], voff[x + 1], off, pins, eta, ps, lo, mid, hi,
+                                 y, [col, nr](int32_t i, int64_t w) { col[(int64_t)i * nr] += w; });
                 }
             if (!active) break;
         }

@@ -255,3 +255,27 @@ def test_lattice_for():
     for n in range(1, 300):
         w, h = lattice_for(n)
         assert w * h >= n and w * (h - 1) < n and abs(w - h) <= 1
+
+
+def test_initial_large_hyperedges_match_oracle(emul_initial):
+    """Hyperedges of up to 12 pins over 20-64 nodes, several starts: many
+    swaps whose hyperedges cross the count thresholds the incremental
+    updates of the gains and the correction matrix follow."""
+    swaps_seen = 0
+    for seed in range(40):
+        rng = np.random.Generator(np.random.PCG64(70_000 + seed))
+        n = int(rng.integers(20, 65))
+        hedges_ = [rng.choice(n, size=int(rng.integers(2, 13)), replace=False).tolist()
+                   for _ in range(int(rng.integers(n, 3 * n)))]
+        eta = rng.integers(1, 30, size=len(hedges_)).tolist()
+        width = int(np.ceil(np.sqrt(n)))
+        height = -(-n // width)
+        seq0s = [rng.permutation(n).tolist() for _ in range(3)]
+        off, pins = csr(hedges_)
+        rc, seqs, gammas = initial_emul(emul_initial, n, off, pins, eta, width, height, seq0s)
+        assert rc == 0
+        for s, s0 in enumerate(seq0s):
+            want = oracle.initial_sequence(n, off, pins, eta, s0).tolist()
+            assert seqs[s] == want, (seed, s)
+            swaps_seen += sum(a != b for a, b in zip(s0, want))
+    assert swaps_seen > 1000
