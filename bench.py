@@ -196,22 +196,73 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
+def host_cpu():
+    """The host's logical CPU count and CPU model (lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith(("model name", "cpu model")):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    return {"cpus": os.cpu_count(), "model": model}
+
+
+class PinnedToOneCore:
+    """Runs the enclosed code with the calling thread pinned to one core (the
+    last one it may use), restoring its affinity afterwards; the oracle is
+    single-threaded and runs in the calling thread."""
+
+    def __enter__(self):
+        self.saved = None
+        self.cpu = None
+        if hasattr(os, "sched_getaffinity"):
+            try:
+                self.saved = os.sched_getaffinity(0)
+                self.cpu = max(self.saved)
+                os.sched_setaffinity(0, {self.cpu})
+            except OSError:
+                self.saved = None
+                self.cpu = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.saved is not None:
+            os.sched_setaffinity(0, self.saved)
+        return False
+
+
 def cpu_baseline(warm=0, steps=1):
-    """The oracle (single-threaded C) on the bounded sample; pins/s."""
+    """The oracle (single-threaded C) on the bounded sample, pinned to one
+    core; pins/s."""
     import oracle
     hg = snngen.conv(**SAMPLE, name="cfg2-sample")
     oracle.build()
-    for _ in range(warm):
-        oracle.partition(hg)
     times = []
-    for _ in range(steps):
-        t0 = time.perf_counter()
-        oracle.partition(hg)
-        times.append(time.perf_counter() - t0)
+    with PinnedToOneCore() as pin:
+        for _ in range(warm):
+            oracle.partition(hg)
+        for _ in range(steps):
+            t0 = time.perf_counter()
+            oracle.partition(hg)
+            times.append(time.perf_counter() - t0)
     t = statistics.median(times)
+    host = host_cpu()
     return {"value": hg.P / t, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{SAMPLE_DESC}; P={hg.P}; {t:.2f} s per pass",
-            "s_per_pass": t, "pins": hg.P}
+            "s_per_pass": t, "pins": hg.P, "pinned_cpu": pin.cpu,
+            "host_cpus": host["cpus"], "host_model": host["model"]}
 
 
 def place_baseline(budget_s=10.0):
@@ -228,13 +279,14 @@ def place_baseline(budget_s=10.0):
     width = int(math.ceil(math.sqrt(K)))
     height = -(-K // width)
     rng = np.random.Generator(np.random.PCG64(0))
-    n, t0 = 0, time.perf_counter()
-    while n < PLACE_STARTS and (n == 0 or time.perf_counter() - t0 < budget_s):
-        g0 = oracle.initial_placement(K, gp["off"], gp["pins"], gp["eta"], width, height,
-                                      rng.permutation(K))
-        oracle.place_refine(K, gp["off"], gp["pins"], gp["eta"], width, height, g0)
-        n += 1
-    per_start = (time.perf_counter() - t0) / n
+    with PinnedToOneCore():
+        n, t0 = 0, time.perf_counter()
+        while n < PLACE_STARTS and (n == 0 or time.perf_counter() - t0 < budget_s):
+            g0 = oracle.initial_placement(K, gp["off"], gp["pins"], gp["eta"], width, height,
+                                          rng.permutation(K))
+            oracle.place_refine(K, gp["off"], gp["pins"], gp["eta"], width, height, g0)
+            n += 1
+        per_start = (time.perf_counter() - t0) / n
     return {"value": 1.0 / (per_start * PLACE_STARTS), "unit": PLACE_UNIT, "cores": 1,
             "kind": "oracle",
             "sample": (f"{n} whole starts on the G_P of the 8192-neuron conv workload's partition "
@@ -271,7 +323,8 @@ def run_reference(args):
             "config": {"workload": args.config, "description": cfg_desc,
                        "sample": cb["sample"]},
             "cpu_baseline": {"value": cb["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": cb["sample"]},
+                             "sample": cb["sample"], "pinned_cpu": cb["pinned_cpu"],
+                             "host_cpus": cb["host_cpus"], "host_model": cb["host_model"]},
             "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -406,7 +459,8 @@ def run_ours(args):
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline()
-        cb = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        cb = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample", "pinned_cpu",
+                                 "host_cpus", "host_model")}
 
     if rank == 0:
         line = {

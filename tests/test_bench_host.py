@@ -18,3 +18,18 @@ def test_onchip_rate():
     assert r["pair_updates_per_s"] == 5e9
     assert r["pair_updates"] == 2_000_000_000 and r["affinity_ms"] == 400.0
     assert b.onchip_rate(10, 0) is None and b.onchip_rate(10, None) is None
+
+
+def test_pinned_to_one_core_restores_affinity():
+    b = load_bench()
+    if not hasattr(os, "sched_getaffinity"):
+        return
+    before = os.sched_getaffinity(0)
+    with b.PinnedToOneCore() as pin:
+        assert os.sched_getaffinity(0) == {pin.cpu} and pin.cpu in before
+    assert os.sched_getaffinity(0) == before
+
+
+def test_host_cpu():
+    h = load_bench().host_cpu()
+    assert h["cpus"] == os.cpu_count() and (h["model"] is None or isinstance(h["model"], str))
