@@ -279,3 +279,27 @@ def test_initial_large_hyperedges_match_oracle(emul_initial):
             assert seqs[s] == want, (seed, s)
             swaps_seen += sum(a != b for a, b in zip(s0, want))
     assert swaps_seen > 1000
+
+
+def test_repeated_pins_count_with_multiplicity(emul):
+    """snnmap_place_refine's contract: a pin repeated within a hyperedge
+    counts as often as it appears, as in the oracle (forces, re-evaluation
+    and the total residual distance)."""
+    compared = 0
+    for seed in range(200):
+        rng = np.random.Generator(np.random.PCG64(90_000 + seed))
+        width, height = int(rng.integers(2, 6)), int(rng.integers(1, 5))
+        n = int(rng.integers(2, width * height + 1))
+        hedges_ = [rng.integers(0, n, size=int(rng.integers(2, 6))).tolist()
+                   for _ in range(int(rng.integers(1, 2 * n)))]
+        eta = rng.integers(1, 6, size=len(hedges_)).tolist()
+        gamma = rng.choice(width * height, size=n, replace=False).tolist()
+        off, pins = csr(hedges_)
+        want_g, want_logs = oracle.place_refine(n, off, pins, eta, width, height, gamma)
+        rc, got, logs = run_emul(emul, n, off, pins, eta, width, height, [gamma])
+        assert rc == 0
+        assert got[0] == want_g.tolist() and logs[0] == want_logs, seed
+        assert trd_emul(emul, n, off, pins, eta, width, got) == \
+            [oracle.place_trd(n, off, pins, eta, width, want_g)]
+        compared += any(len(set(h)) < len(h) for h in hedges_)
+    assert compared > 100
