@@ -106,6 +106,12 @@ class HGraph:
         N.snnmap_level_cid(self._h, level, t, self.stream)
         return t.cpu().numpy()[:V]
 
+    def trace(self, path, extra=None):
+        """Appends this handle's trace to a JSONL file (write_trace): stage
+        times (when profiling was on), one line per level and one per
+        refinement round."""
+        write_trace(path, self.stage_times(), self.level_logs(), self.round_logs(), extra)
+
     def dump_hierarchy(self, path):
         """Writes every level's arrays (level_arrays) and the cid maps between
         them to one .npz (save_hierarchy), for triage of a mismatch against
@@ -154,6 +160,22 @@ class HGraph:
 
     def device_bytes(self):
         return N.snnmap_device_bytes(self._h)
+
+
+def write_trace(path, stage_times, level_logs, round_logs, extra=None):
+    """Appends one pass's trace to a JSONL file: a "pass" line (extra fields
+    and the stage times: calls and ms per stage), then one "level" line per
+    level (sizes, candidates, pairs, histogram pair terms) and one "round"
+    line per refinement round (level, round, proposals, enacted prefix,
+    gain). Returns the number of lines written."""
+    import json
+    lines = [dict({"kind": "pass", "stages": stage_times}, **(extra or {}))]
+    lines += [dict({"kind": "level", "level": i}, **lv) for i, lv in enumerate(level_logs)]
+    lines += [dict({"kind": "round"}, **r) for r in round_logs]
+    with open(path, "a") as f:
+        for line in lines:
+            f.write(json.dumps(line) + "\n")
+    return len(lines)
 
 
 def save_hierarchy(path, levels, cids):

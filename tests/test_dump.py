@@ -33,3 +33,23 @@ def test_round_trip(tmp_path):
                 assert b[k].dtype == a[k].dtype
     for a, b in zip(cids, got_cids):
         np.testing.assert_array_equal(a, b)
+
+
+def test_write_trace(tmp_path):
+    import json
+    from paper_2609_07577_gb300.api import write_trace
+    path = tmp_path / "t.jsonl"
+    stages = {"affinity": {"calls": 3, "ms": 1.5}}
+    levels = [{"V": 10, "E": 5, "P": 20, "n_cand": 8, "n_pairs": 4, "pair_terms": 30,
+               "n_block": 0, "n_global": 0}, {"V": 6, "E": 4, "P": 12, "n_cand": 0,
+                                              "n_pairs": 0, "pair_terms": 9, "n_block": 0,
+                                              "n_global": 0}]
+    rounds = [{"level": 1, "round": 0, "n_props": 3, "istar": 2, "n_active": 6, "rows": 0,
+               "gain": 7}]
+    assert write_trace(path, stages, levels, rounds, {"workload": "t"}) == 4
+    assert write_trace(path, stages, levels[:1], [], None) == 2
+    lines = [json.loads(x) for x in open(path)]
+    assert [x["kind"] for x in lines] == ["pass", "level", "level", "round", "pass", "level"]
+    assert lines[0]["workload"] == "t" and lines[0]["stages"] == stages
+    assert lines[2]["level"] == 1 and lines[2]["V"] == 6
+    assert lines[3]["gain"] == 7 and lines[3]["istar"] == 2
