@@ -2,7 +2,8 @@
 level's arrays and cid maps exactly as the inspection calls return them
 (levels released under the memory budget are rebuilt for the dump), and its
 level 0 has the oracle's sizes (the parity tests compare the arrays). The
-JSONL trace of a profiled pass holds its stage times, levels and rounds."""
+JSONL trace of a profiled pass holds its stage times, levels and rounds, and
+the command line maps a hypergraph file (partition and placement)."""
 import numpy as np
 import pytest
 
@@ -54,3 +55,22 @@ def test_trace_jsonl(tmp_path):
     assert lines[0]["stages"]["affinity"]["calls"] > 0
     assert sum(x["kind"] == "level" for x in lines) == len(levels) > 0
     assert sum(x["kind"] == "round" for x in lines) == len(rounds) > 0
+
+
+def test_cli_map_with_placement(tmp_path):
+    """python -m paper_2609_07577_gb300 map: the partition equals the
+    oracle's, and the placement gives every partition its own core of the
+    lattice."""
+    from paper_2609_07577_gb300.__main__ import main
+    from paper_2609_07577_gb300.io import save_snn
+    hg = snngen.by_name("cfg1s")
+    src, dst = str(tmp_path / "in.npz"), str(tmp_path / "out.npz")
+    save_snn(src, hg)
+    assert main(["map", src, dst, "--place", "--starts", "4"]) == 0
+    rho_o, cost_o, st_o, *_ = oracle.partition(hg, oracle.params_of(hg))
+    with np.load(dst) as z:
+        np.testing.assert_array_equal(z["rho"], rho_o)
+        assert int(z["cost"]) == cost_o
+        gamma, (w, h) = z["gamma"], z["lattice"]
+        assert len(gamma) == st_o["n_parts"] and len(set(gamma.tolist())) == len(gamma)
+        assert gamma.min() >= 0 and gamma.max() < w * h and int(z["trd"]) > 0
