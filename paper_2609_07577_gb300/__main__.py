@@ -3,7 +3,7 @@
     python -m paper_2609_07577_gb300 map INPUT.npz OUT.npz [--omega N --delta N --phi N]
                                          [--place] [--starts 64] [--seed 0]
 
-INPUT.npz is io.save_snn's format (off, pins, w, V and the per-core limits;
+INPUT.npz is snnfile.save_snn's format (off, pins, w, V and the per-core limits;
 limits given here override the file's). The partition runs on the GPU
 (Sec. 4.1); with --place, the partition hypergraph G_P is placed on the
 smallest near-square lattice of cores by the multi-start placement of Sec.
@@ -38,7 +38,7 @@ def parse(argv=None):
 def map_file(args):
     """Runs one `map` command; returns the dict written to the output."""
     from .api import HGraph, place
-    from .io import load_snn
+    from .snnfile import load_snn
     hg = load_snn(args.input, args.omega, args.delta, args.phi)
     G = HGraph.from_hypergraph(hg)
     try:

@@ -62,7 +62,7 @@ def test_cli_map_with_placement(tmp_path):
     oracle's, and the placement gives every partition its own core of the
     lattice."""
     from paper_2609_07577_gb300.__main__ import main
-    from paper_2609_07577_gb300.io import save_snn
+    from paper_2609_07577_gb300.snnfile import save_snn
     hg = snngen.by_name("cfg1s")
     src, dst = str(tmp_path / "in.npz"), str(tmp_path / "out.npz")
     save_snn(src, hg)

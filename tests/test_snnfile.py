@@ -1,4 +1,4 @@
-"""SNN hypergraph files (paper_2609_07577_gb300.io) and the command line's
+"""SNN hypergraph files (paper_2609_07577_gb300.snnfile) and the command line's
 arguments, without a GPU: from_axons builds the layout the C ABI takes
 (source first, destinations deduplicated, sorted and without the source),
 save/load round-trips arrays and limits (overridable), and malformed input
@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import snngen
-from paper_2609_07577_gb300.io import check_snn, from_axons, load_snn, save_snn
+from paper_2609_07577_gb300.snnfile import check_snn, from_axons, load_snn, save_snn
 
 
 def test_from_axons_layout():
