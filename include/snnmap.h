@@ -94,6 +94,10 @@ typedef struct {
     int64_t pair_terms;  /* sum over hyperedges of |e|(|e|-1): neighbour-histogram updates */
     int32_t n_block;     /* vertices whose histogram needed a block-wide table */
     int32_t n_global;    /* vertices whose histogram needed a table in global memory */
+    int32_t carried;     /* 1: candidates carried from the level above (snnmap_set_coarsen_mode),
+                            2: read from the score matrix, 0: full neighbour histogram */
+    int32_t n_full;      /* vertices that took a full neighbour histogram */
+    int64_t hist_work;   /* elements the level's neighbour histograms visited */
 } snnmap_level_log;
 
 /* Device time of one pipeline stage, summed over the calls since the last
@@ -296,9 +300,37 @@ int snnmap_partition_graph_copy(const snnmap_hgraph* h, int64_t* d_offsets, int3
  * library uses them where the measured work of the level above says they
  * pay. Coarsening levels with V vertices use a V x V score matrix when
  * 16 V^2 fits. -1: the default, 1/4 of the device's memory; 0: none. Results
- * do not depend on it (used only when the summed omega stays below 2^31).
+ * do not depend on it (used only when the summed omega stays below 2^31 and
+ * every axon's weight is positive).
  */
 int snnmap_set_row_budget(snnmap_hgraph* h, int64_t bytes);
+
+/*
+ * How a coarsening level's candidates (Sec. 4.1, Eq. neigh_histogram) are
+ * found after the previous level's contraction. mode 0 (default): each level
+ * chooses by its measured work between a full neighbour histogram and the
+ * carried form, in which only the super-nodes just formed, and vertices whose
+ * candidate merged into a super-node that no longer suits them, take a full
+ * histogram, while every other vertex compares its previous candidate with
+ * the super-nodes just formed among its neighbours (exact: the score, shared
+ * count and validity of two vertices neither of which merged do not change).
+ * 1: always full histograms. 2: the carried form wherever a previous level
+ * exists. Results do not depend on the mode. SNNMAP_ERR_INVALID for another
+ * value.
+ */
+int snnmap_set_coarsen_mode(snnmap_hgraph* h, int32_t mode);
+
+/*
+ * Work thresholds of the histogram tiers (neighbour and connection
+ * histograms): a vertex whose histogram visits at most wwork elements takes
+ * one warp with a shared-memory table, at most bwork one block, at most
+ * gwork one large block per SM, and more the split tier (work items spread
+ * over all SMs into a table in global memory); a vertex whose table
+ * overflows a tier moves on to the next. Negative values keep the current
+ * setting; defaults 8192, 65536 and 4194304. Results do not depend on them
+ * (they place work, not decide it): tests use them to drive every tier.
+ */
+int snnmap_set_histogram_tiers(snnmap_hgraph* h, int64_t wwork, int64_t bwork, int64_t gwork);
 
 /* Bytes of device memory the handle currently holds. */
 int snnmap_device_bytes(const snnmap_hgraph* h, int64_t* bytes);
@@ -323,16 +355,21 @@ void snnmap_free(snnmap_hgraph* h);
  * until the process exits; hence the limit n_hedges <= 4,194,304, larger
  * inputs being rejected with SNNMAP_ERR_INVALID before any work is queued.
  * The first call on a device looks up the array's device address (with that
- * device current) and should come before any stream capture. Each call
- * clears the accumulator before use; calls whose work overlaps on the GPU
- * share the array and race, so callers must not overlap them.
+ * device current). Every call copies its error word to the host and
+ * synchronizes the stream, so no call may be issued on a stream under
+ * capture. Each call clears the accumulator before use; calls whose work
+ * overlaps on the GPU share the array and race, so callers must not overlap
+ * them.
  * Inputs (device, caller-owned): the level-0 layout of snnmap_build_hgraph
  * (d_offsets int64[n_hedges+1], d_pins, d_w int32) and d_rho int32[n_vertices]
- * with values in [0, n_parts). Output: *d_cost_out (device int64) = Conn.
+ * with values in [0, n_parts). The caller guarantees d_offsets[n_hedges] <=
+ * the length of d_pins, as for snnmap_build_hgraph (the call takes no pin
+ * count and cannot check it). Output: *d_cost_out (device int64) = Conn.
  * Axons with no destination count zero. Cost grows with the square of an
- * axon's pin count. Errors: SNNMAP_ERR_INVALID (sizes, host pointers,
- * offsets, pin ids, weights or partition ids out of range), SNNMAP_ERR_CUDA.
- * Synchronizes the stream before returning; snnmap_last_error() describes
+ * axon's pin count. Errors: SNNMAP_ERR_INVALID (negative sizes, n_parts < 1,
+ * n_hedges above the limit, host pointers; d_offsets[0] != 0 or decreasing
+ * offsets; a pin id outside [0, n_vertices); a negative weight; a partition
+ * id outside [0, n_parts)), SNNMAP_ERR_CUDA. snnmap_last_error() describes
  * failures.
  */
 int snnmap_connectivity_noalloc(int32_t n_vertices, int32_t n_hedges, const int64_t* d_offsets,

@@ -8,8 +8,9 @@ limits given here override the file's). The partition runs on the GPU
 (Sec. 4.1); with --place, the partition hypergraph G_P is placed on the
 smallest near-square lattice of cores by the multi-start placement of Sec.
 4.2. OUT.npz holds rho (neuron -> partition), cost (Conn), the pass's
-statistics, and with --place the G_P arrays, gamma (partition -> core),
-the lattice and the total residual distance."""
+statistics, and with --place the G_P arrays over the non-empty partitions
+(parts: the partition id of each G_P node), gamma (G_P node -> core), the
+lattice and the total residual distance."""
 from __future__ import annotations
 
 import argparse
@@ -32,11 +33,16 @@ def parse(argv=None):
     m.add_argument("--place", action="store_true")
     m.add_argument("--starts", type=int, default=64)
     m.add_argument("--seed", type=int, default=0)
-    return ap.parse_args(argv)
+    args = ap.parse_args(argv)
+    if args.starts < 1:
+        ap.error("--starts must be at least 1")
+    return args
 
 
 def map_file(args):
     """Runs one `map` command; returns the dict written to the output."""
+    import torch
+
     from .api import HGraph, place
     from .snnfile import load_snn
     hg = load_snn(args.input, args.omega, args.delta, args.phi)
@@ -46,11 +52,17 @@ def map_file(args):
         out = {"rho": rho.cpu().numpy(), "cost": np.int64(cost),
                "stats": np.asarray(json.dumps(stats))}
         if args.place:
-            K = int(stats["n_parts"])
-            gp = G.partition_graph(rho, K)
+            # G_P over the non-empty partitions only, numbered densely in
+            # the order of their ids (parts[i] is the id of G_P node i), so
+            # that no core is spent on a partition refinement emptied
+            rho_h = out["rho"]
+            parts = np.unique(rho_h).astype(np.int32)
+            dense = np.searchsorted(parts, rho_h).astype(np.int32)
+            K = int(parts.shape[0])
+            gp = G.partition_graph(torch.from_numpy(dense).to(rho.device), K)
             res = place(K, gp["off"], gp["pins"], gp["eta"], n_starts=args.starts,
                         seed=args.seed)
-            out.update(gp_off=gp["off"], gp_pins=gp["pins"], gp_eta=gp["eta"],
+            out.update(gp_off=gp["off"], gp_pins=gp["pins"], gp_eta=gp["eta"], parts=parts,
                        gamma=res["gamma"], trd=np.int64(res["trd"]),
                        lattice=np.asarray([res["width"], res["height"]], np.int32))
     finally:

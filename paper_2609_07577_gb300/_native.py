@@ -38,7 +38,8 @@ class RoundLog(C.Structure):
 class LevelLog(C.Structure):
     _fields_ = [("V", C.c_int32), ("E", C.c_int32), ("P", C.c_int64), ("n_cand", C.c_int32),
                 ("n_pairs", C.c_int32), ("pair_terms", C.c_int64), ("n_block", C.c_int32),
-                ("n_global", C.c_int32)]
+                ("n_global", C.c_int32), ("carried", C.c_int32), ("n_full", C.c_int32),
+                ("hist_work", C.c_int64)]
 
 
 class StageTime(C.Structure):
@@ -102,6 +103,8 @@ _SIGS = {
     "snnmap_launch_count": (_i64, []),
     "snnmap_set_level_budget": (C.c_int, [_vp, _i64]),
     "snnmap_set_row_budget": (C.c_int, [_vp, _i64]),
+    "snnmap_set_coarsen_mode": (C.c_int, [_vp, _i32]),
+    "snnmap_set_histogram_tiers": (C.c_int, [_vp, _i64, _i64, _i64]),
     "snnmap_partition_graph": (C.c_int, [_vp, _i32, _vp, _vp, C.POINTER(_i32), C.POINTER(_i64),
                                          C.POINTER(_i64)]),
     "snnmap_partition_graph_copy": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
@@ -431,6 +434,14 @@ def snnmap_hilbert_order(width, height, d_order_out, stream=None):
 
 def snnmap_set_row_budget(h, nbytes):
     check(lib().snnmap_set_row_budget(h, int(nbytes)))
+
+
+def snnmap_set_coarsen_mode(h, mode):
+    check(lib().snnmap_set_coarsen_mode(h, int(mode)))
+
+
+def snnmap_set_histogram_tiers(h, wwork=-1, bwork=-1, gwork=-1):
+    check(lib().snnmap_set_histogram_tiers(h, int(wwork), int(bwork), int(gwork)))
 
 
 def snnmap_launch_count():

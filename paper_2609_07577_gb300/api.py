@@ -152,6 +152,16 @@ class HGraph:
     def set_level_budget(self, nbytes):
         N.snnmap_set_level_budget(self._h, nbytes)
 
+    def set_coarsen_mode(self, mode):
+        """0 auto, 1 full neighbour histograms, 2 carried candidates wherever
+        possible (results never depend on it)."""
+        N.snnmap_set_coarsen_mode(self._h, mode)
+
+    def set_histogram_tiers(self, wwork=-1, bwork=-1, gwork=-1):
+        """Work thresholds of the histogram tiers (results never depend on
+        them; -1 keeps a value)."""
+        N.snnmap_set_histogram_tiers(self._h, wwork, bwork, gwork)
+
     def profile(self, on=True):
         N.snnmap_profile(self._h, on)
 

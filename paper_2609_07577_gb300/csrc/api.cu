@@ -56,6 +56,7 @@ void bind(snnmap_hgraph* h, void* stream)
 
 void drop_levels_above(snnmap_hgraph* h, size_t keep)
 {
+    h->icar.level = -1;
     while (h->levels.size() > keep) {
         snn::level_free(h, h->levels.back());
         h->levels.pop_back();
@@ -127,6 +128,7 @@ void snnmap_free(snnmap_hgraph* h)
     snn::dense_close(h);
     snn::mat_close(h);
     snn::carry_close(h);
+    snn::aff_carry_free(h);
     snn::gp_free(h);
     drop_levels_above(h, 0);
     h->scratch.release();
@@ -196,8 +198,9 @@ static int snnmap_coarsen_level_impl(snnmap_hgraph* h, void* stream, int32_t* n_
     h->scratch.reset();
     if (!st.ok()) return fail(st);
     const snn::Level& L = h->levels.back();
-    h->llog.push_back(snnmap_level_log{L.V, L.E, L.P, nc, np, h->extra.back().pair_terms,
-                                            h->extra.back().n_block, h->extra.back().n_global});
+    const snn::LevelExtra& X = h->extra.back();
+    h->llog.push_back(snnmap_level_log{L.V, L.E, L.P, nc, np, X.pair_terms, X.n_block,
+                                        X.n_global, X.carried, X.n_full, X.hist_work});
     *n_cand_out = nc;
     *n_pairs_out = np;
     return SNNMAP_OK;
@@ -298,8 +301,9 @@ static int snnmap_partition_impl(snnmap_hgraph* h, void* stream, int32_t* d_rho_
         h->scratch.reset();
         if (!s1.ok()) return fail(s1);
         const snn::Level& L = h->levels.back();
-        h->llog.push_back(snnmap_level_log{L.V, L.E, L.P, nc, np, h->extra.back().pair_terms,
-                                            h->extra.back().n_block, h->extra.back().n_global});
+        const snn::LevelExtra& X = h->extra.back();
+        h->llog.push_back(snnmap_level_log{L.V, L.E, L.P, nc, np, X.pair_terms, X.n_block,
+                                            X.n_global, X.carried, X.n_full, X.hist_work});
         if (nc == 0 || np == 0) break;
         API_TRY(snn::contract_level(h));
         snn::note_bytes(h);
@@ -333,7 +337,7 @@ static int snnmap_partition_impl(snnmap_hgraph* h, void* stream, int32_t* d_rho_
     {
         int64_t rb = snn::dense_row_budget(h);
         int64_t per = ((((int64_t)K + 3) & ~(int64_t)3) * 8 + 12);
-        if (rb > 0 && !h->wide && h->wsum <= INT32_MAX)
+        if (rb > 0 && !h->wide && !h->wzero && h->wsum <= INT32_MAX)
             for (int32_t l = nl - 1; l >= 0 && (int64_t)h->levels[l].V * per <= rb; l--) lb = l;
         if (lb < nl && !snn::dense_open(h, K, h->levels[lb].V).ok()) {
             snn::dense_close(h);
@@ -625,6 +629,26 @@ int snnmap_set_row_budget(snnmap_hgraph* h, int64_t bytes)
 {
     if (!h || bytes < -1) return fail(SNNMAP_ERR_INVALID, "bad arguments");
     h->row_budget = bytes;
+    return SNNMAP_OK;
+}
+
+int snnmap_set_coarsen_mode(snnmap_hgraph* h, int32_t mode)
+{
+    g_err.clear();
+    if (!h) return fail(SNNMAP_ERR_INVALID, "NULL handle");
+    if (mode < 0 || mode > 2) return fail(SNNMAP_ERR_INVALID, "mode must be 0, 1 or 2");
+    h->coarsen_mode = mode;
+    if (mode == 1) h->icar.level = -1;
+    return SNNMAP_OK;
+}
+
+int snnmap_set_histogram_tiers(snnmap_hgraph* h, int64_t wwork, int64_t bwork, int64_t gwork)
+{
+    g_err.clear();
+    if (!h) return fail(SNNMAP_ERR_INVALID, "NULL handle");
+    if (wwork >= 0) h->tiers.wwork = wwork;
+    if (bwork >= 0) h->tiers.bwork = bwork;
+    if (gwork >= 0) h->tiers.gwork = gwork;
     return SNNMAP_OK;
 }
 

@@ -304,11 +304,13 @@ __global__ void k_in_hedges(const int64_t* __restrict__ off, const int32_t* __re
 {
     int32_t bad = 0;
     int64_t mx = 0, wsum = 0;
+    int32_t zero = 0;
     for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < E;
          a += (int64_t)gridDim.x * blockDim.x) {
         int64_t len = off[a + 1] - off[a];
         if (len < 1 || len > 0x7fffffff || w[a] < 0) bad = 1;
         int k = len >= 2 ? 1 : 0;
+        if (k && w[a] == 0) zero = 1;
         kept[a] = k;
         klen[a] = k ? len : 0;
         if (len > mx) mx = len;
@@ -320,9 +322,11 @@ __global__ void k_in_hedges(const int64_t* __restrict__ off, const int32_t* __re
         mx = m2 > mx ? m2 : mx;
         wsum += __shfl_xor_sync(FULL, wsum, o);
         bad |= __shfl_xor_sync(FULL, bad, o);
+        zero |= __shfl_xor_sync(FULL, zero, o);
     }
     if ((threadIdx.x & 31) == 0) {
         if (bad) atomicOr((int*)&scal[SC_STATUS], ST_INVALID);
+        if (zero) atomicOr((int*)&scal[SC_E], 1);
         atomicMax((unsigned long long*)&scal[SC_C], (unsigned long long)mx);
         atomicAdd((unsigned long long*)&scal[SC_D], (unsigned long long)wsum);
     }
@@ -465,6 +469,7 @@ Status build_level0(snnmap_hgraph* h, int32_t V, int32_t E, const int64_t* d_off
     int32_t maxlen = (int32_t)h->h_scal[SC_C];
     h->wide = (uint64_t)h->h_scal[SC_D] >= 0xffffffffull;
     h->wsum = h->h_scal[SC_D];
+    h->wzero = h->h_scal[SC_E] != 0;
 
     h->levels.emplace_back();
     h->extra.emplace_back();

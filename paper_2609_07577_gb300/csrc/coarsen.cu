@@ -59,10 +59,12 @@ struct AffPol {
     int32_t* cov;
     const int32_t* vmin;   // smallest size and inbound pins over the level's vertices
     bool prefilter;        // some pair can break Omega or Phi (else elem skips the test)
+    const uint8_t* only = nullptr;   // if set, the vertices evaluated (others untouched)
 
     // n cannot merge even with the smallest vertex: no candidate
     __device__ bool skip(int32_t n) const
     {
+        if (only && !only[n]) return true;
         return (int64_t)L.vsize[n] + vmin[0] > omega || (int64_t)L.vinpins[n] + vmin[1] > phi;
     }
     __device__ int64_t vb(int32_t n) const { return L.voff[n]; }
@@ -112,6 +114,7 @@ struct AffPol {
     }
     __device__ void write(int32_t n, int64_t bs, int32_t bk, uint32_t bo, const Acc&) const
     {
+        if (only && !only[n]) return;
         cand[n] = bk;
         cscore[n] = bk < 0 ? 0 : bs;
         cov[n] = bk < 0 ? 0 : (int32_t)bo;
@@ -306,13 +309,381 @@ static Status affinity(snnmap_hgraph* h, Level& L)
     pol.cscore = h->cscore;
     pol.cov = h->cov;
     int64_t* cnt;
-    SNN_TRY(h->scratch.alloc(&cnt, HT_NTIER));
-    SNN_TRY(run_histogram(pol, h->scratch, h->stream, cnt, h->h_scal + 12, h->d_scal));
-    int64_t hc[HT_NTIER] = {0, 0, 0, 0};
-    SNN_CUDA(cudaMemcpyAsync(hc, cnt, HT_NTIER * sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream));
+    SNN_TRY(h->scratch.alloc(&cnt, HT_NCNT));
+    SNN_TRY(run_histogram(pol, h->scratch, h->stream, cnt, h->h_scal + 12, h->d_scal, h->tiers));
+    int64_t hc[HT_NCNT] = {};
+    SNN_CUDA(cudaMemcpyAsync(hc, cnt, HT_NCNT * sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream));
     SNN_CUDA(cudaStreamSynchronize(h->stream));
-    h->extra.back().n_block = (int32_t)(hc[HT_TIER_BLOCK] + hc[HT_TIER_BIG]);
-    h->extra.back().n_global = (int32_t)hc[HT_TIER_SPLIT];
+    LevelExtra& X = h->extra.back();
+    X.n_block = (int32_t)(hc[HT_TIER_BLOCK] + hc[HT_TIER_BIG]);
+    X.n_global = (int32_t)hc[HT_TIER_SPLIT];
+    X.carried = 0;
+    X.n_full = (int32_t)hc[HT_CNT_VERTS];
+    X.hist_work = hc[HT_CNT_WORK];
+    return Status{};
+}
+
+
+// ---------------------------------------------------------------------------
+// Candidates carried through a contraction.
+//
+// After level l is contracted, a vertex x of level l + 1 is either the
+// super-node of a matched pair (NEW) or the image of an unmatched vertex n.
+// For two unmatched vertices every hyperedge holding both maps onto one of
+// the same omega, k and destination roles (a hyperedge vanishes only when all
+// its pins share one super-node; duplicates that merge hold both as well),
+// and their sizes and inbound counts are unchanged: their score, shared count
+// and validity carry over. With c = cand(n) at level l:
+//   c = -1 (NONE): no unmatched neighbour is valid; only new super-nodes
+//       adjacent to x can be x's candidate.
+//   c unmatched (KEEP): cid(c) stays the best unmatched neighbour with the
+//       same score; a new super-node beats it only by Eq. neigh_histogram's
+//       order (larger score, ties to the lower id).
+//   c matched (MERGED), w = cid(c): score(x, w) >= score(n, c), and w's id is
+//       below that of every unmatched neighbour of equal score (cid keeps the
+//       order of representatives, and min(c, match(c)) <= c), so if w is
+//       valid the best valid new super-node is the candidate; if the best one
+//       is not w, x is evaluated in full.
+// Scores towards new super-nodes come from the hyperedges holding one: each
+// such hyperedge's list of new super-nodes (with destination roles) is the
+// segment x visits, so this histogram does sum_a |a| |new(a)| updates
+// instead of sum_a |a| (|a| - 1). New super-nodes and rejected MERGED vertices
+// then get the full histogram.
+
+enum : uint8_t { AK_NONE = 0, AK_KEEP = 1, AK_MERGED = 2, AK_NEW = 3 };
+constexpr uint32_t NOT_DEST = 0x80000000u;
+
+__global__ void k_ac_prep(int32_t V, const int32_t* __restrict__ cid,
+                          const int32_t* __restrict__ match, const int32_t* __restrict__ cand,
+                          const int64_t* __restrict__ cscore, const int32_t* __restrict__ cov,
+                          AffCarry ac)
+{
+    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < V;
+         n += (int64_t)gridDim.x * blockDim.x) {
+        int32_t x = cid[n];
+        if (match[n] >= 0) {
+            ac.kind[x] = AK_NEW;
+            ac.full[x] = 1;
+            continue;
+        }
+        int32_t c = cand[n];
+        uint8_t k = AK_NONE;
+        int32_t ic = -1;
+        if (c >= 0) {
+            ic = cid[c];
+            k = match[c] >= 0 ? AK_MERGED : AK_KEEP;
+        }
+        ac.kind[x] = k;
+        ac.full[x] = 0;
+        ac.cand[x] = ic;
+        ac.score[x] = k == AK_KEEP ? cscore[n] : 0;
+        ac.ov[x] = k == AK_KEEP ? cov[n] : 0;
+    }
+}
+
+// per hyperedge: its number of new super-nodes; work[0] += (|a| - cnt) cnt
+__global__ void __launch_bounds__(256)
+    k_ac_count(Level L, const uint8_t* __restrict__ kind, int32_t* lcnt, int64_t* work)
+{
+    int lane = threadIdx.x & 31;
+    int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int64_t acc = 0;
+    for (int64_t a = gw; a < L.E; a += nw) {
+        int64_t b = L.hoff[a], e = L.hoff[a + 1];
+        int c = 0;
+        for (int64_t j = b + lane; j < e; j += 32) c += kind[L.hpins[j]] == AK_NEW;
+        c = warp_sum(c);
+        if (lane == 0) {
+            lcnt[a] = c;
+            acc += (e - b - c) * (int64_t)c;
+        }
+    }
+    if (lane == 0 && acc) atomicAdd((unsigned long long*)work, (unsigned long long)acc);
+}
+
+// the lists: new super-nodes of each hyperedge in pin order, bit 31 set for
+// a source that is not also a destination
+__global__ void __launch_bounds__(256)
+    k_ac_fill(Level L, const uint8_t* __restrict__ kind, const int64_t* __restrict__ loff,
+              uint32_t* lpins)
+{
+    int lane = threadIdx.x & 31;
+    unsigned lt = lanemask_lt();
+    int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t a = gw; a < L.E; a += nw) {
+        int64_t b = L.hoff[a], e = L.hoff[a + 1];
+        int64_t o = loff[a];
+        if (loff[a + 1] == o) continue;
+        int sd = L.hsd[a];
+        for (int64_t cb = b; cb < e; cb += 32) {
+            int64_t j = cb + lane;
+            int32_t m = j < e ? L.hpins[j] : 0;
+            bool nw_ = j < e && kind[m] == AK_NEW;
+            unsigned mk = __ballot_sync(FULL, nw_);
+            if (nw_)
+                lpins[o + __popc(mk & lt)] = (uint32_t)m | ((j != b || sd) ? 0u : NOT_DEST);
+            o += __popc(mk);
+        }
+    }
+}
+
+// work[0] += incidence segment lengths of the NEW vertices, work[1] those of
+// the MERGED ones (what full histograms of them cost at most)
+__global__ void __launch_bounds__(256)
+    k_ac_fullwork(Level L, const uint8_t* __restrict__ kind, int64_t* work)
+{
+    int lane = threadIdx.x & 31;
+    int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int64_t acc[2] = {0, 0};
+    for (int64_t base = gw * 32; base < L.V; base += nw * 32) {
+        int64_t n = base + lane;
+        uint8_t k = n < L.V ? kind[n] : AK_NONE;
+        unsigned mem = __ballot_sync(FULL, k >= AK_MERGED);
+        while (mem) {
+            int src = __ffs(mem) - 1;
+            mem &= mem - 1;
+            int32_t m = (int32_t)__shfl_sync(FULL, (int32_t)n, src);
+            int which = __shfl_sync(FULL, (int)k, src) == AK_NEW ? 0 : 1;
+            int64_t t = 0;
+            for (int64_t i = L.voff[m] + lane; i < L.voff[m + 1]; i += 32) {
+                int32_t a = (int32_t)((uint32_t)L.vinc[i] & ~SRC_BIT);
+                t += L.hoff[a + 1] - L.hoff[a];
+            }
+            acc[which] += t;
+        }
+    }
+    for (int u = 0; u < 2; u++) {
+        int64_t v = warp_sum(acc[u]);
+        if (lane == 0 && v) atomicAdd((unsigned long long*)&work[1 + u], (unsigned long long)v);
+    }
+}
+
+// Histogram of each carried vertex over the new super-nodes of its
+// hyperedges, combined with its carried candidate.
+template <typename S_>
+struct AffNewPol {
+    using S = S_;
+    static constexpr bool kOptimistic = false;
+    struct Acc {
+        __device__ Acc() {}
+        __device__ void add(const Acc&) {}
+        __device__ void atomic_into(Acc*) const {}
+    };
+    static __device__ Acc warp_reduce(const Acc& a) { return a; }
+
+    Level L;
+    int32_t V;
+    int64_t keys;
+    int32_t omega, delta, phi;
+    const int64_t* loff;
+    const uint32_t* lpins;
+    AffCarry ac;
+    bool prefilter;
+    int32_t* cand;
+    int64_t* cscore;
+    int32_t* cov;
+
+    __device__ bool skip(int32_t n) const { return ac.kind[n] == AK_NEW; }
+    __device__ int64_t vb(int32_t n) const { return L.voff[n]; }
+    __device__ int64_t ve(int32_t n) const { return L.voff[n + 1]; }
+    __device__ int64_t seg_len(int64_t i) const
+    {
+        int32_t a = (int32_t)((uint32_t)L.vinc[i] & ~SRC_BIT);
+        return loff[a + 1] - loff[a];
+    }
+    __device__ Seg<S> seg(int64_t i, Acc&) const
+    {
+        uint32_t inc = (uint32_t)L.vinc[i];
+        int32_t a = (int32_t)(inc & ~SRC_BIT);
+        Seg<S> g;
+        g.sd = L.hsd[a];
+        g.nd = !(inc & SRC_BIT) || g.sd;
+        g.b = loff[a];
+        g.len = (int32_t)(loff[a + 1] - g.b);
+        g.w = (S)L.hw[a];
+        g.k = (uint32_t)L.hk[a];
+        return g;
+    }
+    template <class Tb>
+    __device__ bool elem(int32_t n, const Seg<S>& g, int32_t off, const Tb& t, Acc&) const
+    {
+        uint32_t e = lpins[g.b + off];
+        int32_t m = (int32_t)(e & ~NOT_DEST);
+        if (prefilter && ((int64_t)L.vsize[n] + L.vsize[m] > omega ||
+                          (int64_t)L.vinpins[n] + L.vinpins[m] > phi))
+            return true;
+        return t.add(m, g.w, (g.nd && !(e & NOT_DEST)) ? g.k : 0u);
+    }
+    __device__ void consider(int32_t n, int32_t m, int64_t s, uint32_t o, const Acc&, int64_t& bs,
+                             int32_t& bk, uint32_t& bo) const
+    {
+        bool valid = (int64_t)L.vsize[n] + L.vsize[m] <= omega &&
+                     (int64_t)L.vinpins[n] + L.vinpins[m] <= phi &&
+                     (int64_t)L.vincnt[n] + L.vincnt[m] - (int64_t)o <= delta;
+        if (valid && better(s, m, bs, bk)) {
+            bs = s;
+            bk = m;
+            bo = o;
+        }
+    }
+    __device__ void write(int32_t n, int64_t bs, int32_t bk, uint32_t bo, const Acc&) const
+    {
+        uint8_t k = ac.kind[n];
+        if (k == AK_NEW) return;
+        if (k == AK_KEEP && better(ac.score[n], ac.cand[n], bs, bk)) {
+            bs = ac.score[n];
+            bk = ac.cand[n];
+            bo = (uint32_t)ac.ov[n];
+        } else if (k == AK_MERGED && bk != ac.cand[n]) {
+            ac.full[n] = 1;
+            return;
+        }
+        cand[n] = bk;
+        cscore[n] = bk < 0 ? 0 : bs;
+        cov[n] = bk < 0 ? 0 : (int32_t)bo;
+    }
+};
+
+void aff_carry_free(snnmap_hgraph* h)
+{
+    AffCarry& C = h->icar;
+    for (void* p : {(void*)C.cand, (void*)C.score, (void*)C.ov, (void*)C.kind, (void*)C.full})
+        if (p) cudaFreeAsync(p, h->stream);
+    C = AffCarry{};
+}
+
+Status aff_carry(snnmap_hgraph* h, int32_t src)
+{
+    AffCarry& C = h->icar;
+    C.level = -1;
+    if (h->coarsen_mode == 1 || h->levels.size() != (size_t)src + 2) return Status{};
+    const Level& F = h->levels[src];
+    if (C.cap < h->levels[src + 1].V) {
+        aff_carry_free(h);
+        size_t n = (size_t)(h->cap_v > 0 ? h->cap_v : 1);
+        cudaStream_t s = h->stream;
+        bool ok = cudaMallocAsync(&C.cand, n * 4, s) == cudaSuccess &&
+                  cudaMallocAsync(&C.score, n * 8, s) == cudaSuccess &&
+                  cudaMallocAsync(&C.ov, n * 4, s) == cudaSuccess &&
+                  cudaMallocAsync(&C.kind, n, s) == cudaSuccess &&
+                  cudaMallocAsync(&C.full, n, s) == cudaSuccess;
+        if (!ok) {
+            // no room: the next levels take full histograms
+            cudaGetLastError();
+            aff_carry_free(h);
+            return Status{};
+        }
+        C.cap = (int64_t)n;
+    }
+    if (F.V > 0) {
+        SNN_L k_ac_prep<<<grid_for(F.V, 256), 256, 0, h->stream>>>(F.V, F.cid, h->match, h->cand,
+                                                                  h->cscore, h->cov, C);
+        SNN_CUDA(cudaGetLastError());
+    }
+    C.level = src + 1;
+    return Status{};
+}
+
+// S1 on a level whose candidates were carried: *done false when the full
+// histogram is expected to be cheaper (nothing written then)
+template <typename S>
+static Status affinity_carried(snnmap_hgraph* h, Level& L, bool* done)
+{
+    *done = false;
+    cudaStream_t s = h->stream;
+    Arena& ar = h->scratch;
+    AffCarry& C = h->icar;
+    int64_t E = L.E;
+    int32_t *vmin, *lcnt;
+    int64_t *work, *loff;
+    SNN_TRY(ar.alloc(&vmin, 4));
+    SNN_TRY(ar.alloc(&work, 4));
+    SNN_TRY(ar.alloc(&lcnt, E));
+    SNN_TRY(ar.alloc(&loff, E + 1));
+    SNN_TRY(fill_i32(vmin, 0x7fffffff, 2, s));
+    SNN_CUDA(cudaMemsetAsync(vmin + 2, 0, 2 * sizeof(int32_t), s));
+    SNN_CUDA(cudaMemsetAsync(work, 0, 4 * sizeof(int64_t), s));
+    SNN_L k_level_min<<<grid_for(L.V, 256), 256, 0, s>>>(L, vmin);
+    if (E > 0) SNN_L k_ac_count<<<grid_for(E * 32, 256), 256, 0, s>>>(L, C.kind, lcnt, work);
+    SNN_L k_ac_fullwork<<<grid_for(L.V, 256), 256, 0, s>>>(L, C.kind, work);
+    SNN_CUDA(cudaGetLastError());
+    SNN_TRY(scan_exclusive_i32_to_i64(lcnt, loff, E, loff + E, ar, s));
+    int64_t hv[4];
+    int32_t vm[4];
+    SNN_CUDA(cudaMemcpyAsync(vm, vmin, sizeof(vm), cudaMemcpyDeviceToHost, s));
+    SNN_CUDA(cudaMemcpyAsync(hv, work, 3 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    SNN_CUDA(cudaMemcpyAsync(hv + 3, loff + E, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    SNN_CUDA(cudaStreamSynchronize(s));
+    // carried work: the new super-nodes' lists, the new super-nodes' full
+    // histograms, and those of the MERGED vertices whose super-node no
+    // longer suits them (at most hv[2]; usually few)
+    int64_t full_work = h->extra.back().pair_terms + L.P;
+    if (h->coarsen_mode != 2 && 4 * (hv[0] + hv[1]) >= 3 * full_work) return Status{};
+    uint32_t* lpins;
+    SNN_TRY(ar.alloc(&lpins, hv[3]));
+    if (E > 0 && hv[3] > 0)
+        SNN_L k_ac_fill<<<grid_for(E * 32, 256), 256, 0, s>>>(L, C.kind, loff, lpins);
+    SNN_CUDA(cudaGetLastError());
+    bool prefilter = 2 * (int64_t)vm[2] > h->prm.omega || 2 * (int64_t)vm[3] > h->prm.phi;
+    int64_t* cnt;
+    SNN_TRY(ar.alloc(&cnt, HT_NCNT));
+    int64_t nb = 0, ng = 0, nf = 0, wk = 0;
+    {
+        AffNewPol<S> pol;
+        pol.L = L;
+        pol.V = L.V;
+        pol.keys = h->last_pairs > 0 ? h->last_pairs : 1;
+        pol.omega = h->prm.omega;
+        pol.delta = h->prm.delta;
+        pol.phi = h->prm.phi;
+        pol.loff = loff;
+        pol.lpins = lpins;
+        pol.ac = C;
+        pol.prefilter = prefilter;
+        pol.cand = h->cand;
+        pol.cscore = h->cscore;
+        pol.cov = h->cov;
+        SNN_TRY(run_histogram(pol, ar, s, cnt, h->h_scal + 12, h->d_scal, h->tiers));
+        int64_t hc[HT_NCNT];
+        SNN_CUDA(cudaMemcpyAsync(hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, s));
+        SNN_CUDA(cudaStreamSynchronize(s));
+        nb += hc[HT_TIER_BLOCK] + hc[HT_TIER_BIG];
+        ng += hc[HT_TIER_SPLIT];
+        wk += hc[HT_CNT_WORK];
+    }
+    {
+        AffPol<S> pol;
+        pol.vmin = vmin;
+        pol.prefilter = prefilter;
+        pol.only = C.full;
+        pol.L = L;
+        pol.V = L.V;
+        pol.keys = L.V;
+        pol.omega = h->prm.omega;
+        pol.delta = h->prm.delta;
+        pol.phi = h->prm.phi;
+        pol.cand = h->cand;
+        pol.cscore = h->cscore;
+        pol.cov = h->cov;
+        SNN_TRY(run_histogram(pol, ar, s, cnt, h->h_scal + 12, h->d_scal, h->tiers));
+        int64_t hc[HT_NCNT];
+        SNN_CUDA(cudaMemcpyAsync(hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, s));
+        SNN_CUDA(cudaStreamSynchronize(s));
+        nb += hc[HT_TIER_BLOCK] + hc[HT_TIER_BIG];
+        ng += hc[HT_TIER_SPLIT];
+        wk += hc[HT_CNT_WORK];
+        nf += hc[HT_CNT_VERTS];
+    }
+    LevelExtra& X = h->extra.back();
+    X.n_block = (int32_t)nb;
+    X.n_global = (int32_t)ng;
+    X.carried = 1;
+    X.n_full = (int32_t)nf;
+    X.hist_work = wk;
+    *done = true;
     return Status{};
 }
 
@@ -330,7 +701,12 @@ Status coarsen_level(snnmap_hgraph* h, int32_t* n_cand, int32_t* n_pairs)
     {
         ProfScope prof(h, PS_AFFINITY);
         bool done = false;
-        SNN_TRY(mat_affinity(h, (int32_t)h->levels.size() - 1, &done));
+        int32_t lev = (int32_t)h->levels.size() - 1;
+        SNN_TRY(mat_affinity(h, lev, &done));
+        if (!done && h->icar.level == lev) {
+            if (h->wide) SNN_TRY(affinity_carried<unsigned long long>(h, L, &done));
+            else SNN_TRY(affinity_carried<uint32_t>(h, L, &done));
+        }
         if (done) {
         } else if (h->wide) {
             SNN_TRY(affinity<unsigned long long>(h, L));

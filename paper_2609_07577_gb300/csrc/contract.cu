@@ -424,10 +424,9 @@ Status contract_level(snnmap_hgraph* h)
     h->extra.emplace_back();
     SNN_TRY(build_coarse(h, src, h->levels[src].cid, d_V2, src + 1));
     h->have_matching = false;
-    if (h->mat.level == src) {
-        ProfScope prof(h, PS_AFFINITY);
-        SNN_TRY(mat_descend(h, src));
-    }
+    ProfScope prof(h, PS_AFFINITY);
+    if (h->mat.level == src) SNN_TRY(mat_descend(h, src));
+    if (h->mat.level != src + 1) SNN_TRY(aff_carry(h, src));
     return Status{};
 }
 

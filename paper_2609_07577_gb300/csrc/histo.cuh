@@ -38,6 +38,7 @@
 //   __device__ void write(n, best, bkey, bov, const Acc& total)
 #pragma once
 #include "common.cuh"
+#include "histo_tiers.cuh"
 
 #include <algorithm>
 
@@ -208,14 +209,14 @@ __device__ __forceinline__ void warp_argmax(int64_t& bs, int32_t& bm, uint32_t& 
 constexpr int HT_WARPS = 8;
 constexpr int HT_WCAP = 512;            // warp table slots
 constexpr int HT_WLOAD = HT_WCAP * 3 / 4;
-constexpr int64_t HT_WWORK = 8192;      // most elements one warp takes alone
 constexpr int HT_BTHREADS = 256;
 constexpr int HT_BCAP = 2048;           // block table slots
-constexpr int64_t HT_BWORK = 1 << 16;
 constexpr int HT_GTHREADS = 512;        // big-block tier
-constexpr int64_t HT_GWORK = 1 << 22;
 constexpr int64_t HT_CHUNK = 1024;      // incidences per split-tier work item
 enum : int { HT_TIER_WARP = 0, HT_TIER_BLOCK = 1, HT_TIER_BIG = 2, HT_TIER_SPLIT = 3, HT_NTIER = 4 };
+// counters of run_histogram: per-tier vertex counts, then the summed work and
+// the number of vertices given a histogram (not skipped)
+enum : int { HT_CNT_WORK = HT_NTIER, HT_CNT_VERTS = HT_NTIER + 1, HT_NCNT = HT_NTIER + 2 };
 
 template <typename S>
 __host__ __device__ constexpr int big_cap()
@@ -267,10 +268,11 @@ __device__ __forceinline__ void ht_push(const Pol& pol, int tier, int32_t n, int
 template <class Pol>
 __global__ void __launch_bounds__(256)
     k_ht_classify(Pol pol, const int64_t* __restrict__ workv, int32_t* lists, int64_t* cnt,
-                  int64_t* scap)
+                  int64_t* scap, HtTiers tiers)
 {
     int lane = threadIdx.x & 31;
     unsigned lt = lanemask_lt();
+    int64_t wsum = 0, vsum = 0;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < pol.V;
          base += (int64_t)gridDim.x * blockDim.x) {
         int64_t n = base + threadIdx.x;
@@ -281,11 +283,13 @@ __global__ void __launch_bounds__(256)
             if (work < 0) {
                 pol.write((int32_t)n, 0, -1, 0, typename Pol::Acc());
             } else {
+                wsum += work;
+                vsum++;
                 int64_t bound = work < pol.keys ? work : pol.keys;
-                if (bound <= HT_WLOAD) tier = work <= HT_WWORK ? HT_TIER_WARP : HT_TIER_SPLIT;
-                else if (Pol::kOptimistic && work <= HT_WWORK) tier = HT_TIER_WARP;
-                else if (work <= HT_BWORK) tier = HT_TIER_BLOCK;
-                else if (work <= HT_GWORK) tier = HT_TIER_BIG;
+                if (bound <= HT_WLOAD) tier = work <= tiers.wwork ? HT_TIER_WARP : HT_TIER_SPLIT;
+                else if (Pol::kOptimistic && work <= tiers.wwork) tier = HT_TIER_WARP;
+                else if (work <= tiers.bwork) tier = HT_TIER_BLOCK;
+                else if (work <= tiers.gwork) tier = HT_TIER_BIG;
                 else tier = HT_TIER_SPLIT;
             }
         }
@@ -305,6 +309,12 @@ __global__ void __launch_bounds__(256)
                 }
             }
         }
+    }
+    wsum = warp_sum(wsum);
+    vsum = warp_sum(vsum);
+    if (lane == 0 && vsum) {
+        atomicAdd((unsigned long long*)&cnt[HT_CNT_WORK], (unsigned long long)wsum);
+        atomicAdd((unsigned long long*)&cnt[HT_CNT_VERTS], (unsigned long long)vsum);
     }
 }
 
@@ -818,10 +828,11 @@ Status split_cuts(const Pol& pol, Arena& ar, cudaStream_t s, const int32_t* sl, 
 // Host driver: work, classification and the warp, block and big-block tiers
 // run without host synchronization; the split tier follows reads of its
 // sizes. d_cnt: >= HT_NTIER device int64; h_cnt: a pinned host int64[>=3];
-// status: device word.
+// status: device word. d_cnt: >= HT_NCNT device int64 (per-tier counts, summed
+// work, vertices histogrammed).
 template <class Pol>
 Status run_histogram(const Pol& pol, Arena& ar, cudaStream_t s, int64_t* d_cnt, int64_t* h_cnt,
-                     int64_t* status)
+                     int64_t* status, const HtTiers& tiers = HtTiers{})
 {
     using S = typename Pol::S;
     int32_t V = pol.V;
@@ -831,10 +842,10 @@ Status run_histogram(const Pol& pol, Arena& ar, cudaStream_t s, int64_t* d_cnt, 
     SNN_TRY(ar.alloc(&lists, (int64_t)HT_NTIER * V));
     SNN_TRY(ar.alloc(&scap, V));
     SNN_TRY(ar.alloc(&workv, V));
-    SNN_CUDA(cudaMemsetAsync(d_cnt, 0, HT_NTIER * sizeof(int64_t), s));
+    SNN_CUDA(cudaMemsetAsync(d_cnt, 0, HT_NCNT * sizeof(int64_t), s));
     SNN_L k_ht_work<Pol><<<grid_for((int64_t)V * 32, 256), 256, 0, s>>>(pol, workv);
     SNN_CUDA(cudaGetLastError());
-    SNN_L k_ht_classify<Pol><<<grid_for(V, 256), 256, 0, s>>>(pol, workv, lists, d_cnt, scap);
+    SNN_L k_ht_classify<Pol><<<grid_for(V, 256), 256, 0, s>>>(pol, workv, lists, d_cnt, scap, tiers);
     SNN_CUDA(cudaGetLastError());
     size_t wsm = (size_t)HT_WARPS * HT_WCAP * slot_bytes<S>();
     size_t bsm = (size_t)HT_BCAP * slot_bytes<S>();

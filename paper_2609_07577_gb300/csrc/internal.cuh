@@ -3,6 +3,7 @@
 #include "../../include/snnmap.h"
 #include "common.cuh"
 #include "segsort.cuh"
+#include "histo_tiers.cuh"
 
 #include <vector>
 
@@ -21,6 +22,9 @@ struct LevelExtra {
     int64_t pair_terms = 0;  // sum of |e|(|e|-1)
     int32_t n_block = 0;     // last histogram: vertices on the block tier
     int32_t n_global = 0;    //                 and on the global-memory tier
+    int32_t carried = 0;     // candidates: 0 full histogram, 1 carried, 2 score matrix
+    int32_t n_full = 0;      // vertices given a full neighbour histogram
+    int64_t hist_work = 0;   // elements visited by the neighbour histograms
 };
 
 // pipeline stages timed by the profiler
@@ -74,6 +78,19 @@ struct Carry {
     int32_t level = -1;   // level whose final state buffers[cur] hold (-1: none)
 };
 
+// Candidates carried through a contraction (coarsen.cu, aff_carry): for each
+// vertex of `level`, what its previous-level candidate says about it
+// (kind), and the carried candidate, score and shared count.
+struct AffCarry {
+    int32_t* cand = nullptr;
+    int64_t* score = nullptr;
+    int32_t* ov = nullptr;
+    uint8_t* kind = nullptr;
+    uint8_t* full = nullptr;    // vertices needing a full histogram
+    int64_t cap = 0;
+    int32_t level = -1;         // level the carry describes (-1: none)
+};
+
 // The partition hypergraph G_P of the last snnmap_partition_graph call.
 struct GpOut {
     int64_t* hoff = nullptr;
@@ -109,11 +126,16 @@ struct snnmap_hgraph {
     int32_t last_pairs = 0;
     bool wide = false;           // some neighbour score may reach 2^32
     int64_t wsum = 0;            // sum of omega over the input hyperedges
+    bool wzero = false;          // some kept hyperedge has omega 0: adjacency is not a
+                                 // nonzero score, so no score matrix and no connection rows
     int64_t row_budget = -1;     // bytes for connection rows (-1: default, 0: none)
     snn::DenseRows dense;
     snn::ScoreMat mat;
     snn::GpOut gp;
     snn::Carry carry;
+    snn::AffCarry icar;
+    int32_t coarsen_mode = 0;    // 0 auto, 1 full histograms, 2 carried whenever possible
+    snn::HtTiers tiers;          // histogram tier thresholds
     std::vector<snnmap_round_log> rlog;
     std::vector<snnmap_level_log> llog;
     // profiler
@@ -183,6 +205,9 @@ Status gp_input(int32_t np, int32_t ne, const int64_t* off, const int32_t* pins,
                 int32_t** hid_out);
 // S3: next level from h->match
 Status contract_level(snnmap_hgraph* h);
+// after a contraction of `src`: candidates of src carried to src + 1
+Status aff_carry(snnmap_hgraph* h, int32_t src);
+void aff_carry_free(snnmap_hgraph* h);
 // materializes levels[dst] from resident levels[src] through map (V(src) ids)
 Status build_coarse(snnmap_hgraph* h, int32_t src, const int32_t* map, const int64_t* d_V2,
                     int32_t dst);

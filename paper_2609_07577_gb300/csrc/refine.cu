@@ -51,6 +51,7 @@ enum : int {
 };
 
 constexpr int REPLAY_WARP_MAX = 32;
+constexpr int PSTAR_MAX = 16;   // partitions of P* the column update takes
 
 struct PinCounts {
     int32_t* p;
@@ -688,8 +689,10 @@ __global__ void k_level_max(Level L, int32_t* vmax)
 // among them (prel), with the round-start state
 __global__ void k_inc_parts(int32_t M, Moves mv, const int64_t* __restrict__ scal, PState ps,
                             const int32_t* __restrict__ vmax, int32_t omega, int32_t delta,
-                            int32_t phi, uint8_t* pchg, uint8_t* prel)
+                            int32_t phi, uint8_t* pchg, uint8_t* prel,
+                            const int32_t* __restrict__ pstar_n)
 {
+    if (*pstar_n <= PSTAR_MAX) return;   // the column update below handles this round
     int64_t istar = scal[RS_BEST] > 0 ? scal[RS_ISTAR] : -1;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= istar && i < M;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -711,8 +714,9 @@ __global__ void k_inc_parts(int32_t M, Moves mv, const int64_t* __restrict__ sca
 __global__ void __launch_bounds__(256)
     k_inc_hedges(Level L, PinCounts pc, const int32_t* __restrict__ moveidx, Moves mv,
                  const int64_t* __restrict__ scal, const uint8_t* __restrict__ prel, uint32_t* buf,
-                 int32_t* dirty)
+                 int32_t* dirty, const int32_t* __restrict__ pstar_n)
 {
+    if (*pstar_n <= PSTAR_MAX) return;
     int64_t istar = scal[RS_BEST] > 0 ? scal[RS_ISTAR] : -1;
     if (istar < 0) return;
     int lane = threadIdx.x & 31;
@@ -773,11 +777,208 @@ __global__ void __launch_bounds__(256)
 
 // (c)
 __global__ void k_inc_targets(int32_t V, const int32_t* __restrict__ pto,
-                              const uint8_t* __restrict__ pchg, int32_t* dirty)
+                              const uint8_t* __restrict__ pchg, int32_t* dirty,
+                              const int32_t* __restrict__ pstar_n)
 {
+    if (*pstar_n <= PSTAR_MAX) return;
     for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < V;
          n += (int64_t)gridDim.x * blockDim.x)
         if (pto[n] >= 0 && pchg[pto[n]]) dirty[n] = 1;
+}
+
+
+// ---------------------------------------------------------------------------
+// Proposals after a short enacted prefix (at most PSTAR_MAX partitions
+// touched). Moves change the state of their source and target partitions
+// only (the set P*), and in every hyperedge only the counts of those
+// partitions. For a vertex n that did not move, an option q outside P*
+// therefore keeps conn(n, q), ov(n, q) and its feasibility, and its gain
+// shifts by the change of save(n) alone; the previous best option outside
+// P* stays the best outside P*. The options inside P* are recomputed from
+// their columns conn(n, p), ov(n, p), summed over the hyperedges that hold
+// a pin of p (found through p's members' incidence lists). n is evaluated
+// in full (flagged for the next round's histogram) only if it moved, if its
+// previous proposal targeted P*, or, when only positive gains are proposed,
+// if it had no proposal and its save grew (its best option outside P* is
+// then unknown). The other vertices get their exact proposal here.
+
+struct PStar {
+    int32_t* pslot = nullptr;   // [K] slot of a partition of P*; -1 none
+    int32_t* slots = nullptr;   // [PSTAR_MAX] partition of each slot
+    int32_t* cnt = nullptr;     // [0] distinct partitions of P*, [1] marked hyperedges,
+                                // [2] value cnt[0] restarts from (> PSTAR_MAX: path off)
+    uint32_t* hmask = nullptr;  // [E] slots whose partition has a pin in the hyperedge
+    int32_t* hl = nullptr;      // [E] hyperedges with a nonzero mask
+    int64_t* colc = nullptr;    // [PSTAR_MAX * V] conn(n, slot)
+    int32_t* colo = nullptr;    // [PSTAR_MAX * V] ov(n, slot)
+    uint32_t* vt = nullptr;     // [V] slots adjacent to n (some incident hyperedge has a pin there)
+    int64_t* save0 = nullptr;   // [V] save at round start
+};
+
+__device__ __forceinline__ bool pstar_on(const int64_t* scal, const int32_t* cnt)
+{
+    return scal[RS_BEST] > 0 && cnt[0] <= PSTAR_MAX;
+}
+
+// P* from the enacted moves; the moved vertices are flagged for a full
+// evaluation
+__global__ void k_ps_slots(int32_t M, Moves mv, const int64_t* __restrict__ scal, PStar ps,
+                           int32_t* dirty)
+{
+    int64_t istar = scal[RS_BEST] > 0 ? scal[RS_ISTAR] : -1;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= istar && i < M;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        dirty[mv.n[i]] = 1;
+        int32_t pp[2] = {mv.from[i], mv.to[i]};
+        for (int u = 0; u < 2; u++) {
+            int32_t p = pp[u];
+            if (atomicCAS(&ps.pslot[p], -1, -2) != -1) continue;
+            int32_t sl = atomicAdd(&ps.cnt[0], 1);
+            if (sl < PSTAR_MAX) {
+                ps.slots[sl] = p;
+                ps.pslot[p] = sl;
+            }
+        }
+    }
+}
+
+// every hyperedge incident to a member of a P* partition gets that slot's
+// bit (warp over 32 consecutive vertices, then over each member's
+// incidences)
+__global__ void __launch_bounds__(256)
+    k_ps_mark(Level L, const int32_t* __restrict__ rho, const int64_t* __restrict__ scal, PStar ps)
+{
+    if (!pstar_on(scal, ps.cnt)) return;
+    int lane = threadIdx.x & 31;
+    int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = gw * 32; base < L.V; base += nw * 32) {
+        int64_t n = base + lane;
+        int32_t sl = n < L.V ? ps.pslot[rho[n]] : -1;
+        unsigned mem = __ballot_sync(FULL, sl >= 0);
+        while (mem) {
+            int src = __ffs(mem) - 1;
+            mem &= mem - 1;
+            int32_t m = (int32_t)__shfl_sync(FULL, (int32_t)n, src);
+            uint32_t bit = 1u << __shfl_sync(FULL, sl, src);
+            for (int64_t i = L.voff[m] + lane; i < L.voff[m + 1]; i += 32) {
+                int32_t a = (int32_t)((uint32_t)L.vinc[i] & ~SRC_BIT);
+                uint32_t old = atomicOr(&ps.hmask[a], bit);
+                if (old == 0) ps.hl[atomicAdd(&ps.cnt[1], 1)] = a;
+            }
+        }
+    }
+}
+
+// columns: for each marked hyperedge and each of its slots p, every pin n
+// outside p adds omega to conn(n, p) and, as a destination of a hyperedge
+// inbound to p, k to ov(n, p) (counts after the moves); masks are cleared
+__global__ void __launch_bounds__(256)
+    k_ps_cols(Level L, PinCounts pc, const int32_t* __restrict__ rho,
+              const int64_t* __restrict__ scal, PStar ps)
+{
+    if (!pstar_on(scal, ps.cnt)) return;
+    int lane = threadIdx.x & 31;
+    int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int32_t nh = ps.cnt[1];
+    int64_t V = L.V;
+    for (int64_t idx = gw; idx < nh; idx += nw) {
+        int32_t a = ps.hl[idx];
+        uint32_t mask = ps.hmask[a];
+        int64_t b = L.hoff[a], e = L.hoff[a + 1];
+        int32_t lam = pc.lam[a];
+        int64_t w = L.hw[a];
+        int32_t k = L.hk[a];
+        int sd = L.hsd[a];
+        while (mask) {
+            int sl = __ffs(mask) - 1;
+            mask &= mask - 1;
+            int32_t p = ps.slots[sl];
+            int32_t c, d;
+            lookup_count(pc, b, lam, p, c, d);
+            int64_t* cc = ps.colc + (int64_t)sl * V;
+            int32_t* co = ps.colo + (int64_t)sl * V;
+            for (int64_t j = b + lane; j < e; j += 32) {
+                int32_t n = L.hpins[j];
+                if (rho[n] == p) continue;
+                atomicAdd((unsigned long long*)&cc[n], (unsigned long long)w);
+                if (d > 0 && (j != b || sd)) atomicAdd(&co[n], k);
+                atomicOr(&ps.vt[n], 1u << sl);
+            }
+        }
+        __syncwarp();
+        if (lane == 0) ps.hmask[a] = 0;
+    }
+}
+
+// each vertex's proposal for the next round (or its flag for a full
+// evaluation); columns read are cleared
+__global__ void k_ps_combine(Level L, const int32_t* __restrict__ rho,
+                             const int64_t* __restrict__ scal, PStar ps, PState st,
+                             const int64_t* __restrict__ savev, const int64_t* __restrict__ Wv,
+                             int32_t omega, int32_t delta, int32_t phi, int nonpos, int32_t* pto,
+                             int64_t* pgain, int32_t* dirty)
+{
+    if (!pstar_on(scal, ps.cnt)) return;
+    int32_t ns = ps.cnt[0];
+    int64_t V = L.V;
+    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < V;
+         n += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t adj = ps.vt[n];
+        if (!dirty[n]) {
+            int64_t ds = savev[n] - ps.save0[n];
+            int32_t q = pto[n];
+            if ((q >= 0 && ps.pslot[q] >= 0) || (!nonpos && q < 0 && ds > 0)) {
+                dirty[n] = 1;
+            } else {
+                int64_t bs = q >= 0 ? pgain[n] + ds : 0;
+                int32_t bk = q;
+                if (adj) {
+                    int64_t sw = savev[n] - Wv[n];
+                    for (int sl = 0; sl < ns; sl++) {
+                        if (!((adj >> sl) & 1u)) continue;
+                        int32_t p = ps.slots[sl];
+                        int64_t c = ps.colc[(int64_t)sl * V + n];
+                        int64_t o = ps.colo[(int64_t)sl * V + n];
+                        bool feas = st.size[p] + L.vsize[n] <= omega &&
+                                    st.inpins[p] + L.vinpins[n] <= phi &&
+                                    st.pincnt[p] + L.vincnt[n] - o <= delta;
+                        if (feas && better(sw + c, p, bs, bk)) {
+                            bs = sw + c;
+                            bk = p;
+                        }
+                    }
+                }
+                bool prop = bk >= 0 && (bs > 0 || nonpos);
+                pto[n] = prop ? bk : -1;
+                pgain[n] = prop ? bs : 0;
+            }
+        }
+        if (adj) {
+            for (int sl = 0; sl < ns; sl++) {
+                if (!((adj >> sl) & 1u)) continue;
+                ps.colc[(int64_t)sl * V + n] = 0;
+                ps.colo[(int64_t)sl * V + n] = 0;
+            }
+            ps.vt[n] = 0;
+        }
+    }
+}
+
+// slot map and counters back to empty
+__global__ void k_ps_reset(int32_t M, Moves mv, const int64_t* __restrict__ scal, PStar ps)
+{
+    int64_t istar = scal[RS_BEST] > 0 ? scal[RS_ISTAR] : -1;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= istar && i < M;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        ps.pslot[mv.from[i]] = -1;
+        ps.pslot[mv.to[i]] = -1;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ps.cnt[0] = ps.cnt[2];
+        ps.cnt[1] = 0;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1141,8 +1342,8 @@ static Status gains(snnmap_hgraph* h, Level& L, const PinCounts& pc, const int32
     pol.pto = pto;
     pol.pgain = pgain;
     int64_t* cnt;
-    SNN_TRY(h->scratch.alloc(&cnt, HT_NTIER));
-    return run_histogram(pol, h->scratch, h->stream, cnt, h->h_scal + 12, h->d_scal);
+    SNN_TRY(h->scratch.alloc(&cnt, HT_NCNT));
+    return run_histogram(pol, h->scratch, h->stream, cnt, h->h_scal + 12, h->d_scal, h->tiers);
 }
 
 // rows of the vertices flagged fresh, from the round's pin counts
@@ -1160,8 +1361,8 @@ static Status dense_fresh(snnmap_hgraph* h, Level& L, const PinCounts& pc)
     pol.O = D.O;
     pol.Kp = D.Kp;
     int64_t* cnt;
-    SNN_TRY(h->scratch.alloc(&cnt, HT_NTIER));
-    return run_histogram(pol, h->scratch, h->stream, cnt, h->h_scal + 12, h->d_scal);
+    SNN_TRY(h->scratch.alloc(&cnt, HT_NCNT));
+    return run_histogram(pol, h->scratch, h->stream, cnt, h->h_scal + 12, h->d_scal, h->tiers);
 }
 
 int64_t dense_row_budget(const snnmap_hgraph* h)
@@ -1428,6 +1629,7 @@ struct IncState {
     int32_t* hlist = nullptr;    // bucket lists filtered to dirty hyperedges
     int32_t* hmeta = nullptr;    // their bucket starts and counts (2 * SEG_NB)
     bool ready = false;          // set once the first round computed them
+    PStar pst;                   // column update of proposals after short prefixes
 };
 
 // One round; *applied = moves enacted, *gain = Conn removed, *cost = Conn at
@@ -1614,13 +1816,19 @@ static Status refine_round(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* 
         SNN_CUDA(cudaMemsetAsync(inc.dirty, 0, (size_t)(V > 0 ? V : 1) * 4, s));
         SNN_CUDA(cudaMemsetAsync(inc.pchg, 0, (size_t)(K > 0 ? K : 1), s));
         SNN_CUDA(cudaMemsetAsync(inc.prel, 0, (size_t)(K > 0 ? K : 1), s));
+        // P* of the enacted prefix; when it is short the column update after
+        // the pin counts below decides the next round's proposals, otherwise
+        // the flags of the three rules below do
+        SNN_L k_ps_slots<<<gm, 256, 0, s>>>(M, mv, h->d_scal, inc.pst, inc.dirty);
         SNN_L k_inc_parts<<<gm, 256, 0, s>>>(M, mv, h->d_scal, ps, inc.vmax, prm.omega, prm.delta,
-                                             prm.phi, inc.pchg, inc.prel);
+                                             prm.phi, inc.pchg, inc.prel, inc.pst.cnt);
         if (L.E > 0)
             SNN_L k_inc_hedges<<<grid_for((int64_t)L.E * 32, 256), 256, 0, s>>>(
-                L, pc, moveidx, mv, h->d_scal, inc.prel, mvbuf, inc.dirty);
-        SNN_L k_inc_targets<<<gv, 256, 0, s>>>(V, pto, inc.pchg, inc.dirty);
+                L, pc, moveidx, mv, h->d_scal, inc.prel, mvbuf, inc.dirty, inc.pst.cnt);
+        SNN_L k_inc_targets<<<gv, 256, 0, s>>>(V, pto, inc.pchg, inc.dirty, inc.pst.cnt);
         SNN_CUDA(cudaGetLastError());
+        if (inc.pst.save0 && V > 0)
+            SNN_CUDA(cudaMemcpyAsync(inc.pst.save0, savev, (size_t)V * 8, cudaMemcpyDeviceToDevice, s));
     }
     // carried pin counts: take out the hyperedges the prefix touches (old
     // counts, old rho), move, count them again, add them back
@@ -1650,6 +1858,18 @@ static Status refine_round(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* 
         SNN_TRY(seg_run(job, db, L.E, ar, s));
         SNN_L k_cost_slots<<<1, 256, 0, s>>>(slots, inc.costv);
         SNN_L k_pc_contrib<<<ghe, 256, 0, s>>>(L, pc, inc.hdirty, rho, ps, savev, inc.costv, 1);
+        SNN_CUDA(cudaGetLastError());
+    }
+    if (!dense) {
+        prof.reset(new ProfScope(h, PS_GAINS));
+        if (inc.pst.colc && V > 0) {
+            SNN_L k_ps_mark<<<grid_for(V, 256), 256, 0, s>>>(L, rho, h->d_scal, inc.pst);
+            SNN_L k_ps_cols<<<152 * 8, 256, 0, s>>>(L, pc, rho, h->d_scal, inc.pst);
+            SNN_L k_ps_combine<<<gv, 256, 0, s>>>(L, rho, h->d_scal, inc.pst, ps, savev, Wv, prm.omega,
+                                                  prm.delta, prm.phi, prm.refine_nonpositive, pto,
+                                                  pgain, inc.dirty);
+        }
+        SNN_L k_ps_reset<<<gm, 256, 0, s>>>(M, mv, h->d_scal, inc.pst);
         SNN_CUDA(cudaGetLastError());
     }
     prof.reset();
@@ -1789,6 +2009,44 @@ Status refine_level(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* rho, in
     SNN_CUDA(cudaMallocAsync(&inc.hdirty, ne * 4, s));
     SNN_CUDA(cudaMallocAsync(&inc.hlist, ne * 4, s));
     SNN_CUDA(cudaMallocAsync(&inc.hmeta, 2 * SEG_NB * 4, s));
+    PStar& pst = inc.pst;
+    SNN_CUDA(cudaMallocAsync(&pst.pslot, nk * 4, s));
+    SNN_CUDA(cudaMallocAsync(&pst.slots, PSTAR_MAX * 4, s));
+    SNN_CUDA(cudaMallocAsync(&pst.cnt, 4 * 4, s));
+    if (!dense_level) {
+        // the column buffers are optional: without them every round takes
+        // the flag rules
+        size_t cols = (size_t)PSTAR_MAX * nv;
+        bool ok = cudaMallocAsync(&pst.hmask, ne * 4, s) == cudaSuccess &&
+                  cudaMallocAsync(&pst.hl, ne * 4, s) == cudaSuccess &&
+                  cudaMallocAsync(&pst.colc, cols * 8, s) == cudaSuccess &&
+                  cudaMallocAsync(&pst.colo, cols * 4, s) == cudaSuccess &&
+                  cudaMallocAsync(&pst.vt, nv * 4, s) == cudaSuccess &&
+                  cudaMallocAsync(&pst.save0, nv * 8, s) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            for (void* p : {(void*)pst.hmask, (void*)pst.hl, (void*)pst.colc, (void*)pst.colo,
+                            (void*)pst.vt, (void*)pst.save0})
+                if (p) cudaFreeAsync(p, s);
+            pst.hmask = nullptr;
+            pst.hl = nullptr;
+            pst.colc = nullptr;
+            pst.colo = nullptr;
+            pst.vt = nullptr;
+            pst.save0 = nullptr;
+        } else {
+            SNN_CUDA(cudaMemsetAsync(pst.hmask, 0, ne * 4, s));
+            SNN_CUDA(cudaMemsetAsync(pst.colc, 0, cols * 8, s));
+            SNN_CUDA(cudaMemsetAsync(pst.colo, 0, cols * 4, s));
+            SNN_CUDA(cudaMemsetAsync(pst.vt, 0, nv * 4, s));
+        }
+    }
+    {
+        int32_t base = pst.colc ? 0 : (1 << 30);
+        int32_t hc[4] = {base, 0, base, 0};
+        SNN_CUDA(cudaMemcpyAsync(pst.cnt, hc, sizeof(hc), cudaMemcpyHostToDevice, s));
+        SNN_TRY(fill_i32(pst.pslot, -1, nk, s));
+    }
     SNN_CUDA(cudaMemsetAsync(inc.vmax, 0, 3 * 4, s));
     if (L.V > 0) SNN_L k_level_max<<<grid_for(L.V, 256), 256, 0, s>>>(L, inc.vmax);
     SNN_CUDA(cudaGetLastError());
@@ -1819,8 +2077,10 @@ Status refine_level(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* rho, in
                     (void*)inc.pc.dcnt, (void*)inc.pc.lam, (void*)inc.ps.size,
                     (void*)inc.ps.inpins, (void*)inc.ps.pincnt, (void*)inc.costv,
                     (void*)inc.savev, (void*)inc.Wv, (void*)inc.hdirty, (void*)inc.hlist,
-                    (void*)inc.hmeta})
-        cudaFreeAsync(p, s);
+                    (void*)inc.hmeta, (void*)pst.pslot, (void*)pst.slots, (void*)pst.cnt,
+                    (void*)pst.hmask, (void*)pst.hl, (void*)pst.colc, (void*)pst.colo,
+                    (void*)pst.vt, (void*)pst.save0})
+        if (p) cudaFreeAsync(p, s);
     if (!st.ok()) return st;
     if (!have_cost) {
         SNN_TRY(level_cost(h, level, K, rho, &c));

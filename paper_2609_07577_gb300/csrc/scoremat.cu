@@ -227,8 +227,8 @@ static Status mat_rows(snnmap_hgraph* h, const Level& L, const int32_t* fresh)
     pol.OVm = M.OV;
     pol.Vs = M.Vs;
     int64_t* cnt;
-    SNN_TRY(h->scratch.alloc(&cnt, HT_NTIER));
-    return run_histogram(pol, h->scratch, h->stream, cnt, h->h_scal + 12, h->d_scal);
+    SNN_TRY(h->scratch.alloc(&cnt, HT_NCNT));
+    return run_histogram(pol, h->scratch, h->stream, cnt, h->h_scal + 12, h->d_scal, h->tiers);
 }
 
 void mat_close(snnmap_hgraph* h)
@@ -246,7 +246,7 @@ void mat_close(snnmap_hgraph* h)
 // it stays (V shrinks while pair_terms barely does).
 static bool mat_fits(const snnmap_hgraph* h, int32_t level)
 {
-    if (h->wide || h->wsum > INT32_MAX) return false;
+    if (h->wide || h->wzero || h->wsum > INT32_MAX) return false;
     int64_t Vs = ((int64_t)h->levels[level].V + 3) & ~(int64_t)3;
     return 16 * Vs * Vs <= dense_row_budget(h) &&
            (double)Vs * (double)Vs <= 5.0 * (double)h->extra[level].pair_terms;
@@ -292,6 +292,9 @@ Status mat_affinity(snnmap_hgraph* h, int32_t level, bool* done)
     }
     h->extra[level].n_block = 0;
     h->extra[level].n_global = 0;
+    h->extra[level].carried = 2;
+    h->extra[level].n_full = 0;
+    h->extra[level].hist_work = 0;
     *done = true;
     return Status{};
 }

@@ -59,7 +59,11 @@ int64_t input_bytes(int64_t V, int64_t E, int64_t P)
 int64_t footprint(int64_t V, int64_t E, int64_t P, bool on_host)
 {
     int64_t L0 = level_bytes(V, E, P);
-    int64_t f = (kFootLevels + kFootScratch) * L0 + 20 * V + kFootFixed + job_row_budget(L0);
+    // 20 B per vertex of candidate arrays, 17 B of carried candidates, and the
+    // refinement's column update of short prefixes (16 slots of 12 B, 16 B of
+    // flags and saves per vertex, 8 B per hyperedge)
+    int64_t f = (kFootLevels + kFootScratch) * L0 + (20 + 17 + 208) * V + 8 * E + kFootFixed +
+                job_row_budget(L0);
     if (on_host) f += input_bytes(V, E, P);
     return f;
 }

@@ -44,8 +44,8 @@ def check_snn(hg) -> None:
         raise ValueError("off[-1] must equal len(pins) and len(w) the number of axons")
     if pins.size and (pins.min() < 0 or pins.max() >= hg.V):
         raise ValueError("a pin outside [0, V)")
-    if w.size and w.min() < 1:
-        raise ValueError("axon weights must be >= 1")
+    if w.size and w.min() < 0:
+        raise ValueError("axon weights (spike frequencies) must be >= 0")
     if hg.omega < 1 or hg.delta < 0 or hg.phi < 0:
         raise ValueError("omega must be >= 1, delta and phi >= 0")
 

@@ -15,12 +15,16 @@ def assert_level_equal(ga, oa, tag=""):
     assert cg == co, f"{tag} hyperedges"
 
 
-def lockstep(hg, max_levels=None, check_levels=True):
-    """Runs coarsening on both sides; returns the number of levels compared."""
+def lockstep(hg, max_levels=None, check_levels=True, setup=None, logs=None):
+    """Runs coarsening on both sides; returns the number of levels compared.
+    setup(G) runs on the CUDA handle first; logs (a list) receives its level
+    logs."""
     from paper_2609_07577_gb300 import HGraph
     prm = oracle.params_of(hg)
     L = oracle.Level.from_hypergraph(hg, prm)
     G = HGraph.from_hypergraph(hg)
+    if setup is not None:
+        setup(G)
     try:
         lev = 0
         while True:
@@ -46,6 +50,8 @@ def lockstep(hg, max_levels=None, check_levels=True):
                 if check_levels:
                     assert_level_equal(G.level_arrays(lev), L.arrays(), f"level {lev}")
                 break
+        if logs is not None:
+            logs.extend(G.level_logs())
         return lev
     finally:
         G.close()

@@ -72,5 +72,7 @@ def test_cli_map_with_placement(tmp_path):
         np.testing.assert_array_equal(z["rho"], rho_o)
         assert int(z["cost"]) == cost_o
         gamma, (w, h) = z["gamma"], z["lattice"]
-        assert len(gamma) == st_o["n_parts"] and len(set(gamma.tolist())) == len(gamma)
+        # one G_P node (and core) per non-empty partition, in id order
+        np.testing.assert_array_equal(z["parts"], np.unique(rho_o))
+        assert len(gamma) == st_o["nonempty_parts"] and len(set(gamma.tolist())) == len(gamma)
         assert gamma.min() >= 0 and gamma.max() < w * h and int(z["trd"]) > 0

@@ -40,11 +40,24 @@ def test_malformed_input_refused(bad):
     elif bad == "off":
         hg.off[1] = 7
     elif bad == "w":
-        hg.w[0] = 0
+        hg.w[0] = -1
     else:
         hg.omega = 0
     with pytest.raises(ValueError):
         check_snn(hg)
+
+
+def test_silent_axon_accepted():
+    # a spike frequency of 0 is valid input for the library, so for the file too
+    hg = from_axons(4, [(0, [1, 2]), (3, [0])], [0, 2], 2, 2, 4)
+    check_snn(hg)
+    assert hg.w.tolist() == [0, 2]
+
+
+def test_cli_rejects_no_starts():
+    from paper_2609_07577_gb300.__main__ import parse
+    with pytest.raises(SystemExit):
+        parse(["map", "in.npz", "out.npz", "--place", "--starts", "0"])
 
 
 def test_cli_arguments():

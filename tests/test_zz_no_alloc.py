@@ -1,5 +1,6 @@
 """The allocation-free connectivity call (snnmap_connectivity_noalloc) gives
-the same Conn as the handle-based snnmap_connectivity.
+the oracle's Conn (Eq. connectivity), as the handle-based
+snnmap_connectivity does.
 
 Some callers cannot allocate device memory at all: their device memory is
 reserved up front by another allocator, or they run in a loop where a
@@ -16,6 +17,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 import snngen
 
 pytestmark = pytest.mark.gpu
@@ -52,9 +54,12 @@ def test_noalloc_matches_connectivity(lib):
             for K in (97, 97, 5, hg.V):
                 rho = torch.from_numpy(rng.integers(0, K, size=hg.V).astype(np.int32)).cuda()
                 ref = P.snnmap_connectivity(g.handle, K, rho)
+                # Eq. connectivity from the oracle on the same partition
+                orc = oracle.Level.from_hypergraph(hg, oracle.params_of(hg)).conn(rho.cpu().numpy())
                 first = _noalloc(P, hg, off, pins, w, rho, K, out)
                 second = _noalloc(P, hg, off, pins, w, rho, K, out)
-                assert first == ref and second == ref, (name, K, first, second, ref)
+                assert ref == orc, (name, K, ref, orc)
+                assert first == orc and second == orc, (name, K, first, second, orc)
         finally:
             g.close()
 
