@@ -530,6 +530,18 @@ int snnmap_place_trd(int32_t n_nodes, int32_t n_hedges, const int64_t* d_offsets
                      const int32_t* d_pins, const int64_t* d_eta, int32_t width, int32_t height,
                      int32_t n_starts, const int32_t* d_gamma, void* stream, int64_t* h_trd_out);
 
+/* The choice among multi-start results (Sec. 4.2, "Placement Refinement"):
+ * the start whose placement has the smallest total residual distance
+ * (snnmap_place_trd), the lowest start on ties. Arguments as in
+ * snnmap_place_trd; outputs on the host: *best_out the start, *trd_out (may
+ * be NULL) its total residual distance, h_trd_out (may be NULL) int64
+ * [n_starts] every start's. Same errors, and SNNMAP_ERR_INVALID for a NULL
+ * best_out. */
+int snnmap_place_best(int32_t n_nodes, int32_t n_hedges, const int64_t* d_offsets,
+                      const int32_t* d_pins, const int64_t* d_eta, int32_t width, int32_t height,
+                      int32_t n_starts, const int32_t* d_gamma, void* stream, int32_t* best_out,
+                      int64_t* trd_out, int64_t* h_trd_out);
+
 /*
  * Initial placement of G_P (Sec. 4.2, "Initial Placement") for n_starts
  * starts at once. Each start's node sequence begins as its given order

@@ -122,6 +122,8 @@ _SIGS = {
     "snnmap_place_refine": (C.c_int, [_i32, _i32, _vp, _vp, _vp, _i32, _i32, _i32, _vp, _i32,
                                       _vp, _vp, _vp, _i32]),
     "snnmap_place_trd": (C.c_int, [_i32, _i32, _vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp, _vp]),
+    "snnmap_place_best": (C.c_int, [_i32, _i32, _vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp,
+                                    C.POINTER(_i32), C.POINTER(_i64), _vp]),
     "snnmap_place_initial": (C.c_int, [_i32, _i32, _vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp,
                                        _vp, _vp]),
     "snnmap_hilbert_order": (C.c_int, [_i32, _i32, _vp, _vp]),
@@ -414,6 +416,19 @@ def snnmap_place_trd(n_nodes, n_hedges, d_offsets, d_pins, d_eta, width, height,
                                  _p(d_eta), int(width), int(height), S, _p(d_gamma),
                                  _stream(stream), out))
     return [out[i] for i in range(S)]
+
+
+def snnmap_place_best(n_nodes, n_hedges, d_offsets, d_pins, d_eta, width, height, n_starts,
+                      d_gamma, stream=None):
+    """The start of smallest total residual distance (lowest on ties):
+    (start, its distance, every start's distance as a list)."""
+    S = int(n_starts)
+    out = (C.c_int64 * max(S, 1))()
+    best, trd = C.c_int32(), C.c_int64()
+    check(lib().snnmap_place_best(int(n_nodes), int(n_hedges), _p(d_offsets), _p(d_pins),
+                                  _p(d_eta), int(width), int(height), S, _p(d_gamma),
+                                  _stream(stream), C.byref(best), C.byref(trd), out))
+    return best.value, trd.value, [out[i] for i in range(S)]
 
 
 def snnmap_place_initial(n_nodes, n_hedges, d_offsets, d_pins, d_eta, width, height, n_starts,

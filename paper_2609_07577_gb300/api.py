@@ -269,8 +269,8 @@ def place(n_nodes, off, pins, eta, width=None, height=None, n_starts=64, seed=0,
     trds0 = N.snnmap_place_trd(K, E, d_off, d_pins, d_eta, width, height, S, gamma, stream)
     rounds, logs = N.snnmap_place_refine(K, E, d_off, d_pins, d_eta, width, height, S, gamma,
                                          max_rounds, stream, log_cap=max_rounds)
-    trds = N.snnmap_place_trd(K, E, d_off, d_pins, d_eta, width, height, S, gamma, stream)
-    best = min(range(S), key=lambda s: (trds[s], s))
+    best, trd, trds = N.snnmap_place_best(K, E, d_off, d_pins, d_eta, width, height, S, gamma,
+                                          stream)
     g = gamma.view(S, K)[best].cpu().numpy() if K else np.zeros(0, np.int32)
-    return {"gamma": g, "trd": trds[best], "start": best, "trds": trds, "trds_initial": trds0,
+    return {"gamma": g, "trd": trd, "start": best, "trds": trds, "trds_initial": trds0,
             "rounds": rounds, "logs": logs, "width": width, "height": height}

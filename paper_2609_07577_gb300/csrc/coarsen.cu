@@ -87,18 +87,36 @@ struct AffPol {
         g.k = (uint32_t)L.hk[a];
         return g;
     }
-    template <class Tb>
-    __device__ bool elem(int32_t n, const Seg<S>& g, int32_t off, const Tb& t, Acc&) const
+    // one element: neighbour m (-1: nothing to add), weight, shared count
+    struct Item {
+        int32_t m;
+        S w;
+        uint32_t o;
+    };
+    static __device__ Item none() { return Item{-1, 0, 0u}; }
+    __device__ Item load(int32_t n, const Seg<S>& g, int32_t off) const
     {
-        int32_t m = L.hpins[g.b + off];
-        if (m == n) return true;
+        Item it;
+        it.m = L.hpins[g.b + off];
+        it.w = g.w;
+        int md = off != 0 || g.sd;   // pin 0 is the source
+        it.o = (g.nd && md) ? g.k : 0u;
         // a neighbour whose size or inbound pins alone break Omega or Phi
         // with n can never be the candidate: leave it out of the table
-        if (prefilter && ((int64_t)L.vsize[n] + L.vsize[m] > omega ||
-                          (int64_t)L.vinpins[n] + L.vinpins[m] > phi))
-            return true;
-        int md = off != 0 || g.sd;   // pin 0 is the source
-        return t.add(m, g.w, (g.nd && md) ? g.k : 0u);
+        if (it.m == n || (prefilter && ((int64_t)L.vsize[n] + L.vsize[it.m] > omega ||
+                                        (int64_t)L.vinpins[n] + L.vinpins[it.m] > phi)))
+            it.m = -1;
+        return it;
+    }
+    template <class Tb>
+    __device__ bool put(int32_t, const Item& it, const Tb& t, Acc&) const
+    {
+        return it.m < 0 || t.add(it.m, it.w, it.o);
+    }
+    template <class Tb>
+    __device__ bool elem(int32_t n, const Seg<S>& g, int32_t off, const Tb& t, Acc& acc) const
+    {
+        return put(n, load(n, g, off), t, acc);
     }
     __device__ void consider(int32_t n, int32_t m, int64_t s, uint32_t o, const Acc&, int64_t& bs,
                              int32_t& bk, uint32_t& bo) const
@@ -461,6 +479,57 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// MERGED vertices whose best valid new super-node is not w = cand (full
+// flag 2): w's validity decides between keeping that result (0) and a full
+// histogram (1). ov(x, w) sums k over the hyperedges in which both are
+// destinations (w found by binary search among the sorted destinations).
+__global__ void __launch_bounds__(256)
+    k_ac_check(Level L, AffCarry ac, int32_t omega, int32_t delta, int32_t phi)
+{
+    int lane = threadIdx.x & 31;
+    int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = gw * 32; base < L.V; base += nw * 32) {
+        int64_t n = base + lane;
+        bool f = n < L.V && ac.full[n] == 2;
+        unsigned mem = __ballot_sync(FULL, f);
+        while (mem) {
+            int src = __ffs(mem) - 1;
+            mem &= mem - 1;
+            int32_t x = (int32_t)__shfl_sync(FULL, (int32_t)n, src);
+            int32_t w = ac.cand[x];
+            int64_t ov = 0;
+            for (int64_t i = L.voff[x] + lane; i < L.voff[x + 1]; i += 32) {
+                uint32_t inc = (uint32_t)L.vinc[i];
+                int32_t a = (int32_t)(inc & ~SRC_BIT);
+                int sd = L.hsd[a];
+                if ((inc & SRC_BIT) && !sd) continue;   // x is not a destination of a
+                int64_t b = L.hoff[a], e = L.hoff[a + 1];
+                bool wd;
+                if (L.hpins[b] == w) {
+                    wd = sd != 0;
+                } else {
+                    int64_t lo = b + 1, hi = e;
+                    while (lo < hi) {
+                        int64_t mid = (lo + hi) >> 1;
+                        if (L.hpins[mid] < w) lo = mid + 1;
+                        else hi = mid;
+                    }
+                    wd = lo < e && L.hpins[lo] == w;
+                }
+                if (wd) ov += L.hk[a];
+            }
+            ov = warp_sum(ov);
+            if (lane == 0) {
+                bool valid = (int64_t)L.vsize[x] + L.vsize[w] <= omega &&
+                             (int64_t)L.vinpins[x] + L.vinpins[w] <= phi &&
+                             (int64_t)L.vincnt[x] + L.vincnt[w] - ov <= delta;
+                ac.full[x] = valid ? 0 : 1;
+            }
+        }
+    }
+}
+
 // Histogram of each carried vertex over the new super-nodes of its
 // hyperedges, combined with its carried candidate.
 template <typename S_>
@@ -507,15 +576,33 @@ struct AffNewPol {
         g.k = (uint32_t)L.hk[a];
         return g;
     }
-    template <class Tb>
-    __device__ bool elem(int32_t n, const Seg<S>& g, int32_t off, const Tb& t, Acc&) const
+    struct Item {
+        int32_t m;
+        S w;
+        uint32_t o;
+    };
+    static __device__ Item none() { return Item{-1, 0, 0u}; }
+    __device__ Item load(int32_t n, const Seg<S>& g, int32_t off) const
     {
         uint32_t e = lpins[g.b + off];
-        int32_t m = (int32_t)(e & ~NOT_DEST);
-        if (prefilter && ((int64_t)L.vsize[n] + L.vsize[m] > omega ||
-                          (int64_t)L.vinpins[n] + L.vinpins[m] > phi))
-            return true;
-        return t.add(m, g.w, (g.nd && !(e & NOT_DEST)) ? g.k : 0u);
+        Item it;
+        it.m = (int32_t)(e & ~NOT_DEST);
+        it.w = g.w;
+        it.o = (g.nd && !(e & NOT_DEST)) ? g.k : 0u;
+        if (prefilter && ((int64_t)L.vsize[n] + L.vsize[it.m] > omega ||
+                          (int64_t)L.vinpins[n] + L.vinpins[it.m] > phi))
+            it.m = -1;
+        return it;
+    }
+    template <class Tb>
+    __device__ bool put(int32_t, const Item& it, const Tb& t, Acc&) const
+    {
+        return it.m < 0 || t.add(it.m, it.w, it.o);
+    }
+    template <class Tb>
+    __device__ bool elem(int32_t n, const Seg<S>& g, int32_t off, const Tb& t, Acc& acc) const
+    {
+        return put(n, load(n, g, off), t, acc);
     }
     __device__ void consider(int32_t n, int32_t m, int64_t s, uint32_t o, const Acc&, int64_t& bs,
                              int32_t& bk, uint32_t& bo) const
@@ -538,8 +625,11 @@ struct AffNewPol {
             bk = ac.cand[n];
             bo = (uint32_t)ac.ov[n];
         } else if (k == AK_MERGED && bk != ac.cand[n]) {
-            ac.full[n] = 1;
-            return;
+            // w = cand is not the best valid new super-node: either it is
+            // invalid (full histogram) or another one beats it (then that one
+            // is the candidate); k_ac_check decides by w's validity
+            ac.full[n] = bk < 0 ? 1 : 2;
+            if (bk < 0) return;
         }
         cand[n] = bk;
         cscore[n] = bk < 0 ? 0 : bs;
@@ -654,6 +744,9 @@ static Status affinity_carried(snnmap_hgraph* h, Level& L, bool* done)
         ng += hc[HT_TIER_SPLIT];
         wk += hc[HT_CNT_WORK];
     }
+    SNN_L k_ac_check<<<grid_for(L.V, 256), 256, 0, s>>>(L, C, h->prm.omega, h->prm.delta,
+                                                        h->prm.phi);
+    SNN_CUDA(cudaGetLastError());
     {
         AffPol<S> pol;
         pol.vmin = vmin;

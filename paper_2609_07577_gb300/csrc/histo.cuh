@@ -41,6 +41,7 @@
 #include "histo_tiers.cuh"
 
 #include <algorithm>
+#include <type_traits>
 
 namespace snn {
 
@@ -216,7 +217,12 @@ constexpr int64_t HT_CHUNK = 1024;      // incidences per split-tier work item
 enum : int { HT_TIER_WARP = 0, HT_TIER_BLOCK = 1, HT_TIER_BIG = 2, HT_TIER_SPLIT = 3, HT_NTIER = 4 };
 // counters of run_histogram: per-tier vertex counts, then the summed work and
 // the number of vertices given a histogram (not skipped)
-enum : int { HT_CNT_WORK = HT_NTIER, HT_CNT_VERTS = HT_NTIER + 1, HT_NCNT = HT_NTIER + 2 };
+// and the next list positions the block and big tiers hand out (dynamic
+// scheduling: a block takes the next vertex when it is done with one)
+enum : int {
+    HT_CNT_WORK = HT_NTIER, HT_CNT_VERTS = HT_NTIER + 1, HT_CNT_NEXT = HT_NTIER + 2,
+    HT_NCNT = HT_NTIER + 2 + HT_NTIER
+};
 
 template <typename S>
 __host__ __device__ constexpr int big_cap()
@@ -366,10 +372,34 @@ __global__ void __launch_bounds__(HT_WARPS * 32)
     }
 }
 
+// A policy may split elem into load (the element's global reads, giving an
+// Item) and put (the table update), declaring `struct Item`; the block tiers
+// then keep several elements' loads in flight per thread.
+template <class P, class = void>
+struct has_item : std::false_type {};
+template <class P>
+struct has_item<P, std::void_t<typename P::Item>> : std::true_type {};
+
+// the last index lo in [from, n) with spre[lo] <= v (spre non-decreasing,
+// spre[from] <= v): one probe while v stays in the same segment, a binary
+// search when it moved on
+__device__ __forceinline__ int32_t seg_find(const int32_t* spre, int32_t n, int32_t from, int32_t v)
+{
+    if (from + 1 >= n || spre[from + 1] > v) return from;
+    int32_t lo = from + 1, hi = n - 1;
+    while (lo < hi) {
+        int32_t mid = (lo + hi + 1) >> 1;
+        if (spre[mid] <= v) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 // Block-wide visit of incidences [vb, ve): tiles of blockDim incidences, one
 // per thread, segment lengths scanned across the block, then every thread
 // takes elements v = tid, tid + blockDim, ... of the tile's flattened range
-// and finds its segment by binary search in shared memory.
+// and finds its segment in shared memory (the elements of a thread are
+// increasing, so its search resumes where the previous one ended).
 template <typename S, class Pol, int T>
 __device__ bool block_visit(const Pol& pol, int32_t n, int64_t vb, int64_t ve, const Table<S>& t,
                             typename Pol::Acc& acc, Seg<S>* sseg, int32_t* spre, int32_t* swarp,
@@ -404,16 +434,31 @@ __device__ bool block_visit(const Pol& pol, int32_t n, int64_t vb, int64_t ve, c
         sseg[threadIdx.x] = sg;
         int32_t total = swarp[nw];
         __syncthreads();
-        for (int32_t v = threadIdx.x; v < total; v += T) {
-            int32_t lo = 0, hi = T - 1;
-            while (lo < hi) {
-                int32_t mid = (lo + hi + 1) >> 1;
-                if (spre[mid] <= v) lo = mid;
-                else hi = mid - 1;
+        int32_t lo = 0;
+        if constexpr (has_item<Pol>::value) {
+            constexpr int U = 4;
+            for (int32_t v0 = threadIdx.x; v0 < total && ok; v0 += U * T) {
+                typename Pol::Item it[U];
+#pragma unroll
+                for (int u = 0; u < U; u++) {
+                    int32_t v = v0 + u * T;
+                    if (v < total) {
+                        lo = seg_find(spre, T, lo, v);
+                        it[u] = pol.load(n, sseg[lo], v - spre[lo]);
+                    } else {
+                        it[u] = Pol::none();
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < U; u++) ok = pol.put(n, it[u], t, acc) && ok;
             }
-            if (!pol.elem(n, sseg[lo], v - spre[lo], t, acc)) {
-                ok = false;
-                break;
+        } else {
+            for (int32_t v = threadIdx.x; v < total; v += T) {
+                lo = seg_find(spre, T, lo, v);
+                if (!pol.elem(n, sseg[lo], v - spre[lo], t, acc)) {
+                    ok = false;
+                    break;
+                }
             }
         }
         if (!ok) *sfail = 1;
@@ -449,10 +494,16 @@ __global__ void __launch_bounds__(T)
     clear_slots(t, threadIdx.x, CAP, T);
     const int32_t* list = lists + (int64_t)TIER * pol.V;
     int64_t nl = cnt[TIER];
-    for (int64_t idx = blockIdx.x; idx < nl; idx += gridDim.x) {
-        int32_t n = list[idx];
-        if (threadIdx.x == 0) sfail = 0;
+    __shared__ int64_t snext;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            snext = (int64_t)atomicAdd((unsigned long long*)&cnt[HT_CNT_NEXT + TIER], 1ull);
+            sfail = 0;
+        }
         __syncthreads();
+        int64_t idx = snext;
+        if (idx >= nl) break;
+        int32_t n = list[idx];
         int64_t vb = pol.vb(n), ve = pol.ve(n);
         Acc acc;
         bool ok = block_visit<S, Pol, T>(pol, n, vb, ve, t, acc, sseg, spre, swarp, &sfail);

@@ -24,6 +24,9 @@
 //   scan, k_pl_best, k_pl_first   the best positive prefix per start
 //   k_pl_apply    the prefix's swaps applied to gamma and pi
 #include "internal.cuh"
+
+#include <algorithm>
+#include <vector>
 #include "place_items.cuh"
 
 #include <climits>
@@ -581,6 +584,33 @@ int snnmap_place_trd(int32_t n_nodes, int32_t n_hedges, const int64_t* d_offsets
         if (!h_trd_out) return finish(Status{SNNMAP_ERR_INVALID, "h_trd_out is NULL"});
         Input in{n_nodes, n_hedges, width, height, n_starts, 0, 0, d_offsets, d_pins, d_eta};
         return finish(trd_impl(in, d_gamma, (cudaStream_t)stream, h_trd_out));
+    } catch (const std::bad_alloc&) {
+        return finish(Status{SNNMAP_ERR_OOM, "host allocation failed"});
+    } catch (...) {
+        return finish(Status{SNNMAP_ERR_CUDA, "internal error"});
+    }
+}
+
+int snnmap_place_best(int32_t n_nodes, int32_t n_hedges, const int64_t* d_offsets,
+                      const int32_t* d_pins, const int64_t* d_eta, int32_t width, int32_t height,
+                      int32_t n_starts, const int32_t* d_gamma, void* stream, int32_t* best_out,
+                      int64_t* trd_out, int64_t* h_trd_out)
+{
+    try {
+        if (!best_out) return finish(Status{SNNMAP_ERR_INVALID, "best_out is NULL"});
+        Input in{n_nodes, n_hedges, width, height, n_starts, 0, 0, d_offsets, d_pins, d_eta};
+        std::vector<int64_t> trd((size_t)(n_starts > 0 ? n_starts : 1));
+        Status st = trd_impl(in, d_gamma, (cudaStream_t)stream, trd.data());
+        if (!st.ok()) return finish(st);
+        // Sec. 4.2: the start of smallest total residual distance; the
+        // lowest start on ties
+        int32_t best = 0;
+        for (int32_t s = 1; s < n_starts; s++)
+            if (trd[(size_t)s] < trd[(size_t)best]) best = s;
+        *best_out = best;
+        if (trd_out) *trd_out = trd[(size_t)best];
+        if (h_trd_out) std::copy(trd.begin(), trd.begin() + n_starts, h_trd_out);
+        return finish(Status{});
     } catch (const std::bad_alloc&) {
         return finish(Status{SNNMAP_ERR_OOM, "host allocation failed"});
     } catch (...) {

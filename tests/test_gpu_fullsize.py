@@ -1,9 +1,11 @@
 """Full-size checks on the 1,048,576-neuron conv workload, in the launch
 configuration bench.py times (device-resident inputs, snnmap_partition).
 
-The oracle cannot run whole passes at this size, so it checks a random
-sample of level-0 candidates one vertex at a time, and everything else is
-checked through properties that hold at any size: the matching pairs
+The whole pass equals the oracle's stored result (tests/golden/full_cfg2.json:
+Conn, statistics, every level's and every round's log, the hash of rho), and
+so does the 2^17-neuron power-law workload in four path settings. Besides,
+the oracle checks a random sample of level-0 candidates one vertex at a
+time, and properties that hold at any size are checked: the matching pairs
 vertices along candidate arcs and never twice, contraction conserves
 neurons, inbound pins and axons, the final partition respects Omega, Phi and
 Delta, its Conn recomputed independently equals the reported cost, and the
@@ -126,3 +128,60 @@ def test_contraction_conserves(big):
     assert (inc == a["in_count"]).all()
     assert (a["size"] <= hg.omega).all() and (a["inpins"] <= hg.phi).all()
     assert (a["in_count"] <= hg.delta).all()
+
+
+# ---------------------------------------------------------------------------
+# Whole passes against the oracle's stored results (tests/golden/full_*.json,
+# written by tests/golden/make_fullsize.py from oracle.partition alone): the
+# 1,048,576-neuron conv workload, and the 2^17-neuron power-law workload that
+# has the 2^23-neuron workload's fan-out law, locality and limits.
+
+def _golden(name):
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", f"full_{name}.json")
+    with open(path) as f:
+        return json.load(f)
+
+
+def _check_against_golden(hg, gold, setup=None):
+    import hashlib
+    from paper_2609_07577_gb300 import HGraph
+    G = HGraph.from_hypergraph(hg)
+    try:
+        if setup is not None:
+            setup(G)
+        rho, cost, st = G.partition()
+        rho = rho.cpu().numpy()
+        lv, rl = G.level_logs(), G.round_logs()
+    finally:
+        G.close()
+    assert (hg.V, hg.E, hg.P) == (gold["V"], gold["E"], gold["P"])
+    assert cost == gold["cost"]
+    for k, v in gold["stats"].items():
+        assert st[k] == v, k
+    assert [(g["V"], g["E"], g["P"], g["n_cand"], g["n_pairs"]) for g in lv] == \
+           [(g["V"], g["E"], g["P"], g["n_cand"], g["n_pairs"]) for g in gold["levels"]]
+    assert [(r["level"], r["round"], r["n_props"], r["istar"], r["gain"]) for r in rl] == \
+           [(r["level"], r["round"], r["n_props"], r["istar"], r["gain"]) for r in gold["rounds"]]
+    assert hashlib.sha256(np.ascontiguousarray(rho, np.int32).tobytes()).hexdigest() == \
+        gold["rho_sha256"]
+    return lv
+
+
+def test_full_pass_equals_oracle_conv(big):
+    _check_against_golden(big, _golden("cfg2"))
+
+
+@pytest.mark.parametrize("mode,rows", [(0, None), (1, 0), (2, 0), (2, None)])
+def test_full_pass_equals_oracle_power_law(mode, rows):
+    hg = snngen.by_name("cfg3m")
+
+    def setup(G):
+        G.set_coarsen_mode(mode)
+        if rows is not None:
+            G.set_row_budget(rows)
+
+    lv = _check_against_golden(hg, _golden("cfg3m"), setup)
+    if mode == 2 and rows == 0:
+        assert all(x["carried"] == 1 for x in lv[1:])

@@ -301,3 +301,23 @@ def test_place_flow_matches_oracle_composition():
     assert res["trds_initial"] == trds0 and res["trds"] == trds
     assert res["start"] == best and res["trd"] == trds[best]
     assert res["gamma"].tolist() == finals[best].tolist()
+
+
+def test_place_best_choice():
+    """snnmap_place_best: every start's total residual distance equals the
+    oracle's, and the chosen start has the smallest one, the lowest start on
+    ties (start 3 repeats start 0's placement)."""
+    import paper_2609_07577_gb300 as P
+    K, off, pins, eta, width, height = gp_of("cfg2s")
+    rng = np.random.default_rng(3)
+    g = [rng.permutation(width * height)[:K].astype(np.int32) for _ in range(3)]
+    g.append(g[0].copy())
+    d_gamma = torch.from_numpy(np.concatenate(g)).cuda()
+    d_off, d_pins, d_eta = (torch.from_numpy(np.ascontiguousarray(a)).cuda()
+                            for a in (off, pins.astype(np.int32), eta.astype(np.int64)))
+    best, trd, trds = P.snnmap_place_best(K, len(off) - 1, d_off, d_pins, d_eta, width, height,
+                                          4, d_gamma)
+    ref = [oracle.place_trd(K, off, pins, eta, width, x) for x in g]
+    assert trds == ref
+    assert best == min(range(4), key=lambda s: (ref[s], s)) and trd == ref[best]
+    assert best != 3
