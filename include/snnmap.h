@@ -590,6 +590,21 @@ int snnmap_hilbert_order(int32_t width, int32_t height, int32_t* d_order_out, vo
 /* Kernels launched by the library in this process so far. */
 int64_t snnmap_launch_count(void);
 
+/*
+ * Measurement utility with no counterpart in the paper: the on-chip ceiling
+ * of the neighbour histogram of Eq. neigh_histogram as this library builds
+ * it. The block tier's shared-memory table insert (hash probe, key claim,
+ * integer adds of score and shared count) runs on keys made in registers
+ * (no global memory), `distinct_keys` distinct neighbours per table (1 to
+ * 1536, the tier's load limit), the tier's block size and blocks per SM,
+ * `rounds` tables per block, each followed by the scan that reads and
+ * resets it. *updates_per_s: element updates per second of the timed launch
+ * (after one untimed launch). Allocates 8 bytes of device memory; synchronizes
+ * the stream. Errors: SNNMAP_ERR_INVALID, SNNMAP_ERR_CUDA.
+ */
+int snnmap_hist_ceiling(int32_t distinct_keys, int32_t rounds, void* stream,
+                        double* updates_per_s);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* snnmap_last_error(void);
 

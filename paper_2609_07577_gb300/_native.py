@@ -104,6 +104,7 @@ _SIGS = {
     "snnmap_set_level_budget": (C.c_int, [_vp, _i64]),
     "snnmap_set_row_budget": (C.c_int, [_vp, _i64]),
     "snnmap_set_coarsen_mode": (C.c_int, [_vp, _i32]),
+    "snnmap_hist_ceiling": (C.c_int, [_i32, _i32, _vp, C.POINTER(C.c_double)]),
     "snnmap_set_histogram_tiers": (C.c_int, [_vp, _i64, _i64, _i64]),
     "snnmap_partition_graph": (C.c_int, [_vp, _i32, _vp, _vp, C.POINTER(_i32), C.POINTER(_i64),
                                          C.POINTER(_i64)]),
@@ -449,6 +450,14 @@ def snnmap_hilbert_order(width, height, d_order_out, stream=None):
 
 def snnmap_set_row_budget(h, nbytes):
     check(lib().snnmap_set_row_budget(h, int(nbytes)))
+
+
+def snnmap_hist_ceiling(distinct_keys=1024, rounds=64, stream=None):
+    """On-chip ceiling of the neighbour-histogram insert (updates/s)."""
+    r = C.c_double()
+    check(lib().snnmap_hist_ceiling(int(distinct_keys), int(rounds), _stream(stream),
+                                    C.byref(r)))
+    return r.value
 
 
 def snnmap_set_coarsen_mode(h, mode):

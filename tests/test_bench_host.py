@@ -14,10 +14,29 @@ def load_bench():
 
 def test_onchip_rate():
     b = load_bench()
-    r = b.onchip_rate(2_000_000_000, 400.0)
-    assert r["pair_updates_per_s"] == 5e9
+    r = b.onchip_rate(2_000_000_000, 1_000_000_000, 400.0, 1e10)
+    assert r["pair_updates_per_s"] == 5e9 and r["elements_per_s"] == 2.5e9
     assert r["pair_updates"] == 2_000_000_000 and r["affinity_ms"] == 400.0
-    assert b.onchip_rate(10, 0) is None and b.onchip_rate(10, None) is None
+    assert r["frac"] == 0.25
+    assert "frac" not in b.onchip_rate(10, 10, 1.0, None)
+    assert b.onchip_rate(10, 10, 0, 1e9) is None and b.onchip_rate(10, 10, None, 1e9) is None
+
+
+def test_traffic_record(tmp_path, monkeypatch):
+    import hashlib
+    import json
+    b = load_bench()
+    src = tmp_path / "k.cu"
+    src.write_text("kernel")
+    (tmp_path / "profiles").mkdir()
+    rec = {"stage": "affinity", "kernel": "k", "dram_bytes": 300, "algorithmic_bytes": 100,
+           "sources": ["k.cu"], "sources_sha256": hashlib.sha256(b"kernel").hexdigest()}
+    (tmp_path / "profiles" / "roofline_traffic.json").write_text(json.dumps(rec))
+    monkeypatch.setattr(b, "ROOT", str(tmp_path))
+    assert b.traffic_record("affinity", 1000) == (3000.0, "k")
+    assert b.traffic_record("gains", 1000) == (None, None)
+    src.write_text("kernel changed")
+    assert b.traffic_record("affinity", 1000)[0] is None
 
 
 def test_pinned_to_one_core_restores_affinity():
