@@ -332,6 +332,20 @@ int snnmap_set_coarsen_mode(snnmap_hgraph* h, int32_t mode);
  */
 int snnmap_set_histogram_tiers(snnmap_hgraph* h, int64_t wwork, int64_t bwork, int64_t gwork);
 
+/*
+ * Process-wide defaults of the histogram tier thresholds by input size, as an
+ * autotuning sweep picked them (paper_2609_07577_gb300/autotune.py writes the
+ * table, the Python package loads it): a handle built from a hypergraph of P
+ * pins takes the thresholds of the first row with P <= max_pins[i] (rows in
+ * increasing max_pins), or of the last row beyond them; snnmap_set_histogram_tiers
+ * overrides them per handle. n = 0 restores the built-in defaults. Handles
+ * already built keep theirs. Results do not depend on the table.
+ * SNNMAP_ERR_INVALID for n < 0, NULL arrays, negative thresholds or max_pins
+ * not increasing.
+ */
+int snnmap_set_tier_table(int32_t n, const int64_t* max_pins, const int64_t* wwork,
+                          const int64_t* bwork, const int64_t* gwork);
+
 /* Bytes of device memory the handle currently holds. */
 int snnmap_device_bytes(const snnmap_hgraph* h, int64_t* bytes);
 

@@ -13,6 +13,7 @@ from ._native import (  # noqa: F401
     snnmap_round_logs, snnmap_level_logs, snnmap_device_bytes, snnmap_free, snnmap_last_error,
     snnmap_profile, snnmap_stage_times, snnmap_launch_count, snnmap_set_level_budget, snnmap_set_row_budget, snnmap_connectivity_noalloc,
     snnmap_set_coarsen_mode, snnmap_set_histogram_tiers, snnmap_hist_ceiling,
+    snnmap_set_tier_table,
     snnmap_partition_graph, snnmap_partition_graph_copy, PlaceLog, snnmap_place_refine,
     snnmap_place_trd, snnmap_place_best, snnmap_place_initial, snnmap_hilbert_order,
     Job, ServeOpts, snnmap_peak_bytes, snnmap_job_footprint, snnmap_serve_create, snnmap_serve_submit,

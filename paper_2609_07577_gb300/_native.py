@@ -106,6 +106,7 @@ _SIGS = {
     "snnmap_set_coarsen_mode": (C.c_int, [_vp, _i32]),
     "snnmap_hist_ceiling": (C.c_int, [_i32, _i32, _vp, C.POINTER(C.c_double)]),
     "snnmap_set_histogram_tiers": (C.c_int, [_vp, _i64, _i64, _i64]),
+    "snnmap_set_tier_table": (C.c_int, [_i32, _vp, _vp, _vp, _vp]),
     "snnmap_partition_graph": (C.c_int, [_vp, _i32, _vp, _vp, C.POINTER(_i32), C.POINTER(_i64),
                                          C.POINTER(_i64)]),
     "snnmap_partition_graph_copy": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
@@ -134,8 +135,11 @@ _SIGS = {
 
 
 def lib():
-    """Loads libsnnmap.so; raises if it is missing (build it first)."""
+    """Loads libsnnmap.so; raises if it is missing (build it first). On first
+    load, installs the autotuned histogram tier table if the package has one
+    (autotune.load_table)."""
     global _lib
+    fresh = False
     with _lock:
         if _lib is None:
             if not os.path.exists(LIB_PATH):
@@ -148,7 +152,11 @@ def lib():
                 f.restype = res
                 f.argtypes = args
             _lib = L
-        return _lib
+            fresh = True
+    if fresh:
+        from .autotune import load_table
+        load_table()
+    return _lib
 
 
 def check(rc):
@@ -462,6 +470,14 @@ def snnmap_hist_ceiling(distinct_keys=1024, rounds=64, stream=None):
 
 def snnmap_set_coarsen_mode(h, mode):
     check(lib().snnmap_set_coarsen_mode(h, int(mode)))
+
+
+def snnmap_set_tier_table(rows):
+    """rows: [(max_pins, wwork, bwork, gwork), ...] in increasing max_pins
+    (empty: built-in defaults)."""
+    n = len(rows)
+    arr = [(C.c_int64 * max(n, 1))(*[int(r[i]) for r in rows]) for i in range(4)]
+    check(lib().snnmap_set_tier_table(n, *[C.cast(a, C.c_void_p) for a in arr]))
 
 
 def snnmap_set_histogram_tiers(h, wwork=-1, bwork=-1, gwork=-1):

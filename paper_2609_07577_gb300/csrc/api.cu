@@ -5,8 +5,10 @@
 #include "internal.cuh"
 
 #include <climits>
+#include <mutex>
 #include <new>
 #include <string>
+#include <vector>
 
 namespace {
 
@@ -52,6 +54,23 @@ void bind(snnmap_hgraph* h, void* stream)
 {
     h->stream = (cudaStream_t)stream;
     h->scratch.stream = h->stream;
+}
+
+// process-wide histogram tier table (snnmap_set_tier_table): rows by
+// ascending level-0 pin count
+struct TierRow {
+    int64_t max_pins;
+    snn::HtTiers t;
+};
+std::mutex g_tier_mu;
+std::vector<TierRow> g_tier_rows;
+
+snn::HtTiers tiers_for(int64_t pins)
+{
+    std::lock_guard<std::mutex> lk(g_tier_mu);
+    for (const TierRow& r : g_tier_rows)
+        if (pins <= r.max_pins) return r.t;
+    return g_tier_rows.empty() ? snn::HtTiers{} : g_tier_rows.back().t;
 }
 
 void drop_levels_above(snnmap_hgraph* h, size_t keep)
@@ -184,6 +203,7 @@ static int snnmap_build_hgraph_impl(const snnmap_params* params, int32_t n_verti
         snnmap_free(h);
         return fail(st);
     }
+    h->tiers = tiers_for(h->levels[0].P);
     *out = h;
     return SNNMAP_OK;
 }
@@ -639,6 +659,27 @@ int snnmap_set_coarsen_mode(snnmap_hgraph* h, int32_t mode)
     if (mode < 0 || mode > 2) return fail(SNNMAP_ERR_INVALID, "mode must be 0, 1 or 2");
     h->coarsen_mode = mode;
     if (mode == 1) h->icar.level = -1;
+    return SNNMAP_OK;
+}
+
+int snnmap_set_tier_table(int32_t n, const int64_t* max_pins, const int64_t* wwork,
+                          const int64_t* bwork, const int64_t* gwork)
+{
+    g_err.clear();
+    if (n < 0 || (n > 0 && (!max_pins || !wwork || !bwork || !gwork)))
+        return fail(SNNMAP_ERR_INVALID, "n < 0 or a NULL array");
+    std::vector<TierRow> rows;
+    try {
+        for (int32_t i = 0; i < n; i++) {
+            if (wwork[i] < 0 || bwork[i] < 0 || gwork[i] < 0 || (i > 0 && max_pins[i] <= max_pins[i - 1]))
+                return fail(SNNMAP_ERR_INVALID, "negative thresholds or max_pins not increasing");
+            rows.push_back(TierRow{max_pins[i], snn::HtTiers{wwork[i], bwork[i], gwork[i]}});
+        }
+    } catch (const std::bad_alloc&) {
+        return fail(SNNMAP_ERR_OOM, "host allocation failed");
+    }
+    std::lock_guard<std::mutex> lk(g_tier_mu);
+    g_tier_rows.swap(rows);
     return SNNMAP_OK;
 }
 
