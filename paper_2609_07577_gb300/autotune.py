@@ -48,7 +48,7 @@ def load_table(path=TABLE):
     return rows
 
 
-def sample_jobs(per_class=2, scan=256):
+def sample_jobs(per_class=2, scan=64):
     """Jobs of the batched workload (seed = job index), the first `per_class`
     of each generator (layered, power-law) in every size class; classes the
     batched workload does not reach take scaled-up instances of the conv

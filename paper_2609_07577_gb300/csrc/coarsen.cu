@@ -60,6 +60,7 @@ struct AffPol {
     const int32_t* vmin;   // smallest size and inbound pins over the level's vertices
     bool prefilter;        // some pair can break Omega or Phi (else elem skips the test)
     const uint8_t* only = nullptr;   // if set, the vertices evaluated (others untouched)
+    const int4* vst;       // (size, inbound pins, inbound axons) per vertex
 
     // n cannot merge even with the smallest vertex: no candidate
     __device__ bool skip(int32_t n) const
@@ -103,9 +104,12 @@ struct AffPol {
         it.o = (g.nd && md) ? g.k : 0u;
         // a neighbour whose size or inbound pins alone break Omega or Phi
         // with n can never be the candidate: leave it out of the table
-        if (it.m == n || (prefilter && ((int64_t)L.vsize[n] + L.vsize[it.m] > omega ||
-                                        (int64_t)L.vinpins[n] + L.vinpins[it.m] > phi)))
+        if (it.m == n) {
             it.m = -1;
+        } else if (prefilter) {
+            int4 a = vst[n], b = vst[it.m];
+            if ((int64_t)a.x + b.x > omega || (int64_t)a.y + b.y > phi) it.m = -1;
+        }
         return it;
     }
     template <class Tb>
@@ -121,9 +125,9 @@ struct AffPol {
     __device__ void consider(int32_t n, int32_t m, int64_t s, uint32_t o, const Acc&, int64_t& bs,
                              int32_t& bk, uint32_t& bo) const
     {
-        bool valid = (int64_t)L.vsize[n] + L.vsize[m] <= omega &&
-                     (int64_t)L.vinpins[n] + L.vinpins[m] <= phi &&
-                     (int64_t)L.vincnt[n] + L.vincnt[m] - (int64_t)o <= delta;
+        int4 a = vst[n], b = vst[m];
+        bool valid = (int64_t)a.x + b.x <= omega && (int64_t)a.y + b.y <= phi &&
+                     (int64_t)a.z + b.z - (int64_t)o <= delta;
         if (valid && better(s, m, bs, bk)) {
             bs = s;
             bk = m;
@@ -138,6 +142,15 @@ struct AffPol {
         cov[n] = bk < 0 ? 0 : (int32_t)bo;
     }
 };
+
+// (size, inbound pins, inbound axons) of every vertex in one 16-byte entry, so
+// a neighbour's state is one gather in the histograms' hot loops
+__global__ void k_pack_state(Level L, int4* vst)
+{
+    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < L.V;
+         n += (int64_t)gridDim.x * blockDim.x)
+        vst[n] = make_int4(L.vsize[n], L.vinpins[n], L.vincnt[n], 0);
+}
 
 // ---------------------------------------------------------------------------
 // matching
@@ -314,7 +327,12 @@ static Status affinity(snnmap_hgraph* h, Level& L)
     int32_t vm[4];
     SNN_CUDA(cudaMemcpyAsync(vm, vmin, sizeof(vm), cudaMemcpyDeviceToHost, h->stream));
     SNN_CUDA(cudaStreamSynchronize(h->stream));
+    int4* vst;
+    SNN_TRY(h->scratch.alloc(&vst, L.V));
+    SNN_L k_pack_state<<<grid_for(L.V, 256), 256, 0, h->stream>>>(L, vst);
+    SNN_CUDA(cudaGetLastError());
     AffPol<S> pol;
+    pol.vst = vst;
     pol.vmin = vmin;
     pol.prefilter = 2 * (int64_t)vm[2] > h->prm.omega || 2 * (int64_t)vm[3] > h->prm.phi;
     pol.L = L;
@@ -551,6 +569,7 @@ struct AffNewPol {
     const uint32_t* lpins;
     AffCarry ac;
     bool prefilter;
+    const int4* vst;   // (size, inbound pins, inbound axons) per vertex
     int32_t* cand;
     int64_t* cscore;
     int32_t* cov;
@@ -589,9 +608,10 @@ struct AffNewPol {
         it.m = (int32_t)(e & ~NOT_DEST);
         it.w = g.w;
         it.o = (g.nd && !(e & NOT_DEST)) ? g.k : 0u;
-        if (prefilter && ((int64_t)L.vsize[n] + L.vsize[it.m] > omega ||
-                          (int64_t)L.vinpins[n] + L.vinpins[it.m] > phi))
-            it.m = -1;
+        if (prefilter) {
+            int4 a = vst[n], b = vst[it.m];
+            if ((int64_t)a.x + b.x > omega || (int64_t)a.y + b.y > phi) it.m = -1;
+        }
         return it;
     }
     template <class Tb>
@@ -607,9 +627,9 @@ struct AffNewPol {
     __device__ void consider(int32_t n, int32_t m, int64_t s, uint32_t o, const Acc&, int64_t& bs,
                              int32_t& bk, uint32_t& bo) const
     {
-        bool valid = (int64_t)L.vsize[n] + L.vsize[m] <= omega &&
-                     (int64_t)L.vinpins[n] + L.vinpins[m] <= phi &&
-                     (int64_t)L.vincnt[n] + L.vincnt[m] - (int64_t)o <= delta;
+        int4 a = vst[n], b = vst[m];
+        bool valid = (int64_t)a.x + b.x <= omega && (int64_t)a.y + b.y <= phi &&
+                     (int64_t)a.z + b.z - (int64_t)o <= delta;
         if (valid && better(s, m, bs, bk)) {
             bs = s;
             bk = m;
@@ -718,6 +738,10 @@ static Status affinity_carried(snnmap_hgraph* h, Level& L, bool* done)
         SNN_L k_ac_fill<<<grid_for(E * 32, 256), 256, 0, s>>>(L, C.kind, loff, lpins);
     SNN_CUDA(cudaGetLastError());
     bool prefilter = 2 * (int64_t)vm[2] > h->prm.omega || 2 * (int64_t)vm[3] > h->prm.phi;
+    int4* vst;
+    SNN_TRY(ar.alloc(&vst, L.V));
+    SNN_L k_pack_state<<<grid_for(L.V, 256), 256, 0, s>>>(L, vst);
+    SNN_CUDA(cudaGetLastError());
     int64_t* cnt;
     SNN_TRY(ar.alloc(&cnt, HT_NCNT));
     int64_t nb = 0, ng = 0, nf = 0, wk = 0;
@@ -733,6 +757,7 @@ static Status affinity_carried(snnmap_hgraph* h, Level& L, bool* done)
         pol.lpins = lpins;
         pol.ac = C;
         pol.prefilter = prefilter;
+        pol.vst = vst;
         pol.cand = h->cand;
         pol.cscore = h->cscore;
         pol.cov = h->cov;
@@ -752,6 +777,7 @@ static Status affinity_carried(snnmap_hgraph* h, Level& L, bool* done)
         pol.vmin = vmin;
         pol.prefilter = prefilter;
         pol.only = C.full;
+        pol.vst = vst;
         pol.L = L;
         pol.V = L.V;
         pol.keys = L.V;

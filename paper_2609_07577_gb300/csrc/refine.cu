@@ -377,6 +377,14 @@ struct Moves {
     int32_t* to;
 };
 
+// Hyperedges holding a proposed move (k_prop_hedges builds the list): a
+// round's replay, row updates, re-evaluation flags and pin-count updates
+// iterate it instead of every hyperedge of the level.
+struct HedgeList {
+    const int32_t* a;   // hyperedge ids
+    const int32_t* n;   // their number (device)
+};
+
 // ---------------------------------------------------------------------------
 // Connection rows (refinement levels whose rows fit the memory budget)
 //
@@ -521,7 +529,7 @@ __global__ void __launch_bounds__(256)
 __global__ void __launch_bounds__(256)
     k_dense_cross(Level L, PinCounts pc, const int32_t* __restrict__ moveidx, Moves mv,
                   const int64_t* __restrict__ scal, const int32_t* __restrict__ rowid, int32_t* C,
-                  int32_t* O, int64_t Kp, uint32_t* buf)
+                  int32_t* O, int64_t Kp, uint32_t* buf, HedgeList hl)
 {
     int64_t istar = scal[RS_BEST] > 0 ? scal[RS_ISTAR] : -1;
     if (istar < 0) return;
@@ -529,7 +537,9 @@ __global__ void __launch_bounds__(256)
     unsigned lt = lanemask_lt();
     int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t a = gw; a < L.E; a += nw) {
+    int32_t nh = *hl.n;
+    for (int64_t x = gw; x < nh; x += nw) {
+        int32_t a = hl.a[x];
         int64_t b = L.hoff[a], e = L.hoff[a + 1];
         int sd = L.hsd[a];
         int m = 0;
@@ -1047,6 +1057,36 @@ __global__ void k_moves(int32_t M, const uint32_t* __restrict__ vals, const int3
 }
 
 // ---------------------------------------------------------------------------
+// The list of hyperedges holding a proposed move, from the proposers'
+// incidence lists.
+
+__global__ void __launch_bounds__(256)
+    k_prop_hedges(int32_t M, Moves mv, Level L, int32_t* hmark, int32_t* list, int32_t* n)
+{
+    int lane = threadIdx.x & 31;
+    int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = gw; i < M; i += nw) {
+        int32_t v = mv.n[i];
+        for (int64_t j = L.voff[v] + lane; j < L.voff[v + 1]; j += 32) {
+            int32_t a = (int32_t)((uint32_t)L.vinc[j] & ~SRC_BIT);
+            if (atomicExch(&hmark[a], 1) == 0) list[atomicAdd(n, 1)] = a;
+        }
+    }
+}
+
+// the marks of the listed hyperedges back to zero for the next round
+__global__ void k_hedges_clear(HedgeList hl, int32_t* hmark, int32_t* hdirty)
+{
+    int32_t nh = *hl.n;
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < nh;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        hmark[hl.a[x]] = 0;
+        hdirty[hl.a[x]] = 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // S9 / S10 events
 
 struct Events {
@@ -1116,13 +1156,15 @@ __device__ __forceinline__ void replay_one(const Level& L, const PinCounts& pc, 
 __global__ void __launch_bounds__(256)
     k_replay_warp(Level L, PinCounts pc, const int32_t* __restrict__ moveidx, Moves mv,
                   uint32_t* mvbuf, int64_t* gp, Events ev, int64_t evbase, int32_t* heavy,
-                  int32_t* heavycnt, int64_t* scal)
+                  int32_t* heavycnt, int64_t* scal, HedgeList hl)
 {
     int lane = threadIdx.x & 31;
     unsigned lt = lanemask_lt();
     int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t a = gw; a < L.E; a += nw) {
+    int32_t nh = *hl.n;
+    for (int64_t x = gw; x < nh; x += nw) {
+        int32_t a = hl.a[x];
         int64_t b = L.hoff[a], e = L.hoff[a + 1];
         int sd = L.hsd[a];
         int cnt = 0;
@@ -1512,13 +1554,15 @@ Status level_cost(snnmap_hgraph* h, int32_t level, int32_t K, const int32_t* rho
 
 __global__ void __launch_bounds__(256)
     k_pc_mark(Level L, const int32_t* __restrict__ moveidx, const int64_t* __restrict__ scal,
-              int32_t* hdirty)
+              int32_t* hdirty, HedgeList hl)
 {
     int64_t istar = scal[RS_BEST] > 0 ? scal[RS_ISTAR] : -1;
     int lane = threadIdx.x & 31;
     int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t a = gw; a < L.E; a += nw) {
+    int32_t nh = *hl.n;
+    for (int64_t x = gw; x < nh; x += nw) {
+        int32_t a = hl.a[x];
         bool hit = false;
         if (istar >= 0)
             for (int64_t j = L.hoff[a] + lane; j < L.hoff[a + 1] && !hit; j += 32) {
@@ -1535,12 +1579,14 @@ __global__ void __launch_bounds__(256)
 __global__ void __launch_bounds__(256)
     k_pc_contrib(Level L, PinCounts pc, const int32_t* __restrict__ hdirty,
                  const int32_t* __restrict__ rho, PState ps, int64_t* savev, int64_t* costv,
-                 int sign)
+                 int sign, HedgeList hl)
 {
     int lane = threadIdx.x & 31;
     int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t a = gw; a < L.E; a += nw) {
+    int32_t nh = *hl.n;
+    for (int64_t x = gw; x < nh; x += nw) {
+        int32_t a = hl.a[x];
         if (!hdirty[a]) continue;
         int64_t b = L.hoff[a], e = L.hoff[a + 1];
         int32_t lam = pc.lam[a];
@@ -1626,6 +1672,7 @@ struct IncState {
     int64_t* savev = nullptr;
     int64_t* Wv = nullptr;
     int32_t* hdirty = nullptr;   // per hyperedge
+    int32_t* hmark = nullptr;    // per hyperedge: listed this round (k_prop_hedges)
     int32_t* hlist = nullptr;    // bucket lists filtered to dirty hyperedges
     int32_t* hmeta = nullptr;    // their bucket starts and counts (2 * SEG_NB)
     bool ready = false;          // set once the first round computed them
@@ -1740,6 +1787,16 @@ static Status refine_round(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* 
     int gm = grid_for(M, 256);
     SNN_L k_moves<<<gm, 256, 0, s>>>(M, vals, rho, pto, mv, moveidx);
     SNN_CUDA(cudaGetLastError());
+    // the hyperedges holding a proposed move
+    int64_t nhl = std::max<int64_t>(1, std::min<int64_t>(L.E, deg));
+    int32_t *hla, *hln;
+    SNN_TRY(ar.alloc(&hla, nhl));
+    SNN_TRY(ar.alloc(&hln, 1));
+    SNN_CUDA(cudaMemsetAsync(hln, 0, sizeof(int32_t), s));
+    SNN_L k_prop_hedges<<<grid_for((int64_t)M * 32, 256), 256, 0, s>>>(M, mv, L, inc.hmark, hla, hln);
+    SNN_CUDA(cudaGetLastError());
+    HedgeList hl{hla, hln};
+    const int ghl = grid_for(nhl * 32, 256);
 
     // S9
     prof.reset(new ProfScope(h, PS_REPLAY));
@@ -1767,9 +1824,8 @@ static Status refine_round(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* 
     SNN_TRY(ar.alloc(&hv, L.E));
     SNN_TRY(ar.alloc(&hvc, L.E));
     if (L.E > 0) {
-        SNN_L k_replay_warp<<<grid_for((int64_t)L.E * 32, 256), 256, 0, s>>>(L, pc, moveidx, mv, mvbuf, gp,
-                                                                      ev, 2 * (int64_t)M, hv, hvc,
-                                                                      h->d_scal);
+        SNN_L k_replay_warp<<<ghl, 256, 0, s>>>(L, pc, moveidx, mv, mvbuf, gp, ev, 2 * (int64_t)M, hv,
+                                                hvc, h->d_scal, hl);
         SNN_CUDA(cudaGetLastError());
         SNN_L k_replay_block<<<152 * 2, 256, 0, s>>>(L, pc, mv, mvbuf, gp, ev, 2 * (int64_t)M, hv, hvc,
                                                h->d_scal);
@@ -1807,8 +1863,8 @@ static Status refine_round(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* 
     SNN_L k_best2<<<gm, 256, 0, s>>>(M, G, nviol, h->d_scal);
     if (dense && L.E > 0) {
         prof.reset(new ProfScope(h, PS_CROSS));
-        SNN_L k_dense_cross<<<grid_for((int64_t)L.E * 32, 256), 256, 0, s>>>(
-            L, pc, moveidx, mv, h->d_scal, D.rowid, D.C, D.O, D.Kp, mvbuf);
+        SNN_L k_dense_cross<<<ghl, 256, 0, s>>>(L, pc, moveidx, mv, h->d_scal, D.rowid, D.C, D.O,
+                                                D.Kp, mvbuf, hl);
         prof.reset(new ProfScope(h, PS_APPLY));
     }
     if (!dense) {
@@ -1833,10 +1889,9 @@ static Status refine_round(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* 
     // carried pin counts: take out the hyperedges the prefix touches (old
     // counts, old rho), move, count them again, add them back
     prof.reset(new ProfScope(h, PS_PINCOUNT));
-    int ghe = grid_for((int64_t)(L.E > 0 ? L.E : 1) * 32, 256);
     if (L.E > 0) {
-        SNN_L k_pc_mark<<<ghe, 256, 0, s>>>(L, moveidx, h->d_scal, inc.hdirty);
-        SNN_L k_pc_contrib<<<ghe, 256, 0, s>>>(L, pc, inc.hdirty, rho, ps, savev, inc.costv, -1);
+        SNN_L k_pc_mark<<<ghl, 256, 0, s>>>(L, moveidx, h->d_scal, inc.hdirty, hl);
+        SNN_L k_pc_contrib<<<ghl, 256, 0, s>>>(L, pc, inc.hdirty, rho, ps, savev, inc.costv, -1, hl);
         SNN_CUDA(cudaGetLastError());
     }
     SNN_L k_ps_moves<<<gm, 256, 0, s>>>(M, mv, L, h->d_scal, ps);
@@ -1857,7 +1912,8 @@ static Status refine_round(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* 
         PinCountJob job{L.hoff, L.hpins, L.hsd, L.hk, L.hw, rho, pc, ps.pincnt, slots};
         SNN_TRY(seg_run(job, db, L.E, ar, s));
         SNN_L k_cost_slots<<<1, 256, 0, s>>>(slots, inc.costv);
-        SNN_L k_pc_contrib<<<ghe, 256, 0, s>>>(L, pc, inc.hdirty, rho, ps, savev, inc.costv, 1);
+        SNN_L k_pc_contrib<<<ghl, 256, 0, s>>>(L, pc, inc.hdirty, rho, ps, savev, inc.costv, 1, hl);
+        SNN_L k_hedges_clear<<<grid_for(nhl, 256), 256, 0, s>>>(hl, inc.hmark, inc.hdirty);
         SNN_CUDA(cudaGetLastError());
     }
     if (!dense) {
@@ -2007,6 +2063,9 @@ Status refine_level(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* rho, in
     SNN_CUDA(cudaMallocAsync(&inc.savev, nv * 8, s));
     SNN_CUDA(cudaMallocAsync(&inc.Wv, nv * 8, s));
     SNN_CUDA(cudaMallocAsync(&inc.hdirty, ne * 4, s));
+    SNN_CUDA(cudaMallocAsync(&inc.hmark, ne * 4, s));
+    SNN_CUDA(cudaMemsetAsync(inc.hdirty, 0, ne * 4, s));
+    SNN_CUDA(cudaMemsetAsync(inc.hmark, 0, ne * 4, s));
     SNN_CUDA(cudaMallocAsync(&inc.hlist, ne * 4, s));
     SNN_CUDA(cudaMallocAsync(&inc.hmeta, 2 * SEG_NB * 4, s));
     PStar& pst = inc.pst;
@@ -2076,7 +2135,8 @@ Status refine_level(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* rho, in
                     (void*)inc.prel, (void*)inc.vmax, (void*)inc.pc.p, (void*)inc.pc.cnt,
                     (void*)inc.pc.dcnt, (void*)inc.pc.lam, (void*)inc.ps.size,
                     (void*)inc.ps.inpins, (void*)inc.ps.pincnt, (void*)inc.costv,
-                    (void*)inc.savev, (void*)inc.Wv, (void*)inc.hdirty, (void*)inc.hlist,
+                    (void*)inc.savev, (void*)inc.Wv, (void*)inc.hdirty, (void*)inc.hmark,
+                    (void*)inc.hlist,
                     (void*)inc.hmeta, (void*)pst.pslot, (void*)pst.slots, (void*)pst.cnt,
                     (void*)pst.hmask, (void*)pst.hl, (void*)pst.colc, (void*)pst.colo,
                     (void*)pst.vt, (void*)pst.save0})

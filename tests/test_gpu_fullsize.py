@@ -185,3 +185,46 @@ def test_full_pass_equals_oracle_power_law(mode, rows):
     lv = _check_against_golden(hg, _golden("cfg3m"), setup)
     if mode == 2 and rows == 0:
         assert all(x["carried"] == 1 for x in lv[1:])
+
+
+def _properties(hg, rho, cost, levels, inpins):
+    assert cost == conn_np(hg, rho)
+    K = int(rho.max()) + 1
+    assert (np.bincount(rho, minlength=K) <= hg.omega).all()
+    assert (np.bincount(rho, weights=inpins, minlength=K) <= hg.phi).all()
+    isdst = np.ones(hg.P, bool)
+    isdst[hg.off[:-1]] = False
+    hid = np.repeat(np.arange(hg.E, dtype=np.int64), np.diff(hg.off))
+    key = np.unique(rho[hg.pins[isdst]].astype(np.int64) * hg.E + hid[isdst])
+    assert (np.bincount(key // hg.E, minlength=K) <= hg.delta).all()
+    Vs = [g["V"] for g in levels]
+    assert all(b < a for a, b in zip(Vs, Vs[1:]))
+
+
+def test_power_law_2e23_sampled_and_properties():
+    """The 2^23-neuron power-law workload: level-0 candidates of 1,500
+    sampled vertices equal the oracle's one-vertex evaluation, and the whole
+    pass satisfies Conn, Omega, Phi and Delta."""
+    from paper_2609_07577_gb300 import HGraph
+    hg = snngen.cfg3()
+    prm = oracle.params_of(hg)
+    G = HGraph.from_hypergraph(hg)
+    try:
+        G.coarsen_level()
+        cand, cs, cov, _ = G.last_matching()
+        a0 = G.level_arrays(0)
+    finally:
+        G.close()
+    L = oracle.Level.from_hypergraph(hg, prm)
+    rng = np.random.default_rng(9)
+    for n in np.concatenate([rng.choice(hg.V, 1500, replace=False), [0, hg.V - 1]]):
+        assert (cand[n], cs[n], cov[n]) == L.cand_one(int(n), prm), n
+    del L
+    G = HGraph.from_hypergraph(hg)
+    try:
+        rho_t, cost, st = G.partition()
+        rho = rho_t.cpu().numpy()
+        levels = G.level_logs()
+    finally:
+        G.close()
+    _properties(hg, rho, cost, levels, a0["inpins"])
