@@ -337,7 +337,8 @@ int snnmap_set_histogram_tiers(snnmap_hgraph* h, int64_t wwork, int64_t bwork, i
  * autotuning sweep picked them (paper_2609_07577_gb300/autotune.py writes the
  * table, the Python package loads it): a handle built from a hypergraph of P
  * pins takes the thresholds of the first row with P <= max_pins[i] (rows in
- * increasing max_pins), or of the last row beyond them; snnmap_set_histogram_tiers
+ * increasing max_pins), or the built-in defaults beyond the last row (sizes
+ * the sweep did not time); snnmap_set_histogram_tiers
  * overrides them per handle. n = 0 restores the built-in defaults. Handles
  * already built keep theirs. Results do not depend on the table.
  * SNNMAP_ERR_INVALID for n < 0, NULL arrays, negative thresholds or max_pins

@@ -70,7 +70,7 @@ snn::HtTiers tiers_for(int64_t pins)
     std::lock_guard<std::mutex> lk(g_tier_mu);
     for (const TierRow& r : g_tier_rows)
         if (pins <= r.max_pins) return r.t;
-    return g_tier_rows.empty() ? snn::HtTiers{} : g_tier_rows.back().t;
+    return snn::HtTiers{};   // sizes the table does not cover keep the built-in defaults
 }
 
 void drop_levels_above(snnmap_hgraph* h, size_t keep)

@@ -465,36 +465,31 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-// work[0] += incidence segment lengths of the NEW vertices, work[1] those of
-// the MERGED ones (what full histograms of them cost at most)
+// work[0] += incidence segment lengths of the NEW vertices (what their full
+// histograms cost); MERGED vertices mostly keep the new super-node their
+// candidate merged into (k_ac_check), so they are left out of the estimate
 __global__ void __launch_bounds__(256)
     k_ac_fullwork(Level L, const uint8_t* __restrict__ kind, int64_t* work)
 {
     int lane = threadIdx.x & 31;
     int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    int64_t acc[2] = {0, 0};
+    int64_t acc = 0;
     for (int64_t base = gw * 32; base < L.V; base += nw * 32) {
         int64_t n = base + lane;
-        uint8_t k = n < L.V ? kind[n] : AK_NONE;
-        unsigned mem = __ballot_sync(FULL, k >= AK_MERGED);
+        unsigned mem = __ballot_sync(FULL, n < L.V && kind[n] == AK_NEW);
         while (mem) {
             int src = __ffs(mem) - 1;
             mem &= mem - 1;
             int32_t m = (int32_t)__shfl_sync(FULL, (int32_t)n, src);
-            int which = __shfl_sync(FULL, (int)k, src) == AK_NEW ? 0 : 1;
-            int64_t t = 0;
             for (int64_t i = L.voff[m] + lane; i < L.voff[m + 1]; i += 32) {
                 int32_t a = (int32_t)((uint32_t)L.vinc[i] & ~SRC_BIT);
-                t += L.hoff[a + 1] - L.hoff[a];
+                acc += L.hoff[a + 1] - L.hoff[a];
             }
-            acc[which] += t;
         }
     }
-    for (int u = 0; u < 2; u++) {
-        int64_t v = warp_sum(acc[u]);
-        if (lane == 0 && v) atomicAdd((unsigned long long*)&work[1 + u], (unsigned long long)v);
-    }
+    acc = warp_sum(acc);
+    if (lane == 0 && acc) atomicAdd((unsigned long long*)work, (unsigned long long)acc);
 }
 
 // MERGED vertices whose best valid new super-node is not w = cand (full
@@ -718,23 +713,23 @@ static Status affinity_carried(snnmap_hgraph* h, Level& L, bool* done)
     SNN_CUDA(cudaMemsetAsync(work, 0, 4 * sizeof(int64_t), s));
     SNN_L k_level_min<<<grid_for(L.V, 256), 256, 0, s>>>(L, vmin);
     if (E > 0) SNN_L k_ac_count<<<grid_for(E * 32, 256), 256, 0, s>>>(L, C.kind, lcnt, work);
-    SNN_L k_ac_fullwork<<<grid_for(L.V, 256), 256, 0, s>>>(L, C.kind, work);
+    SNN_L k_ac_fullwork<<<grid_for(L.V, 256), 256, 0, s>>>(L, C.kind, work + 1);
     SNN_CUDA(cudaGetLastError());
     SNN_TRY(scan_exclusive_i32_to_i64(lcnt, loff, E, loff + E, ar, s));
-    int64_t hv[4];
+    int64_t hv[3];
     int32_t vm[4];
     SNN_CUDA(cudaMemcpyAsync(vm, vmin, sizeof(vm), cudaMemcpyDeviceToHost, s));
-    SNN_CUDA(cudaMemcpyAsync(hv, work, 3 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    SNN_CUDA(cudaMemcpyAsync(hv + 3, loff + E, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    SNN_CUDA(cudaMemcpyAsync(hv, work, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    SNN_CUDA(cudaMemcpyAsync(hv + 2, loff + E, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     SNN_CUDA(cudaStreamSynchronize(s));
-    // carried work: the new super-nodes' lists, the new super-nodes' full
-    // histograms, and those of the MERGED vertices whose super-node no
-    // longer suits them (at most hv[2]; usually few)
+    // carried work: the new super-nodes' lists and the new super-nodes' full
+    // histograms (plus those of the few MERGED vertices whose super-node no
+    // longer suits them)
     int64_t full_work = h->extra.back().pair_terms + L.P;
     if (h->coarsen_mode != 2 && 4 * (hv[0] + hv[1]) >= 3 * full_work) return Status{};
     uint32_t* lpins;
-    SNN_TRY(ar.alloc(&lpins, hv[3]));
-    if (E > 0 && hv[3] > 0)
+    SNN_TRY(ar.alloc(&lpins, hv[2]));
+    if (E > 0 && hv[2] > 0)
         SNN_L k_ac_fill<<<grid_for(E * 32, 256), 256, 0, s>>>(L, C.kind, loff, lpins);
     SNN_CUDA(cudaGetLastError());
     bool prefilter = 2 * (int64_t)vm[2] > h->prm.omega || 2 * (int64_t)vm[3] > h->prm.phi;

@@ -4,10 +4,12 @@
 // 1. Coarse ids: a vertex represents its pair if it is unmatched or the
 //    lower id of the pair; cid = rank of the representative (exclusive scan).
 // 2. Super-node state: size, inbound pins and internal axons add up over the
-//    members; the size of the merged inbound set (the paper's
-//    in_count(n) + in_count(m) - shared(n, m)) is recomputed from the coarse
-//    level as internal axons + the k of every coarse hyperedge the
-//    super-node is a destination of, which the two share.
+//    members; the size of the merged inbound set is the paper's
+//    in_count(n) + in_count(m) - shared(n, m), the shared count being the
+//    candidate overlap of the pair. A level rebuilt through composed maps
+//    (no matching at hand) recomputes it from the coarse level as internal
+//    axons + the k of every coarse hyperedge the super-node is a
+//    destination of.
 // 3. Per hyperedge (segmented sort): s' = cid(source), destinations mapped
 //    through cid, sorted, made unique; s' among them sets selfdst and is
 //    removed. A hyperedge left with no destination is dropped and its
@@ -75,6 +77,26 @@ __global__ void k_in_count(Level N)
         int32_t k = N.hk[a];
         for (int64_t j = b + 1 + lane; j < e; j += 32) atomicAdd(&N.vincnt[N.hpins[j]], k);
         if (lane == 0 && N.hsd[a]) atomicAdd(&N.vincnt[N.hpins[b]], k);
+    }
+}
+
+// in_count of the next level straight from a matching: an unmatched vertex
+// keeps its count; a pair's super-node has in_count(n) + in_count(m) -
+// shared(n, m), the shared count being the candidate overlap of the member
+// whose candidate is the other (pairs are matched along candidate arcs)
+__global__ void k_in_count_pairs(Level S, const int32_t* __restrict__ map,
+                                 const int32_t* __restrict__ match, const int32_t* __restrict__ cand,
+                                 const int32_t* __restrict__ cov, int32_t* incnt_next)
+{
+    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < S.V;
+         n += (int64_t)gridDim.x * blockDim.x) {
+        int32_t m = match[n];
+        if (m < 0) {
+            incnt_next[map[n]] = S.vincnt[n];
+        } else if ((int32_t)n < m) {
+            int32_t ov = cand[n] == m ? cov[n] : cov[m];
+            incnt_next[map[n]] = S.vincnt[n] + S.vincnt[m] - ov;
+        }
     }
 }
 
@@ -281,7 +303,7 @@ __global__ void k_set_off_end(int64_t* hoff, int32_t E, int64_t P) { hoff[E] = P
 // count. If levels[dst] already records sizes (a released level being
 // rebuilt), the rebuilt sizes must match them.
 Status build_coarse(snnmap_hgraph* h, int32_t src, const int32_t* map, const int64_t* d_V2,
-                    int32_t dst)
+                    int32_t dst, const int32_t* match, const int32_t* cand, const int32_t* cov)
 {
     cudaStream_t s = h->stream;
     Arena& ar = h->scratch;
@@ -375,7 +397,12 @@ Status build_coarse(snnmap_hgraph* h, int32_t src, const int32_t* map, const int
         SNN_CUDA(cudaMemcpyAsync(N.vsize, ns.size, (size_t)V2 * 4, cudaMemcpyDeviceToDevice, s));
         SNN_CUDA(cudaMemcpyAsync(N.vinpins, ns.inpins, (size_t)V2 * 4, cudaMemcpyDeviceToDevice, s));
         SNN_CUDA(cudaMemcpyAsync(N.vinint, ns.inint, (size_t)V2 * 4, cudaMemcpyDeviceToDevice, s));
-        SNN_CUDA(cudaMemcpyAsync(N.vincnt, ns.inint, (size_t)V2 * 4, cudaMemcpyDeviceToDevice, s));
+        if (!match)
+            SNN_CUDA(cudaMemcpyAsync(N.vincnt, ns.inint, (size_t)V2 * 4, cudaMemcpyDeviceToDevice, s));
+    }
+    if (match && V > 0) {
+        SNN_L k_in_count_pairs<<<grid_for(V, 256), 256, 0, s>>>(L, map, match, cand, cov, N.vincnt);
+        SNN_CUDA(cudaGetLastError());
     }
     if (E > 0) {
         SNN_L k_dedup_emit<<<grid_for((int64_t)E * 32, 256), 256, 0, s>>>(
@@ -384,7 +411,7 @@ Status build_coarse(snnmap_hgraph* h, int32_t src, const int32_t* map, const int
     }
     SNN_L k_set_off_end<<<1, 1, 0, s>>>(N.hoff, E2, P2);
     SNN_CUDA(cudaGetLastError());
-    if (E2 > 0) {
+    if (E2 > 0 && !match) {
         SNN_L k_in_count<<<grid_for((int64_t)E2 * 32, 256), 256, 0, s>>>(N);
         SNN_CUDA(cudaGetLastError());
     }
@@ -422,7 +449,7 @@ Status contract_level(snnmap_hgraph* h)
     }
     h->levels.emplace_back();
     h->extra.emplace_back();
-    SNN_TRY(build_coarse(h, src, h->levels[src].cid, d_V2, src + 1));
+    SNN_TRY(build_coarse(h, src, h->levels[src].cid, d_V2, src + 1, h->match, h->cand, h->cov));
     h->have_matching = false;
     ProfScope prof(h, PS_AFFINITY);
     if (h->mat.level == src) SNN_TRY(mat_descend(h, src));

@@ -237,23 +237,30 @@ __host__ __device__ inline int64_t pow2_ceil(int64_t x)
     return p;
 }
 
-// work[n] = total segment length over n's incidences (one warp per vertex),
-// or -1 when the policy decides n without a histogram
+// work[n] = total segment length over n's incidences, or -1 when the policy
+// decides n without a histogram. A warp tests 32 consecutive vertices at
+// once and sums the segments of the ones to count one at a time, so rounds
+// that evaluate few vertices do not pay a warp per vertex.
 template <class Pol>
 __global__ void __launch_bounds__(256) k_ht_work(Pol pol, int64_t* work)
 {
     int lane = threadIdx.x & 31;
     int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t n = gw; n < pol.V; n += nw) {
-        if (pol.skip((int32_t)n)) {
-            if (lane == 0) work[n] = -1;
-            continue;
+    for (int64_t base = gw * 32; base < pol.V; base += nw * 32) {
+        int64_t n = base + lane;
+        bool sk = n >= pol.V || pol.skip((int32_t)n);
+        if (n < pol.V && sk) work[n] = -1;
+        unsigned todo = __ballot_sync(FULL, !sk);
+        while (todo) {
+            int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            int32_t m = (int32_t)(base + src);
+            int64_t w = 0;
+            for (int64_t i = pol.vb(m) + lane; i < pol.ve(m); i += 32) w += pol.seg_len(i);
+            w = warp_sum(w);
+            if (lane == 0) work[m] = w;
         }
-        int64_t w = 0;
-        for (int64_t i = pol.vb((int32_t)n) + lane; i < pol.ve((int32_t)n); i += 32) w += pol.seg_len(i);
-        w = warp_sum(w);
-        if (lane == 0) work[n] = w;
     }
 }
 
@@ -286,7 +293,9 @@ __global__ void __launch_bounds__(256)
         int64_t work = 0;
         if (n < pol.V) {
             work = workv[n];
-            if (work < 0) {
+            if (work <= 0) {
+                // skipped, or nothing to count: the empty table's result
+                // (no key, zero sums) without a histogram
                 pol.write((int32_t)n, 0, -1, 0, typename Pol::Acc());
             } else {
                 wsum += work;
@@ -894,7 +903,7 @@ Status run_histogram(const Pol& pol, Arena& ar, cudaStream_t s, int64_t* d_cnt, 
     SNN_TRY(ar.alloc(&scap, V));
     SNN_TRY(ar.alloc(&workv, V));
     SNN_CUDA(cudaMemsetAsync(d_cnt, 0, HT_NCNT * sizeof(int64_t), s));
-    SNN_L k_ht_work<Pol><<<grid_for((int64_t)V * 32, 256), 256, 0, s>>>(pol, workv);
+    SNN_L k_ht_work<Pol><<<grid_for(V, 256), 256, 0, s>>>(pol, workv);
     SNN_CUDA(cudaGetLastError());
     SNN_L k_ht_classify<Pol><<<grid_for(V, 256), 256, 0, s>>>(pol, workv, lists, d_cnt, scap, tiers);
     SNN_CUDA(cudaGetLastError());

@@ -208,9 +208,12 @@ Status contract_level(snnmap_hgraph* h);
 // after a contraction of `src`: candidates of src carried to src + 1
 Status aff_carry(snnmap_hgraph* h, int32_t src);
 void aff_carry_free(snnmap_hgraph* h);
-// materializes levels[dst] from resident levels[src] through map (V(src) ids)
+// materializes levels[dst] from resident levels[src] through map (V(src) ids);
+// with the matching that produced map (match, and the candidates and their
+// overlaps), in_count comes from the pairs instead of a pass over the pins
 Status build_coarse(snnmap_hgraph* h, int32_t src, const int32_t* map, const int64_t* d_V2,
-                    int32_t dst);
+                    int32_t dst, const int32_t* match = nullptr, const int32_t* cand = nullptr,
+                    const int32_t* cov = nullptr);
 // rebuilds a released level from the nearest resident level below it
 Status ensure_resident(snnmap_hgraph* h, int32_t level);
 // releases intermediate levels while their memory exceeds the budget

@@ -467,12 +467,14 @@ __global__ void __launch_bounds__(256)
                  const int64_t* __restrict__ savev, const int64_t* __restrict__ Wv,
                  const int32_t* __restrict__ rowid, const int32_t* __restrict__ C,
                  const int32_t* __restrict__ O, int64_t Kp, int32_t K, int32_t omega,
-                 int32_t delta, int32_t phi, int nonpos, int32_t* pto, int64_t* pgain)
+                 int32_t delta, int32_t phi, int nonpos, int32_t* pto, int64_t* pgain,
+                 const int32_t* __restrict__ dirty)
 {
     int lane = threadIdx.x & 31;
     int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t n = gw; n < L.V; n += nw) {
+        if (dirty && !dirty[n]) continue;   // proposal kept from the previous round
         int64_t sv = savev[n];
         if (sv == 0 && !nonpos) {
             if (lane == 0) {
@@ -973,6 +975,57 @@ __global__ void k_ps_combine(Level L, const int32_t* __restrict__ rho,
             }
             ps.vt[n] = 0;
         }
+    }
+}
+
+// The same update on levels refined from connection rows: a vertex's
+// columns of P* are entries of its row (already updated by k_dense_cross;
+// adjacency is a positive entry there, rows being used only when every
+// omega is positive). With more than PSTAR_MAX partitions in P*, every
+// vertex is flagged for a row scan.
+__global__ void k_ps_rows(Level L, const int32_t* __restrict__ rho,
+                          const int64_t* __restrict__ scal, PStar ps, PState st,
+                          const int64_t* __restrict__ savev, const int64_t* __restrict__ Wv,
+                          const int32_t* __restrict__ rowid, const int32_t* __restrict__ C,
+                          const int32_t* __restrict__ O, int64_t Kp, int32_t omega,
+                          int32_t delta, int32_t phi, int nonpos, int32_t* pto, int64_t* pgain,
+                          int32_t* dirty)
+{
+    if (scal[RS_BEST] <= 0) return;
+    bool on = ps.cnt[0] <= PSTAR_MAX;
+    int32_t ns = on ? ps.cnt[0] : 0;
+    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < L.V;
+         n += (int64_t)gridDim.x * blockDim.x) {
+        if (!on) {
+            dirty[n] = 1;
+            continue;
+        }
+        if (dirty[n]) continue;   // moved
+        int64_t ds = savev[n] - ps.save0[n];
+        int32_t q = pto[n];
+        if ((q >= 0 && ps.pslot[q] >= 0) || (!nonpos && q < 0 && ds > 0)) {
+            dirty[n] = 1;
+            continue;
+        }
+        int64_t bs = q >= 0 ? pgain[n] + ds : 0;
+        int32_t bk = q;
+        int64_t r0 = (int64_t)rowid[n] * Kp;
+        int64_t sw = savev[n] - Wv[n];
+        int32_t own = rho[n];
+        for (int sl = 0; sl < ns; sl++) {
+            int32_t p = ps.slots[sl];
+            int64_t c = C[r0 + p];
+            if (p == own || c <= 0) continue;
+            bool feas = st.size[p] + L.vsize[n] <= omega && st.inpins[p] + L.vinpins[n] <= phi &&
+                        st.pincnt[p] + L.vincnt[n] - (int64_t)O[r0 + p] <= delta;
+            if (feas && better(sw + c, p, bs, bk)) {
+                bs = sw + c;
+                bk = p;
+            }
+        }
+        bool prop = bk >= 0 && (bs > 0 || nonpos);
+        pto[n] = prop ? bk : -1;
+        pgain[n] = prop ? bs : 0;
     }
 }
 
@@ -1742,7 +1795,7 @@ static Status refine_round(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* 
         if (V > 0) {
             SNN_L k_dense_best<<<grid_for((int64_t)V * 32, 256), 256, 0, s>>>(
                 L, rho, ps, savev, Wv, D.rowid, D.C, D.O, D.Kp, K, prm.omega, prm.delta, prm.phi,
-                prm.refine_nonpositive, pto, pgain);
+                prm.refine_nonpositive, pto, pgain, inc.dirty);
             SNN_CUDA(cudaGetLastError());
         }
     } else if (h->wide) {
@@ -1867,7 +1920,15 @@ static Status refine_round(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* 
                                                 D.Kp, mvbuf, hl);
         prof.reset(new ProfScope(h, PS_APPLY));
     }
-    if (!dense) {
+    if (dense) {
+        // P* of the enacted prefix; k_ps_rows below decides the next round's
+        // proposals from the rows
+        SNN_CUDA(cudaMemsetAsync(inc.dirty, 0, (size_t)(V > 0 ? V : 1) * 4, s));
+        SNN_L k_ps_slots<<<gm, 256, 0, s>>>(M, mv, h->d_scal, inc.pst, inc.dirty);
+        SNN_CUDA(cudaGetLastError());
+        if (inc.pst.save0 && V > 0)
+            SNN_CUDA(cudaMemcpyAsync(inc.pst.save0, savev, (size_t)V * 8, cudaMemcpyDeviceToDevice, s));
+    } else {
         // vertices the enacted prefix can affect, for the next round
         SNN_CUDA(cudaMemsetAsync(inc.dirty, 0, (size_t)(V > 0 ? V : 1) * 4, s));
         SNN_CUDA(cudaMemsetAsync(inc.pchg, 0, (size_t)(K > 0 ? K : 1), s));
@@ -1925,6 +1986,14 @@ static Status refine_round(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* 
                                                   prm.delta, prm.phi, prm.refine_nonpositive, pto,
                                                   pgain, inc.dirty);
         }
+        SNN_L k_ps_reset<<<gm, 256, 0, s>>>(M, mv, h->d_scal, inc.pst);
+        SNN_CUDA(cudaGetLastError());
+    } else {
+        prof.reset(new ProfScope(h, PS_GAINS));
+        if (V > 0)
+            SNN_L k_ps_rows<<<gv, 256, 0, s>>>(L, rho, h->d_scal, inc.pst, ps, savev, Wv, D.rowid, D.C,
+                                               D.O, D.Kp, prm.omega, prm.delta, prm.phi,
+                                               prm.refine_nonpositive, pto, pgain, inc.dirty);
         SNN_L k_ps_reset<<<gm, 256, 0, s>>>(M, mv, h->d_scal, inc.pst);
         SNN_CUDA(cudaGetLastError());
     }
@@ -2072,7 +2141,13 @@ Status refine_level(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* rho, in
     SNN_CUDA(cudaMallocAsync(&pst.pslot, nk * 4, s));
     SNN_CUDA(cudaMallocAsync(&pst.slots, PSTAR_MAX * 4, s));
     SNN_CUDA(cudaMallocAsync(&pst.cnt, 4 * 4, s));
-    if (!dense_level) {
+    if (dense_level) {
+        // rows levels need only the round-start saves besides the slot map
+        if (cudaMallocAsync(&pst.save0, nv * 8, s) != cudaSuccess) {
+            cudaGetLastError();
+            pst.save0 = nullptr;
+        }
+    } else {
         // the column buffers are optional: without them every round takes
         // the flag rules
         size_t cols = (size_t)PSTAR_MAX * nv;
@@ -2101,7 +2176,7 @@ Status refine_level(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* rho, in
         }
     }
     {
-        int32_t base = pst.colc ? 0 : (1 << 30);
+        int32_t base = (pst.colc || (dense_level && pst.save0)) ? 0 : (1 << 30);
         int32_t hc[4] = {base, 0, base, 0};
         SNN_CUDA(cudaMemcpyAsync(pst.cnt, hc, sizeof(hc), cudaMemcpyHostToDevice, s));
         SNN_TRY(fill_i32(pst.pslot, -1, nk, s));
