@@ -237,30 +237,49 @@ __host__ __device__ inline int64_t pow2_ceil(int64_t x)
     return p;
 }
 
-// work[n] = total segment length over n's incidences, or -1 when the policy
-// decides n without a histogram. A warp tests 32 consecutive vertices at
-// once and sums the segments of the ones to count one at a time, so rounds
-// that evaluate few vertices do not pay a warp per vertex.
+// Work of each vertex: total segment length over its incidences, or -1 when
+// the policy decides it without a histogram. One thread per vertex tests
+// skip() and lists the vertices to count (warp-aggregated appends); then one
+// warp per listed vertex sums its segments. Rounds that evaluate few
+// vertices pay a thread, not a warp, per skipped vertex, while full passes
+// keep a warp per vertex.
 template <class Pol>
-__global__ void __launch_bounds__(256) k_ht_work(Pol pol, int64_t* work)
+__global__ void __launch_bounds__(256) k_ht_skip(Pol pol, int64_t* work, int32_t* todo, int32_t* ntodo)
+{
+    int lane = threadIdx.x & 31;
+    unsigned lt = lanemask_lt();
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < pol.V;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        int64_t n = base + threadIdx.x;
+        bool count = false;
+        if (n < pol.V) {
+            if (pol.skip((int32_t)n)) work[n] = -1;
+            else count = true;
+        }
+        unsigned m = __ballot_sync(FULL, count);
+        if (!m) continue;
+        int leader = __ffs(m) - 1;
+        int32_t pos = 0;
+        if (lane == leader) pos = atomicAdd(ntodo, __popc(m));
+        pos = __shfl_sync(FULL, pos, leader);
+        if (count) todo[pos + __popc(m & lt)] = (int32_t)n;
+    }
+}
+
+template <class Pol>
+__global__ void __launch_bounds__(256)
+    k_ht_work(Pol pol, int64_t* work, const int32_t* __restrict__ todo, const int32_t* __restrict__ ntodo)
 {
     int lane = threadIdx.x & 31;
     int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t base = gw * 32; base < pol.V; base += nw * 32) {
-        int64_t n = base + lane;
-        bool sk = n >= pol.V || pol.skip((int32_t)n);
-        if (n < pol.V && sk) work[n] = -1;
-        unsigned todo = __ballot_sync(FULL, !sk);
-        while (todo) {
-            int src = __ffs(todo) - 1;
-            todo &= todo - 1;
-            int32_t m = (int32_t)(base + src);
-            int64_t w = 0;
-            for (int64_t i = pol.vb(m) + lane; i < pol.ve(m); i += 32) w += pol.seg_len(i);
-            w = warp_sum(w);
-            if (lane == 0) work[m] = w;
-        }
+    int32_t nt = *ntodo;
+    for (int64_t idx = gw; idx < nt; idx += nw) {
+        int32_t n = todo[idx];
+        int64_t w = 0;
+        for (int64_t i = pol.vb(n) + lane; i < pol.ve(n); i += 32) w += pol.seg_len(i);
+        w = warp_sum(w);
+        if (lane == 0) work[n] = w;
     }
 }
 
@@ -903,7 +922,12 @@ Status run_histogram(const Pol& pol, Arena& ar, cudaStream_t s, int64_t* d_cnt, 
     SNN_TRY(ar.alloc(&scap, V));
     SNN_TRY(ar.alloc(&workv, V));
     SNN_CUDA(cudaMemsetAsync(d_cnt, 0, HT_NCNT * sizeof(int64_t), s));
-    SNN_L k_ht_work<Pol><<<grid_for(V, 256), 256, 0, s>>>(pol, workv);
+    int32_t *todo, *ntodo;
+    SNN_TRY(ar.alloc(&todo, V));
+    SNN_TRY(ar.alloc(&ntodo, 1));
+    SNN_CUDA(cudaMemsetAsync(ntodo, 0, sizeof(int32_t), s));
+    SNN_L k_ht_skip<Pol><<<grid_for(V, 256), 256, 0, s>>>(pol, workv, todo, ntodo);
+    SNN_L k_ht_work<Pol><<<grid_for((int64_t)V * 32, 256), 256, 0, s>>>(pol, workv, todo, ntodo);
     SNN_CUDA(cudaGetLastError());
     SNN_L k_ht_classify<Pol><<<grid_for(V, 256), 256, 0, s>>>(pol, workv, lists, d_cnt, scap, tiers);
     SNN_CUDA(cudaGetLastError());
