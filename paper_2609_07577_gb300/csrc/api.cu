@@ -5,6 +5,7 @@
 #include "internal.cuh"
 
 #include <climits>
+#include <cstring>
 #include <mutex>
 #include <new>
 #include <string>
@@ -158,7 +159,9 @@ void snnmap_free(snnmap_hgraph* h)
     if (h->d_scal) cudaFreeAsync(h->d_scal, h->stream);
     cudaStreamSynchronize(h->stream);
     if (h->h_scal) cudaFreeHost(h->h_scal);
+    if (h->h_tier) cudaFreeHost(h->h_tier);
     delete h;
+    snn::pool_handles(-1);
 }
 
 static int snnmap_build_hgraph_impl(const snnmap_params* params, int32_t n_vertices, int32_t n_hedges,
@@ -175,6 +178,7 @@ static int snnmap_build_hgraph_impl(const snnmap_params* params, int32_t n_verti
         return fail(SNNMAP_ERR_INVALID, "d_pins / d_w are not device memory");
     snnmap_hgraph* h = new (std::nothrow) snnmap_hgraph;
     if (!h) return fail(SNNMAP_ERR_OOM, "host allocation failed");
+    snn::pool_handles(1);
     h->prm = *params;
     bind(h, stream);
     cudaGetDevice(&h->device);
@@ -188,11 +192,13 @@ static int snnmap_build_hgraph_impl(const snnmap_params* params, int32_t n_verti
         else h->level_budget = (int64_t)1 << 34;
     }
     cudaError_t e = cudaMallocHost(&h->h_scal, snn::SC_COUNT * sizeof(int64_t));
-    if (e == cudaSuccess) e = cudaMallocAsync(&h->d_scal, snn::SC_COUNT * sizeof(int64_t), h->stream);
-    if (e == cudaSuccess) e = cudaMallocAsync(&h->cand, (size_t)cap * 4, h->stream);
-    if (e == cudaSuccess) e = cudaMallocAsync(&h->cov, (size_t)cap * 4, h->stream);
-    if (e == cudaSuccess) e = cudaMallocAsync(&h->match, (size_t)cap * 4, h->stream);
-    if (e == cudaSuccess) e = cudaMallocAsync(&h->cscore, (size_t)cap * 8, h->stream);
+    if (e == cudaSuccess) e = cudaMallocHost(&h->h_tier, 2 * snn::TIER_SLOTS * sizeof(int64_t));
+    if (e == cudaSuccess) memset(h->h_tier, 0, 2 * snn::TIER_SLOTS * sizeof(int64_t));
+    if (e == cudaSuccess) e = snn::dev_malloc(&h->d_scal, snn::SC_COUNT * sizeof(int64_t), h->stream);
+    if (e == cudaSuccess) e = snn::dev_malloc(&h->cand, (size_t)cap * 4, h->stream);
+    if (e == cudaSuccess) e = snn::dev_malloc(&h->cov, (size_t)cap * 4, h->stream);
+    if (e == cudaSuccess) e = snn::dev_malloc(&h->match, (size_t)cap * 4, h->stream);
+    if (e == cudaSuccess) e = snn::dev_malloc(&h->cscore, (size_t)cap * 8, h->stream);
     if (e != cudaSuccess) {
         snnmap_free(h);
         return fail(e == cudaErrorMemoryAllocation ? SNNMAP_ERR_OOM : SNNMAP_ERR_CUDA,
@@ -217,6 +223,7 @@ static int snnmap_coarsen_level_impl(snnmap_hgraph* h, void* stream, int32_t* n_
     snn::Status st = snn::coarsen_level(h, &nc, &np);
     h->scratch.reset();
     if (!st.ok()) return fail(st);
+    snn::tier_fold(h);
     const snn::Level& L = h->levels.back();
     const snn::LevelExtra& X = h->extra.back();
     h->llog.push_back(snnmap_level_log{L.V, L.E, L.P, nc, np, X.pair_terms, X.n_block,
@@ -320,6 +327,7 @@ static int snnmap_partition_impl(snnmap_hgraph* h, void* stream, int32_t* d_rho_
         snn::Status s1 = snn::coarsen_level(h, &nc, &np);
         h->scratch.reset();
         if (!s1.ok()) return fail(s1);
+        snn::tier_fold(h);
         const snn::Level& L = h->levels.back();
         const snn::LevelExtra& X = h->extra.back();
         h->llog.push_back(snnmap_level_log{L.V, L.E, L.P, nc, np, X.pair_terms, X.n_block,
@@ -337,7 +345,7 @@ static int snnmap_partition_impl(snnmap_hgraph* h, void* stream, int32_t* d_rho_
     for (auto& L : h->levels) st.pins_total += L.P;
     // uncoarsening
     int32_t* tmp = nullptr;
-    cudaError_t e = cudaMallocAsync(&tmp, (size_t)(V0 > 0 ? V0 : 1) * 4, h->stream);
+    cudaError_t e = snn::dev_malloc(&tmp, (size_t)(V0 > 0 ? V0 : 1) * 4, h->stream);
     if (e != cudaSuccess) return fail(SNNMAP_ERR_OOM, cudaGetErrorString(e));
     // rho of the current level lives in `cur`; projection writes `oth`
     int32_t* cur = ((nl - 1) % 2 == 0) ? d_rho_out : tmp;
@@ -444,10 +452,10 @@ static int snnmap_partition_host_impl(const snnmap_params* params, int32_t n_ver
     if (h_offsets[0] != 0 || P < 0) return fail(SNNMAP_ERR_INVALID, "bad offsets");
     int64_t *d_off = nullptr;
     int32_t *d_pins = nullptr, *d_w = nullptr, *d_rho = nullptr;
-    cudaError_t e = cudaMallocAsync(&d_off, ((size_t)n_hedges + 1) * 8, s);
-    if (e == cudaSuccess) e = cudaMallocAsync(&d_pins, (size_t)(P > 0 ? P : 1) * 4, s);
-    if (e == cudaSuccess) e = cudaMallocAsync(&d_w, (size_t)(n_hedges > 0 ? n_hedges : 1) * 4, s);
-    if (e == cudaSuccess) e = cudaMallocAsync(&d_rho, (size_t)(n_vertices > 0 ? n_vertices : 1) * 4, s);
+    cudaError_t e = snn::dev_malloc(&d_off, ((size_t)n_hedges + 1) * 8, s);
+    if (e == cudaSuccess) e = snn::dev_malloc(&d_pins, (size_t)(P > 0 ? P : 1) * 4, s);
+    if (e == cudaSuccess) e = snn::dev_malloc(&d_w, (size_t)(n_hedges > 0 ? n_hedges : 1) * 4, s);
+    if (e == cudaSuccess) e = snn::dev_malloc(&d_rho, (size_t)(n_vertices > 0 ? n_vertices : 1) * 4, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_off, h_offsets, ((size_t)n_hedges + 1) * 8, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && P > 0) e = cudaMemcpyAsync(d_pins, h_pins, (size_t)P * 4, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && n_hedges > 0) e = cudaMemcpyAsync(d_w, h_w, (size_t)n_hedges * 4, cudaMemcpyHostToDevice, s);
@@ -468,6 +476,7 @@ static int snnmap_partition_host_impl(const snnmap_params* params, int32_t n_ver
     cudaFreeAsync(d_w, s);
     cudaFreeAsync(d_rho, s);
     cudaStreamSynchronize(s);
+    snn::pool_handles(0);   // hands the pool back when no handle is live
     g_err = keep;
     return rc;
 }

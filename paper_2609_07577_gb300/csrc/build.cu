@@ -112,11 +112,11 @@ Status level_alloc(snnmap_hgraph* h, Level& L, LevelExtra& X, int32_t V, int32_t
     c.add(&X.seg.list, E);
     c.add(&X.seg.meta, 2 * SEG_NB);
     void* p = nullptr;
-    SNN_CUDA(cudaMallocAsync(&p, c.total, h->stream));
+    SNN_CUDA(dev_malloc(&p, c.total, h->stream));
     c.assign(p);
     L.block = p;
     L.bytes = c.total;
-    if (!L.cid) SNN_CUDA(cudaMallocAsync((void**)&L.cid, (size_t)(V > 0 ? V : 1) * 4, h->stream));
+    if (!L.cid) SNN_CUDA(dev_malloc((void**)&L.cid, (size_t)(V > 0 ? V : 1) * 4, h->stream));
     L.resident = true;
     return Status{};
 }
@@ -254,16 +254,18 @@ __global__ void k_count_deg(const int32_t* __restrict__ pins, int64_t P, int32_t
         atomicAdd(&deg[pins[j]], 1);
 }
 
+// a group of G lanes per hyperedge
+template <int G>
 __global__ void k_csc_fill(const int64_t* __restrict__ hoff, const int32_t* __restrict__ pins,
                            int32_t E, const int64_t* __restrict__ voff, int32_t* cursor,
                            int32_t* vinc)
 {
-    int lane = threadIdx.x & 31;
-    int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int lane = threadIdx.x & (G - 1);
+    int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) / G;
     for (int64_t a = gw; a < E; a += nw) {
         int64_t b = hoff[a], e = hoff[a + 1];
-        for (int64_t j = b + lane; j < e; j += 32) {
+        for (int64_t j = b + lane; j < e; j += G) {
             int32_t q = pins[j];
             int32_t slot = atomicAdd(&cursor[q], 1);
             vinc[voff[q] + slot] = (int32_t)((uint32_t)a | (j == b ? SRC_BIT : 0u));
@@ -289,8 +291,8 @@ Status build_incidence(snnmap_hgraph* h, Level& L)
     }
     SNN_TRY(scan_exclusive_i32_to_i64(deg, L.voff, L.V, L.voff + L.V, ar, s));
     if (L.E > 0) {
-        SNN_L k_csc_fill<<<grid_for((int64_t)L.E * 32, 256), 256, 0, s>>>(L.hoff, L.hpins, L.E, L.voff,
-                                                                    cursor, L.vinc);
+        SNN_HEDGE_LAUNCH(hedge_lanes(L.P, L.E), k_csc_fill, L.E, s, L.hoff, L.hpins, L.E, L.voff,
+                         cursor, L.vinc);
         SNN_CUDA(cudaGetLastError());
     }
     return Status{};

@@ -346,17 +346,39 @@ static Status affinity(snnmap_hgraph* h, Level& L)
     pol.cov = h->cov;
     int64_t* cnt;
     SNN_TRY(h->scratch.alloc(&cnt, HT_NCNT));
+    if (L.V <= 0) SNN_CUDA(cudaMemsetAsync(cnt, 0, HT_NCNT * sizeof(int64_t), h->stream));
     SNN_TRY(run_histogram(pol, h->scratch, h->stream, cnt, h->h_scal + 12, h->d_scal, h->tiers));
-    int64_t hc[HT_NCNT] = {};
-    SNN_CUDA(cudaMemcpyAsync(hc, cnt, HT_NCNT * sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream));
-    SNN_CUDA(cudaStreamSynchronize(h->stream));
-    LevelExtra& X = h->extra.back();
-    X.n_block = (int32_t)(hc[HT_TIER_BLOCK] + hc[HT_TIER_BIG]);
-    X.n_global = (int32_t)hc[HT_TIER_SPLIT];
-    X.carried = 0;
-    X.n_full = (int32_t)hc[HT_CNT_VERTS];
-    X.hist_work = hc[HT_CNT_WORK];
+    // the counters reach the level record after the matching's synchronization
+    SNN_CUDA(cudaMemcpyAsync(h->h_tier, cnt, HT_NCNT * sizeof(int64_t), cudaMemcpyDeviceToHost,
+                             h->stream));
+    h->extra.back().carried = 0;
+    h->tier_level = (int32_t)h->extra.size() - 1;
+    h->tier_form = 1;
     return Status{};
+}
+
+void tier_fold(snnmap_hgraph* h)
+{
+    static_assert(HT_NCNT <= TIER_SLOTS, "counter set larger than its slot in h_tier");
+    int32_t l = h->tier_level;
+    if (l < 0) return;
+    h->tier_level = -1;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess || l >= (int32_t)h->extra.size()) return;
+    LevelExtra& X = h->extra[l];
+    const int64_t* a = h->h_tier;
+    const int64_t* b = h->h_tier + TIER_SLOTS;
+    int64_t blk = a[HT_TIER_BLOCK] + a[HT_TIER_BIG], glb = a[HT_TIER_SPLIT], wk = a[HT_CNT_WORK];
+    int64_t nf = a[HT_CNT_VERTS];
+    if (h->tier_form == 2) {   // carried: new super-nodes' lists, then the full histograms
+        blk += b[HT_TIER_BLOCK] + b[HT_TIER_BIG];
+        glb += b[HT_TIER_SPLIT];
+        wk += b[HT_CNT_WORK];
+        nf = b[HT_CNT_VERTS];
+    }
+    X.n_block = (int32_t)blk;
+    X.n_global = (int32_t)glb;
+    X.n_full = (int32_t)nf;
+    X.hist_work = wk;
 }
 
 
@@ -417,22 +439,33 @@ __global__ void k_ac_prep(int32_t V, const int32_t* __restrict__ cid,
     }
 }
 
-// per hyperedge: its number of new super-nodes; work[0] += (|a| - cnt) cnt
+// per hyperedge: its number of new super-nodes; work[0] += (|a| - cnt) cnt.
+// A group of G lanes per hyperedge; each warp takes 32 / G consecutive
+// hyperedges per step, so the group sums run with the whole warp.
+template <int G>
 __global__ void __launch_bounds__(256)
     k_ac_count(Level L, const uint8_t* __restrict__ kind, int32_t* lcnt, int64_t* work)
 {
-    int lane = threadIdx.x & 31;
-    int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    constexpr int PER = 32 / G;
+    int lane = threadIdx.x & (G - 1);
+    int grp = (threadIdx.x & 31) / G;
+    int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
     int64_t acc = 0;
-    for (int64_t a = gw; a < L.E; a += nw) {
-        int64_t b = L.hoff[a], e = L.hoff[a + 1];
+    for (int64_t base = warp * PER; base < L.E; base += nwarp * PER) {
+        int64_t a = base + grp;
         int c = 0;
-        for (int64_t j = b + lane; j < e; j += 32) c += kind[L.hpins[j]] == AK_NEW;
-        c = warp_sum(c);
-        if (lane == 0) {
+        int64_t len = 0;
+        if (a < L.E) {
+            int64_t b = L.hoff[a], e = L.hoff[a + 1];
+            len = e - b;
+            for (int64_t j = b + lane; j < e; j += G) c += kind[L.hpins[j]] == AK_NEW;
+        }
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) c += __shfl_xor_sync(FULL, c, o);
+        if (lane == 0 && a < L.E) {
             lcnt[a] = c;
-            acc += (e - b - c) * (int64_t)c;
+            acc += (len - c) * (int64_t)c;
         }
     }
     if (lane == 0 && acc) atomicAdd((unsigned long long*)work, (unsigned long long)acc);
@@ -670,11 +703,11 @@ Status aff_carry(snnmap_hgraph* h, int32_t src)
         aff_carry_free(h);
         size_t n = (size_t)(h->cap_v > 0 ? h->cap_v : 1);
         cudaStream_t s = h->stream;
-        bool ok = cudaMallocAsync(&C.cand, n * 4, s) == cudaSuccess &&
-                  cudaMallocAsync(&C.score, n * 8, s) == cudaSuccess &&
-                  cudaMallocAsync(&C.ov, n * 4, s) == cudaSuccess &&
-                  cudaMallocAsync(&C.kind, n, s) == cudaSuccess &&
-                  cudaMallocAsync(&C.full, n, s) == cudaSuccess;
+        bool ok = dev_malloc(&C.cand, n * 4, s) == cudaSuccess &&
+                  dev_malloc(&C.score, n * 8, s) == cudaSuccess &&
+                  dev_malloc(&C.ov, n * 4, s) == cudaSuccess &&
+                  dev_malloc(&C.kind, n, s) == cudaSuccess &&
+                  dev_malloc(&C.full, n, s) == cudaSuccess;
         if (!ok) {
             // no room: the next levels take full histograms
             cudaGetLastError();
@@ -712,7 +745,7 @@ static Status affinity_carried(snnmap_hgraph* h, Level& L, bool* done)
     SNN_CUDA(cudaMemsetAsync(vmin + 2, 0, 2 * sizeof(int32_t), s));
     SNN_CUDA(cudaMemsetAsync(work, 0, 4 * sizeof(int64_t), s));
     SNN_L k_level_min<<<grid_for(L.V, 256), 256, 0, s>>>(L, vmin);
-    if (E > 0) SNN_L k_ac_count<<<grid_for(E * 32, 256), 256, 0, s>>>(L, C.kind, lcnt, work);
+    if (E > 0) SNN_HEDGE_LAUNCH(hedge_lanes(L.P, E), k_ac_count, E, s, L, C.kind, lcnt, work);
     SNN_L k_ac_fullwork<<<grid_for(L.V, 256), 256, 0, s>>>(L, C.kind, work + 1);
     SNN_CUDA(cudaGetLastError());
     SNN_TRY(scan_exclusive_i32_to_i64(lcnt, loff, E, loff + E, ar, s));
@@ -739,7 +772,7 @@ static Status affinity_carried(snnmap_hgraph* h, Level& L, bool* done)
     SNN_CUDA(cudaGetLastError());
     int64_t* cnt;
     SNN_TRY(ar.alloc(&cnt, HT_NCNT));
-    int64_t nb = 0, ng = 0, nf = 0, wk = 0;
+    if (L.V <= 0) SNN_CUDA(cudaMemsetAsync(cnt, 0, HT_NCNT * sizeof(int64_t), s));
     {
         AffNewPol<S> pol;
         pol.L = L;
@@ -757,12 +790,7 @@ static Status affinity_carried(snnmap_hgraph* h, Level& L, bool* done)
         pol.cscore = h->cscore;
         pol.cov = h->cov;
         SNN_TRY(run_histogram(pol, ar, s, cnt, h->h_scal + 12, h->d_scal, h->tiers));
-        int64_t hc[HT_NCNT];
-        SNN_CUDA(cudaMemcpyAsync(hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, s));
-        SNN_CUDA(cudaStreamSynchronize(s));
-        nb += hc[HT_TIER_BLOCK] + hc[HT_TIER_BIG];
-        ng += hc[HT_TIER_SPLIT];
-        wk += hc[HT_CNT_WORK];
+        SNN_CUDA(cudaMemcpyAsync(h->h_tier, cnt, HT_NCNT * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     }
     SNN_L k_ac_check<<<grid_for(L.V, 256), 256, 0, s>>>(L, C, h->prm.omega, h->prm.delta,
                                                         h->prm.phi);
@@ -783,20 +811,12 @@ static Status affinity_carried(snnmap_hgraph* h, Level& L, bool* done)
         pol.cscore = h->cscore;
         pol.cov = h->cov;
         SNN_TRY(run_histogram(pol, ar, s, cnt, h->h_scal + 12, h->d_scal, h->tiers));
-        int64_t hc[HT_NCNT];
-        SNN_CUDA(cudaMemcpyAsync(hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, s));
-        SNN_CUDA(cudaStreamSynchronize(s));
-        nb += hc[HT_TIER_BLOCK] + hc[HT_TIER_BIG];
-        ng += hc[HT_TIER_SPLIT];
-        wk += hc[HT_CNT_WORK];
-        nf += hc[HT_CNT_VERTS];
+        SNN_CUDA(cudaMemcpyAsync(h->h_tier + TIER_SLOTS, cnt, HT_NCNT * sizeof(int64_t),
+                                 cudaMemcpyDeviceToHost, s));
     }
-    LevelExtra& X = h->extra.back();
-    X.n_block = (int32_t)nb;
-    X.n_global = (int32_t)ng;
-    X.carried = 1;
-    X.n_full = (int32_t)nf;
-    X.hist_work = wk;
+    h->extra.back().carried = 1;
+    h->tier_level = (int32_t)h->extra.size() - 1;
+    h->tier_form = 2;
     *done = true;
     return Status{};
 }

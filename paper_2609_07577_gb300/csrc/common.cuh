@@ -144,6 +144,22 @@ struct Carver {
     }
 };
 
+// Device memory of a handle: stream-ordered allocations from one memory pool
+// per device that keeps freed blocks for reuse across stream
+// synchronizations. (The default pool hands unused memory back to the driver
+// at every synchronization, so each level's and each refinement round's
+// arrays would be mapped afresh.) The pool is trimmed to nothing when the
+// last live handle is freed (pool_handles(-1) returns 0).
+cudaError_t dev_malloc(void** p, size_t bytes, cudaStream_t s);
+template <typename T>
+inline cudaError_t dev_malloc(T** p, size_t bytes, cudaStream_t s)
+{
+    return dev_malloc((void**)p, bytes, s);
+}
+// adds `delta` (+1 at handle creation, -1 at its release) to the count of
+// live handles and returns the new count; at 0 the pools are trimmed
+int pool_handles(int delta);
+
 // Bump allocator for temporaries of one step. Memory stays reserved across
 // steps and grows (stream-ordered) when a step needs more.
 struct Arena {
@@ -209,5 +225,36 @@ inline int grid_for(int64_t n, int threads, int cap = 152 * 32)
     int64_t g = ceil_div(n > 0 ? n : 1, threads);
     return (int)(g < cap ? g : cap);
 }
+
+// Lanes per hyperedge for the kernels that spread one hyperedge's pins over a
+// group of lanes: the mean hyperedge size (pins per hyperedge) rounded up to
+// a power of two in [4, 32], so that short hyperedges do not leave most of a
+// warp idle. Groups are aligned within their warp.
+inline int hedge_lanes(int64_t P, int64_t E)
+{
+    int64_t m = E > 0 ? (P + E - 1) / E : 32;
+    int g = 4;
+    while (g < 32 && g < m) g <<= 1;
+    return g;
+}
+
+// launches kern<G> (G of 4, 8, 16, 32 lanes per hyperedge) with enough
+// threads for n hyperedges
+#define SNN_HEDGE_LAUNCH(G, kern, n, s, ...)                                                     \
+    do {                                                                                         \
+        switch (G) {                                                                             \
+        case 4:                                                                                  \
+            SNN_L kern<4><<<::snn::grid_for((int64_t)(n) * 4, 256), 256, 0, s>>>(__VA_ARGS__);     \
+            break;                                                                               \
+        case 8:                                                                                  \
+            SNN_L kern<8><<<::snn::grid_for((int64_t)(n) * 8, 256), 256, 0, s>>>(__VA_ARGS__);     \
+            break;                                                                               \
+        case 16:                                                                                 \
+            SNN_L kern<16><<<::snn::grid_for((int64_t)(n) * 16, 256), 256, 0, s>>>(__VA_ARGS__);   \
+            break;                                                                               \
+        default:                                                                                 \
+            SNN_L kern<32><<<::snn::grid_for((int64_t)(n) * 32, 256), 256, 0, s>>>(__VA_ARGS__);   \
+        }                                                                                        \
+    } while (0)
 
 }  // namespace snn

@@ -270,6 +270,8 @@ __global__ void k_dedup_accum(int32_t E, const uint32_t* __restrict__ vals,
     }
 }
 
+// a group of G lanes per hyperedge
+template <int G>
 __global__ void k_dedup_emit(int32_t E, const uint32_t* __restrict__ vals,
                              const int32_t* __restrict__ rep, const int32_t* __restrict__ gid,
                              const int64_t* __restrict__ hoff, const int32_t* __restrict__ tpins,
@@ -277,16 +279,16 @@ __global__ void k_dedup_emit(int32_t E, const uint32_t* __restrict__ vals,
                              const int64_t* __restrict__ tw, const int32_t* __restrict__ tk,
                              const int64_t* __restrict__ newoff, Level N)
 {
-    int lane = threadIdx.x & 31;
-    int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int lane = threadIdx.x & (G - 1);
+    int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) / G;
     for (int64_t i = gw; i < E; i += nw) {
         if (rep[i] != (int32_t)i) continue;
         int32_t a = (int32_t)vals[i];
         int32_t g = gid[i];
         int64_t dst = newoff[g], src = hoff[a];
         int32_t len = tlen[a];
-        for (int32_t j = lane; j < len; j += 32) N.hpins[dst + j] = tpins[src + j];
+        for (int32_t j = lane; j < len; j += G) N.hpins[dst + j] = tpins[src + j];
         if (lane == 0) {
             N.hoff[g] = dst;
             N.hsd[g] = tsd[a];
@@ -405,8 +407,8 @@ Status build_coarse(snnmap_hgraph* h, int32_t src, const int32_t* map, const int
         SNN_CUDA(cudaGetLastError());
     }
     if (E > 0) {
-        SNN_L k_dedup_emit<<<grid_for((int64_t)E * 32, 256), 256, 0, s>>>(
-            E, vals, rep, gid, L.hoff, tpins, tlen, tsd, tw, tk, newoff, N);
+        SNN_HEDGE_LAUNCH(hedge_lanes(L.P, L.E), k_dedup_emit, E, s, E, vals, rep, gid, L.hoff, tpins,
+                         tlen, tsd, tw, tk, newoff, N);
         SNN_CUDA(cudaGetLastError());
     }
     SNN_L k_set_off_end<<<1, 1, 0, s>>>(N.hoff, E2, P2);
@@ -549,11 +551,11 @@ Status emit_gp(snnmap_hgraph* h, int32_t K, const int32_t* rho)
     int32_t E2 = (int32_t)(h->h_scal[SC_B] & 0xffffffff);
     int64_t P2 = h->h_scal[SC_C];
     GpOut& G = h->gp;
-    SNN_CUDA(cudaMallocAsync(&G.hoff, ((size_t)E2 + 1) * 8, s));
-    SNN_CUDA(cudaMallocAsync(&G.hpins, (size_t)(P2 > 0 ? P2 : 1) * 4, s));
-    SNN_CUDA(cudaMallocAsync(&G.eta, (size_t)(E2 > 0 ? E2 : 1) * 8, s));
-    SNN_CUDA(cudaMallocAsync(&G.axons, (size_t)(E2 > 0 ? E2 : 1) * 4, s));
-    SNN_CUDA(cudaMallocAsync(&G.hsd, (size_t)(E2 > 0 ? E2 : 1), s));
+    SNN_CUDA(dev_malloc(&G.hoff, ((size_t)E2 + 1) * 8, s));
+    SNN_CUDA(dev_malloc(&G.hpins, (size_t)(P2 > 0 ? P2 : 1) * 4, s));
+    SNN_CUDA(dev_malloc(&G.eta, (size_t)(E2 > 0 ? E2 : 1) * 8, s));
+    SNN_CUDA(dev_malloc(&G.axons, (size_t)(E2 > 0 ? E2 : 1) * 4, s));
+    SNN_CUDA(dev_malloc(&G.hsd, (size_t)(E2 > 0 ? E2 : 1), s));
     G.E = E2;
     G.P = P2;
     G.K = K;
@@ -565,8 +567,8 @@ Status emit_gp(snnmap_hgraph* h, int32_t K, const int32_t* rho)
     N.hw = G.eta;
     N.hk = G.axons;
     if (E > 0) {
-        SNN_L k_dedup_emit<<<grid_for((int64_t)E * 32, 256), 256, 0, s>>>(
-            E, vals, rep, gid, L.hoff, tpins, tlen, tsd, tw, tk, newoff, N);
+        SNN_HEDGE_LAUNCH(hedge_lanes(L.P, L.E), k_dedup_emit, E, s, E, vals, rep, gid, L.hoff, tpins,
+                         tlen, tsd, tw, tk, newoff, N);
         SNN_CUDA(cudaGetLastError());
     }
     SNN_L k_set_off_end<<<1, 1, 0, s>>>(G.hoff, E2, P2);

@@ -113,6 +113,12 @@ struct snnmap_hgraph {
     snn::Arena scratch;
     int64_t* d_scal = nullptr;   // SC_COUNT device slots
     int64_t* h_scal = nullptr;   // pinned mirror
+    // pinned: the counters of a level's neighbour histograms (two sets for the
+    // carried form), copied without a wait and folded into the level's extra
+    // record once the stream has been synchronized (tier_fold)
+    int64_t* h_tier = nullptr;
+    int32_t tier_level = -1;     // level whose counters are in flight, else -1
+    int32_t tier_form = 0;       // 1 full histogram, 2 carried form
     // results of the last coarsening step (for the current coarsest level)
     int32_t* cand = nullptr;
     int64_t* cscore = nullptr;
@@ -167,6 +173,11 @@ void prof_release(snnmap_hgraph* h);
 
 // text of snnmap_last_error for the calling thread (api.cu)
 void set_last_error(const std::string& msg);
+
+// folds the histogram counters in flight into their level's extra record
+// (synchronizes the handle's stream first)
+void tier_fold(snnmap_hgraph* h);
+constexpr int TIER_SLOTS = 16;   // int64 per counter set in h_tier (two sets)
 
 // scalars: copy the SC_COUNT slots device->host and synchronize the stream
 Status read_scalars(snnmap_hgraph* h);

@@ -7,12 +7,76 @@
 
 #include <atomic>
 #include <climits>
+#include <mutex>
 
 namespace snn {
 
 static std::atomic<int64_t> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
+// ---------------------------------------------------------------------------
+// Pool-backed device allocations
+
+namespace {
+constexpr int kMaxPoolDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[kMaxPoolDevices] = {};
+int g_live_handles = 0;
+}  // namespace
+
+static cudaError_t pool_of(int dev, cudaMemPool_t* out)
+{
+    if (dev < 0 || dev >= kMaxPoolDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pools[dev]) {
+        cudaMemPoolProps pr{};
+        pr.allocType = cudaMemAllocationTypePinned;
+        pr.handleTypes = cudaMemHandleTypeNone;
+        pr.location.type = cudaMemLocationTypeDevice;
+        pr.location.id = dev;
+        cudaMemPool_t p = nullptr;
+        cudaError_t e = cudaMemPoolCreate(&p, &pr);
+        if (e != cudaSuccess) return e;
+        uint64_t keep = UINT64_MAX;
+        e = cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+        // handles on other streams (the batched and served forms) reuse
+        // freed blocks only once their frees are known complete: no wait is
+        // ever inserted between their streams
+        int no = 0;
+        if (e == cudaSuccess)
+            e = cudaMemPoolSetAttribute(p, cudaMemPoolReuseAllowInternalDependencies, &no);
+        if (e != cudaSuccess) {
+            cudaMemPoolDestroy(p);
+            return e;
+        }
+        g_pools[dev] = p;
+    }
+    *out = g_pools[dev];
+    return cudaSuccess;
+}
+
+cudaError_t dev_malloc(void** p, size_t bytes, cudaStream_t s)
+{
+    int dev = -1;
+    cudaError_t e = cudaStreamGetDevice(s, &dev);
+    if (e != cudaSuccess) return e;
+    cudaMemPool_t pool = nullptr;
+    e = pool_of(dev, &pool);
+    if (e != cudaSuccess) return e;
+    return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
+
+int pool_handles(int delta)
+{
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    g_live_handles += delta;
+    if (g_live_handles < 0) g_live_handles = 0;
+    if (g_live_handles == 0)
+        for (cudaMemPool_t p : g_pools)
+            if (p) cudaMemPoolTrimTo(p, 0);
+    return g_live_handles;
+}
 
 // ---------------------------------------------------------------------------
 // Arena
@@ -22,7 +86,7 @@ Status Arena::reserve(size_t bytes)
     if (!chunks.empty() && sizes.back() >= bytes && chunks.size() == 1) return Status{};
     release();
     void* p = nullptr;
-    SNN_CUDA(cudaMallocAsync(&p, bytes, stream));
+    SNN_CUDA(dev_malloc(&p, bytes, stream));
     chunks.push_back(p);
     sizes.push_back(bytes);
     used = 0;
@@ -38,7 +102,7 @@ Status Arena::take(size_t bytes, void** out)
         if (chunks.empty() && peak > want) want = peak;
         if (want < ((size_t)64 << 20)) want = (size_t)64 << 20;
         void* p = nullptr;
-        SNN_CUDA(cudaMallocAsync(&p, want, stream));
+        SNN_CUDA(dev_malloc(&p, want, stream));
         chunks.push_back(p);
         sizes.push_back(want);
         used = 0;
@@ -58,7 +122,7 @@ void Arena::reset()
         sizes.clear();
         void* p = nullptr;
         size_t want = peak + ((size_t)16 << 20);
-        if (cudaMallocAsync(&p, want, stream) == cudaSuccess) {
+        if (dev_malloc(&p, want, stream) == cudaSuccess) {
             chunks.push_back(p);
             sizes.push_back(want);
         }

@@ -247,19 +247,20 @@ __device__ __forceinline__ void lookup_count(const PinCounts& pc, int64_t b, int
 // save(n) = omega of incident hyperedges in which n is the last pin of its
 // partition, W(n) = omega of all incident hyperedges. A move of n gains
 // save(n) - W(n) + conn(n, p) <= save(n), so a vertex with save(n) = 0
-// never proposes. One warp per hyperedge, lanes over its pins (both arrays
-// cleared before).
+// never proposes. A group of G lanes per hyperedge, lanes over its pins
+// (both arrays cleared before).
+template <int G>
 __global__ void __launch_bounds__(256)
     k_save(Level L, PinCounts pc, const int32_t* __restrict__ rho, int64_t* savev, int64_t* Wv)
 {
-    int lane = threadIdx.x & 31;
-    int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int lane = threadIdx.x & (G - 1);
+    int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) / G;
     for (int64_t a = gw; a < L.E; a += nw) {
         int64_t b = L.hoff[a], e = L.hoff[a + 1];
         int32_t lam = pc.lam[a];
         unsigned long long w = (unsigned long long)L.hw[a];
-        for (int64_t j = b + lane; j < e; j += 32) {
+        for (int64_t j = b + lane; j < e; j += G) {
             int32_t x = L.hpins[j];
             atomicAdd((unsigned long long*)&Wv[x], w);
             int32_t c, d;
@@ -1476,11 +1477,11 @@ Status dense_open(snnmap_hgraph* h, int32_t K, int64_t rows)
     D.K = K;
     D.Kp = ((int64_t)K + 3) & ~(int64_t)3;
     D.cap = rows > 0 ? rows : 1;
-    SNN_CUDA(cudaMallocAsync(&D.C, (size_t)(D.cap * D.Kp) * 4, s));
-    SNN_CUDA(cudaMallocAsync(&D.O, (size_t)(D.cap * D.Kp) * 4, s));
-    SNN_CUDA(cudaMallocAsync(&D.rowid, (size_t)D.cap * 4, s));
-    SNN_CUDA(cudaMallocAsync(&D.rowid2, (size_t)D.cap * 4, s));
-    SNN_CUDA(cudaMallocAsync(&D.fresh, (size_t)D.cap * 4, s));
+    SNN_CUDA(dev_malloc(&D.C, (size_t)(D.cap * D.Kp) * 4, s));
+    SNN_CUDA(dev_malloc(&D.O, (size_t)(D.cap * D.Kp) * 4, s));
+    SNN_CUDA(dev_malloc(&D.rowid, (size_t)D.cap * 4, s));
+    SNN_CUDA(dev_malloc(&D.rowid2, (size_t)D.cap * 4, s));
+    SNN_CUDA(dev_malloc(&D.fresh, (size_t)D.cap * 4, s));
     D.level = -1;
     D.pending = false;
     return Status{};
@@ -1786,7 +1787,7 @@ static Status refine_round(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* 
         SNN_CUDA(cudaMemsetAsync(savev, 0, (size_t)(V > 0 ? V : 1) * 8, s));
         SNN_CUDA(cudaMemsetAsync(Wv, 0, (size_t)(V > 0 ? V : 1) * 8, s));
         if (L.E > 0) {
-            SNN_L k_save<<<grid_for((int64_t)L.E * 32, 256), 256, 0, s>>>(L, pc, rho, savev, Wv);
+            SNN_HEDGE_LAUNCH(hedge_lanes(L.P, L.E), k_save, L.E, s, L, pc, rho, savev, Wv);
             SNN_CUDA(cudaGetLastError());
         }
     }
@@ -2061,9 +2062,9 @@ Status carry_open(snnmap_hgraph* h, int64_t cap)
     Carry& C = h->carry;
     size_t n = (size_t)(cap > 0 ? cap : 1);
     for (int b = 0; b < 2; b++) {
-        SNN_CUDA(cudaMallocAsync(&C.pto[b], n * 4, h->stream));
-        SNN_CUDA(cudaMallocAsync(&C.pgain[b], n * 8, h->stream));
-        SNN_CUDA(cudaMallocAsync(&C.dirty[b], n * 4, h->stream));
+        SNN_CUDA(dev_malloc(&C.pto[b], n * 4, h->stream));
+        SNN_CUDA(dev_malloc(&C.pgain[b], n * 8, h->stream));
+        SNN_CUDA(dev_malloc(&C.dirty[b], n * 4, h->stream));
     }
     C.cap = cap;
     C.level = -1;
@@ -2092,7 +2093,7 @@ Status refine_level(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* rho, in
     const bool dense_level = h->dense.C && h->dense.level == level;
     const bool use_carry = CA.pto[0] && L.V <= CA.cap;
     bool inherited = false;
-    SNN_CUDA(cudaMallocAsync(&moveidx, nv * sizeof(int32_t), s));
+    SNN_CUDA(dev_malloc(&moveidx, nv * sizeof(int32_t), s));
     if (use_carry) {
         int nb = 1 - CA.cur;
         inc.pto = CA.pto[nb];
@@ -2113,37 +2114,37 @@ Status refine_level(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* rho, in
         CA.cur = nb;
         CA.level = -1;
     } else {
-        SNN_CUDA(cudaMallocAsync(&inc.pto, nv * 4, s));
-        SNN_CUDA(cudaMallocAsync(&inc.pgain, nv * 8, s));
-        SNN_CUDA(cudaMallocAsync(&inc.dirty, nv * 4, s));
+        SNN_CUDA(dev_malloc(&inc.pto, nv * 4, s));
+        SNN_CUDA(dev_malloc(&inc.pgain, nv * 8, s));
+        SNN_CUDA(dev_malloc(&inc.dirty, nv * 4, s));
     }
-    SNN_CUDA(cudaMallocAsync(&inc.pchg, nk, s));
-    SNN_CUDA(cudaMallocAsync(&inc.prel, nk, s));
-    SNN_CUDA(cudaMallocAsync(&inc.vmax, 3 * 4, s));
+    SNN_CUDA(dev_malloc(&inc.pchg, nk, s));
+    SNN_CUDA(dev_malloc(&inc.prel, nk, s));
+    SNN_CUDA(dev_malloc(&inc.vmax, 3 * 4, s));
     size_t np = (size_t)(L.P > 0 ? L.P : 1), ne = (size_t)(L.E > 0 ? L.E : 1);
-    SNN_CUDA(cudaMallocAsync(&inc.pc.p, np * 4, s));
-    SNN_CUDA(cudaMallocAsync(&inc.pc.cnt, np * 4, s));
-    SNN_CUDA(cudaMallocAsync(&inc.pc.dcnt, np * 4, s));
-    SNN_CUDA(cudaMallocAsync(&inc.pc.lam, ne * 4, s));
-    SNN_CUDA(cudaMallocAsync(&inc.ps.size, nk * 8, s));
-    SNN_CUDA(cudaMallocAsync(&inc.ps.inpins, nk * 8, s));
-    SNN_CUDA(cudaMallocAsync(&inc.ps.pincnt, nk * 8, s));
-    SNN_CUDA(cudaMallocAsync(&inc.costv, 8, s));
-    SNN_CUDA(cudaMallocAsync(&inc.savev, nv * 8, s));
-    SNN_CUDA(cudaMallocAsync(&inc.Wv, nv * 8, s));
-    SNN_CUDA(cudaMallocAsync(&inc.hdirty, ne * 4, s));
-    SNN_CUDA(cudaMallocAsync(&inc.hmark, ne * 4, s));
+    SNN_CUDA(dev_malloc(&inc.pc.p, np * 4, s));
+    SNN_CUDA(dev_malloc(&inc.pc.cnt, np * 4, s));
+    SNN_CUDA(dev_malloc(&inc.pc.dcnt, np * 4, s));
+    SNN_CUDA(dev_malloc(&inc.pc.lam, ne * 4, s));
+    SNN_CUDA(dev_malloc(&inc.ps.size, nk * 8, s));
+    SNN_CUDA(dev_malloc(&inc.ps.inpins, nk * 8, s));
+    SNN_CUDA(dev_malloc(&inc.ps.pincnt, nk * 8, s));
+    SNN_CUDA(dev_malloc(&inc.costv, 8, s));
+    SNN_CUDA(dev_malloc(&inc.savev, nv * 8, s));
+    SNN_CUDA(dev_malloc(&inc.Wv, nv * 8, s));
+    SNN_CUDA(dev_malloc(&inc.hdirty, ne * 4, s));
+    SNN_CUDA(dev_malloc(&inc.hmark, ne * 4, s));
     SNN_CUDA(cudaMemsetAsync(inc.hdirty, 0, ne * 4, s));
     SNN_CUDA(cudaMemsetAsync(inc.hmark, 0, ne * 4, s));
-    SNN_CUDA(cudaMallocAsync(&inc.hlist, ne * 4, s));
-    SNN_CUDA(cudaMallocAsync(&inc.hmeta, 2 * SEG_NB * 4, s));
+    SNN_CUDA(dev_malloc(&inc.hlist, ne * 4, s));
+    SNN_CUDA(dev_malloc(&inc.hmeta, 2 * SEG_NB * 4, s));
     PStar& pst = inc.pst;
-    SNN_CUDA(cudaMallocAsync(&pst.pslot, nk * 4, s));
-    SNN_CUDA(cudaMallocAsync(&pst.slots, PSTAR_MAX * 4, s));
-    SNN_CUDA(cudaMallocAsync(&pst.cnt, 4 * 4, s));
+    SNN_CUDA(dev_malloc(&pst.pslot, nk * 4, s));
+    SNN_CUDA(dev_malloc(&pst.slots, PSTAR_MAX * 4, s));
+    SNN_CUDA(dev_malloc(&pst.cnt, 4 * 4, s));
     if (dense_level) {
         // rows levels need only the round-start saves besides the slot map
-        if (cudaMallocAsync(&pst.save0, nv * 8, s) != cudaSuccess) {
+        if (dev_malloc(&pst.save0, nv * 8, s) != cudaSuccess) {
             cudaGetLastError();
             pst.save0 = nullptr;
         }
@@ -2151,12 +2152,12 @@ Status refine_level(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* rho, in
         // the column buffers are optional: without them every round takes
         // the flag rules
         size_t cols = (size_t)PSTAR_MAX * nv;
-        bool ok = cudaMallocAsync(&pst.hmask, ne * 4, s) == cudaSuccess &&
-                  cudaMallocAsync(&pst.hl, ne * 4, s) == cudaSuccess &&
-                  cudaMallocAsync(&pst.colc, cols * 8, s) == cudaSuccess &&
-                  cudaMallocAsync(&pst.colo, cols * 4, s) == cudaSuccess &&
-                  cudaMallocAsync(&pst.vt, nv * 4, s) == cudaSuccess &&
-                  cudaMallocAsync(&pst.save0, nv * 8, s) == cudaSuccess;
+        bool ok = dev_malloc(&pst.hmask, ne * 4, s) == cudaSuccess &&
+                  dev_malloc(&pst.hl, ne * 4, s) == cudaSuccess &&
+                  dev_malloc(&pst.colc, cols * 8, s) == cudaSuccess &&
+                  dev_malloc(&pst.colo, cols * 4, s) == cudaSuccess &&
+                  dev_malloc(&pst.vt, nv * 4, s) == cudaSuccess &&
+                  dev_malloc(&pst.save0, nv * 8, s) == cudaSuccess;
         if (!ok) {
             cudaGetLastError();
             for (void* p : {(void*)pst.hmask, (void*)pst.hl, (void*)pst.colc, (void*)pst.colo,

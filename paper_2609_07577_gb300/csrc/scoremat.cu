@@ -263,10 +263,10 @@ Status mat_affinity(snnmap_hgraph* h, int32_t level, bool* done)
         if (!mat_fits(h, level)) return Status{};
         int64_t Vs = ((int64_t)L.V + 3) & ~(int64_t)3;
         size_t bytes = (size_t)(Vs * Vs) * 4;
-        cudaError_t e = cudaMallocAsync(&M.S, bytes, s);
-        if (e == cudaSuccess) e = cudaMallocAsync(&M.OV, bytes, s);
-        if (e == cudaSuccess) e = cudaMallocAsync(&M.S2, bytes, s);
-        if (e == cudaSuccess) e = cudaMallocAsync(&M.OV2, bytes, s);
+        cudaError_t e = dev_malloc(&M.S, bytes, s);
+        if (e == cudaSuccess) e = dev_malloc(&M.OV, bytes, s);
+        if (e == cudaSuccess) e = dev_malloc(&M.S2, bytes, s);
+        if (e == cudaSuccess) e = dev_malloc(&M.OV2, bytes, s);
         if (e != cudaSuccess) {
             // no room: this level and the next ones use histograms
             cudaGetLastError();

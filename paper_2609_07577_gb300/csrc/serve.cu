@@ -148,10 +148,10 @@ void snnmap_server::run(Ticket* t, int slot)
             msg = "bad offsets";
         } else {
             in_bytes = input_bytes(V, E, P);
-            cudaError_t e = cudaMallocAsync(&d_off, (size_t)(E + 1) * 8, s);
-            if (e == cudaSuccess) e = cudaMallocAsync(&d_pins, (size_t)(P > 0 ? P : 1) * 4, s);
-            if (e == cudaSuccess) e = cudaMallocAsync(&d_w, (size_t)(E > 0 ? E : 1) * 4, s);
-            if (e == cudaSuccess) e = cudaMallocAsync(&d_rho, (size_t)(V > 0 ? V : 1) * 4, s);
+            cudaError_t e = snn::dev_malloc(&d_off, (size_t)(E + 1) * 8, s);
+            if (e == cudaSuccess) e = snn::dev_malloc(&d_pins, (size_t)(P > 0 ? P : 1) * 4, s);
+            if (e == cudaSuccess) e = snn::dev_malloc(&d_w, (size_t)(E > 0 ? E : 1) * 4, s);
+            if (e == cudaSuccess) e = snn::dev_malloc(&d_rho, (size_t)(V > 0 ? V : 1) * 4, s);
             if (e == cudaSuccess) e = cudaMemcpyAsync(d_off, off, (size_t)(E + 1) * 8, cudaMemcpyHostToDevice, s);
             if (e == cudaSuccess && P > 0)
                 e = cudaMemcpyAsync(d_pins, pins, (size_t)P * 4, cudaMemcpyHostToDevice, s);
@@ -455,8 +455,12 @@ int snnmap_serve_destroy(snnmap_server* s)
         if (kv.second->h) snnmap_free(kv.second->h);
         delete kv.second;
     }
-    for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
+    for (cudaStream_t st : s->streams) {
+        cudaStreamSynchronize(st);
+        cudaStreamDestroy(st);
+    }
     delete s;
+    snn::pool_handles(0);   // hands the pool back when no handle is live
     return SNNMAP_OK;
 }
 
