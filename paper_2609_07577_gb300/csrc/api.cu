@@ -364,7 +364,7 @@ static int snnmap_partition_impl(snnmap_hgraph* h, void* stream, int32_t* d_rho_
     int32_t lb = nl;
     {
         int64_t rb = snn::dense_row_budget(h);
-        int64_t per = ((((int64_t)K + 3) & ~(int64_t)3) * 8 + 12);
+        int64_t per = ((((int64_t)K + 3) & ~(int64_t)3) * 8 + 20);
         if (rb > 0 && !h->wide && !h->wzero && h->wsum <= INT32_MAX)
             for (int32_t l = nl - 1; l >= 0 && (int64_t)h->levels[l].V * per <= rb; l--) lb = l;
         if (lb < nl && !snn::dense_open(h, K, h->levels[lb].V).ok()) {

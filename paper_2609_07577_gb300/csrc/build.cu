@@ -124,7 +124,7 @@ Status level_alloc(snnmap_hgraph* h, Level& L, LevelExtra& X, int32_t V, int32_t
 int64_t held_bytes(const snnmap_hgraph* h)
 {
     int64_t t = (int64_t)h->scratch.held() + (int64_t)h->cap_v * 20;
-    if (h->dense.C) t += h->dense.cap * (h->dense.Kp * 8 + 12);
+    if (h->dense.C) t += h->dense.cap * (h->dense.Kp * 8 + 20);
     if (h->mat.S) t += h->mat.cap * 16;
     for (auto& L : h->levels) t += (int64_t)L.bytes + 4 * (int64_t)L.V;
     return t;

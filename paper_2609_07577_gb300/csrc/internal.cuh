@@ -49,6 +49,11 @@ struct DenseRows {
     int32_t* rowid = nullptr;
     int32_t* rowid2 = nullptr;
     int32_t* fresh = nullptr;
+    // per row: bit c set when entries [c cw, (c + 1) cw) of its C row may be
+    // nonzero (set wherever an entry becomes nonzero, cleared with the row);
+    // cw is the smallest power of two >= 32 giving at most 64 chunks
+    unsigned long long* M = nullptr;
+    int32_t cw = 32;
     int32_t level = -1;       // level the rows describe
     bool pending = false;     // fresh rows of this level not computed yet
 };

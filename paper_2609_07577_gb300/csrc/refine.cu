@@ -421,6 +421,8 @@ struct RowPol {
     int32_t* C;
     int32_t* O;
     int64_t Kp;
+    unsigned long long* M;
+    int32_t cw;
 
     __device__ bool skip(int32_t n) const { return fresh[n] == 0; }
     __device__ int64_t vb(int32_t n) const { return L.voff[n]; }
@@ -453,23 +455,27 @@ struct RowPol {
     __device__ void consider(int32_t n, int32_t p, int64_t conn, uint32_t o, const Acc&, int64_t&,
                              int32_t&, uint32_t&) const
     {
-        int64_t r = (int64_t)rowid[n] * Kp + p;
+        int32_t row = rowid[n];
+        int64_t r = (int64_t)row * Kp + p;
         C[r] = (int32_t)conn;
         O[r] = (int32_t)o;
+        atomicOr(&M[row], 1ull << (p / cw));
     }
     __device__ void write(int32_t, int64_t, int32_t, uint32_t, const Acc&) const {}
 };
 
 // best move per vertex from its row: largest gain = C - (W - save) over
 // partitions p != rho(n) that can take n, ties to the lower p; proposed if
-// positive
+// positive. Only the chunks of the row that the mask M marks are read (an
+// entry outside them is 0, and a partition with conn 0 is never taken);
+// each lane still visits its partitions in increasing order.
 __global__ void __launch_bounds__(256)
     k_dense_best(Level L, const int32_t* __restrict__ rho, PState ps,
                  const int64_t* __restrict__ savev, const int64_t* __restrict__ Wv,
                  const int32_t* __restrict__ rowid, const int32_t* __restrict__ C,
-                 const int32_t* __restrict__ O, int64_t Kp, int32_t K, int32_t omega,
-                 int32_t delta, int32_t phi, int nonpos, int32_t* pto, int64_t* pgain,
-                 const int32_t* __restrict__ dirty)
+                 const int32_t* __restrict__ O, const unsigned long long* __restrict__ M,
+                 int32_t cw, int64_t Kp, int32_t K, int32_t omega, int32_t delta, int32_t phi,
+                 int nonpos, int32_t* pto, int64_t* pgain, const int32_t* __restrict__ dirty)
 {
     int lane = threadIdx.x & 31;
     int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -487,24 +493,34 @@ __global__ void __launch_bounds__(256)
         int64_t T = Wv[n] - sv;
         int32_t own = rho[n];
         int64_t sz = L.vsize[n], ip = L.vinpins[n], ic = L.vincnt[n];
-        int64_t r0 = (int64_t)rowid[n] * Kp;
+        int32_t rw = rowid[n];
+        int64_t r0 = (int64_t)rw * Kp;
         const int4* row = reinterpret_cast<const int4*>(C + r0);
         int64_t bs = 0;
         int32_t bk = -1;
-        for (int64_t q = lane; 4 * q < K; q += 32) {
-            int4 c4 = row[q];
-            int cv[4] = {c4.x, c4.y, c4.z, c4.w};
+        const int64_t nq = ((int64_t)K + 3) >> 2;
+        unsigned long long msk = M[rw];   // the same word in every lane
+        while (msk) {
+            int c = __ffsll((long long)msk) - 1;
+            msk &= msk - 1;
+            int64_t q0 = (int64_t)c * (cw >> 2);
+            int64_t q1 = q0 + (cw >> 2) < nq ? q0 + (cw >> 2) : nq;
+            for (int64_t q = q0 + lane; q < q1; q += 32) {
+                int4 c4 = row[q];
+                int cv[4] = {c4.x, c4.y, c4.z, c4.w};
 #pragma unroll
-            for (int u = 0; u < 4; u++) {
-                int32_t p = (int32_t)(4 * q + u);
-                int64_t g = (int64_t)cv[u] - T;
-                // default: positive gains only (bs starts at 0); variant: any
-                // adjacent partition (conn > 0), the first one found seeds bs
-                if (p < K && (g > bs || (nonpos && bk < 0 && cv[u] > 0)) && cv[u] > 0 &&
-                    p != own && ps.size[p] + sz <= omega &&
-                    ps.inpins[p] + ip <= phi && ps.pincnt[p] + ic - (int64_t)O[r0 + p] <= delta) {
-                    bs = g;
-                    bk = p;
+                for (int u = 0; u < 4; u++) {
+                    int32_t p = (int32_t)(4 * q + u);
+                    int64_t g = (int64_t)cv[u] - T;
+                    // default: positive gains only (bs starts at 0); variant:
+                    // any adjacent partition (conn > 0), the first one found
+                    // seeds bs
+                    if (p < K && (g > bs || (nonpos && bk < 0 && cv[u] > 0)) && cv[u] > 0 &&
+                        p != own && ps.size[p] + sz <= omega && ps.inpins[p] + ip <= phi &&
+                        ps.pincnt[p] + ic - (int64_t)O[r0 + p] <= delta) {
+                        bs = g;
+                        bk = p;
+                    }
                 }
             }
         }
@@ -532,7 +548,8 @@ __global__ void __launch_bounds__(256)
 __global__ void __launch_bounds__(256)
     k_dense_cross(Level L, PinCounts pc, const int32_t* __restrict__ moveidx, Moves mv,
                   const int64_t* __restrict__ scal, const int32_t* __restrict__ rowid, int32_t* C,
-                  int32_t* O, int64_t Kp, uint32_t* buf, HedgeList hl)
+                  int32_t* O, unsigned long long* M, int32_t cw, int64_t Kp, uint32_t* buf,
+                  HedgeList hl)
 {
     int64_t istar = scal[RS_BEST] > 0 ? scal[RS_ISTAR] : -1;
     if (istar < 0) return;
@@ -602,8 +619,10 @@ __global__ void __launch_bounds__(256)
                     int cs = __shfl_sync(FULL, rc[u], src);
                     int ds = __shfl_sync(FULL, rd[u], src);
                     for (int64_t j = b + lane; j < e; j += 32) {
-                        int64_t r = (int64_t)rowid[L.hpins[j]] * Kp + p;
+                        int32_t rw = rowid[L.hpins[j]];
+                        int64_t r = (int64_t)rw * Kp + p;
                         if (cs) atomicAdd(&C[r], (int32_t)(cs * w));
+                        if (cs > 0) atomicOr(&M[rw], 1ull << (p / cw));
                         if (ds && (j != b || sd)) atomicAdd(&O[r], ds * k);
                     }
                 }
@@ -649,13 +668,15 @@ __global__ void k_dense_rowid(int32_t V, int32_t Vc, const int32_t* __restrict__
 
 // clears the rows of vertices flagged fresh (one warp per vertex)
 __global__ void k_dense_zero(int32_t V, const int32_t* __restrict__ fresh,
-                             const int32_t* __restrict__ rowid, int32_t* C, int32_t* O, int64_t Kp)
+                             const int32_t* __restrict__ rowid, int32_t* C, int32_t* O,
+                             unsigned long long* M, int64_t Kp)
 {
     int lane = threadIdx.x & 31;
     int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t n = gw; n < V; n += nw) {
         if (!fresh[n]) continue;
+        if (lane == 0) M[rowid[n]] = 0;
         int4* c = reinterpret_cast<int4*>(C + (int64_t)rowid[n] * Kp);
         int4* o = reinterpret_cast<int4*>(O + (int64_t)rowid[n] * Kp);
         for (int64_t q = lane; q < Kp / 4; q += 32) {
@@ -1456,6 +1477,8 @@ static Status dense_fresh(snnmap_hgraph* h, Level& L, const PinCounts& pc)
     pol.C = D.C;
     pol.O = D.O;
     pol.Kp = D.Kp;
+    pol.M = D.M;
+    pol.cw = D.cw;
     int64_t* cnt;
     SNN_TRY(h->scratch.alloc(&cnt, HT_NCNT));
     return run_histogram(pol, h->scratch, h->stream, cnt, h->h_scal + 12, h->d_scal, h->tiers);
@@ -1482,6 +1505,9 @@ Status dense_open(snnmap_hgraph* h, int32_t K, int64_t rows)
     SNN_CUDA(dev_malloc(&D.rowid, (size_t)D.cap * 4, s));
     SNN_CUDA(dev_malloc(&D.rowid2, (size_t)D.cap * 4, s));
     SNN_CUDA(dev_malloc(&D.fresh, (size_t)D.cap * 4, s));
+    SNN_CUDA(dev_malloc(&D.M, (size_t)D.cap * 8, s));
+    D.cw = 32;
+    while ((int64_t)D.cw * 64 < D.Kp) D.cw <<= 1;
     D.level = -1;
     D.pending = false;
     return Status{};
@@ -1492,6 +1518,7 @@ void dense_close(snnmap_hgraph* h)
     DenseRows& D = h->dense;
     for (int32_t* p : {D.C, D.O, D.rowid, D.rowid2, D.fresh})
         if (p) cudaFreeAsync(p, h->stream);
+    if (D.M) cudaFreeAsync(D.M, h->stream);
     D = DenseRows{};
 }
 
@@ -1504,7 +1531,7 @@ Status dense_begin(snnmap_hgraph* h, int32_t level)
     SNN_TRY(fill_i32(D.fresh, 1, L.V, h->stream));
     if (L.V > 0) {
         SNN_L k_dense_zero<<<grid_for((int64_t)L.V * 32, 256), 256, 0, h->stream>>>(L.V, D.fresh, D.rowid,
-                                                                            D.C, D.O, D.Kp);
+                                                                            D.C, D.O, D.M, D.Kp);
         SNN_CUDA(cudaGetLastError());
     }
     D.level = level;
@@ -1538,7 +1565,7 @@ Status dense_descend(snnmap_hgraph* h, int32_t level)
         SNN_CUDA(cudaGetLastError());
         std::swap(D.rowid, D.rowid2);
         SNN_L k_dense_zero<<<grid_for((int64_t)L.V * 32, 256), 256, 0, s>>>(L.V, D.fresh, D.rowid, D.C,
-                                                                     D.O, D.Kp);
+                                                                     D.O, D.M, D.Kp);
         SNN_CUDA(cudaGetLastError());
     }
     D.level = level;
@@ -1795,8 +1822,8 @@ static Status refine_round(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* 
     if (dense) {
         if (V > 0) {
             SNN_L k_dense_best<<<grid_for((int64_t)V * 32, 256), 256, 0, s>>>(
-                L, rho, ps, savev, Wv, D.rowid, D.C, D.O, D.Kp, K, prm.omega, prm.delta, prm.phi,
-                prm.refine_nonpositive, pto, pgain, inc.dirty);
+                L, rho, ps, savev, Wv, D.rowid, D.C, D.O, D.M, D.cw, D.Kp, K, prm.omega, prm.delta,
+                prm.phi, prm.refine_nonpositive, pto, pgain, inc.dirty);
             SNN_CUDA(cudaGetLastError());
         }
     } else if (h->wide) {
@@ -1918,7 +1945,7 @@ static Status refine_round(snnmap_hgraph* h, int32_t level, int32_t K, int32_t* 
     if (dense && L.E > 0) {
         prof.reset(new ProfScope(h, PS_CROSS));
         SNN_L k_dense_cross<<<ghl, 256, 0, s>>>(L, pc, moveidx, mv, h->d_scal, D.rowid, D.C, D.O,
-                                                D.Kp, mvbuf, hl);
+                                                D.M, D.cw, D.Kp, mvbuf, hl);
         prof.reset(new ProfScope(h, PS_APPLY));
     }
     if (dense) {
