@@ -247,11 +247,20 @@ Status seg_classify(const int64_t* hoff, int32_t E, int32_t maxlen, SegBuckets& 
 // ---------------------------------------------------------------------------
 // incidence lists: degree count, scan, scatter with the source bit
 
+// Lanes of a warp holding the same vertex add their count once (consecutive
+// hyperedges of a coarse level share most of their super-nodes); the loop
+// runs over whole warps so the match covers all 32 lanes.
 __global__ void k_count_deg(const int32_t* __restrict__ pins, int64_t P, int32_t* deg)
 {
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < P;
-         j += (int64_t)gridDim.x * blockDim.x)
-        atomicAdd(&deg[pins[j]], 1);
+    int lane = threadIdx.x & 31;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); base < P;
+         base += stride) {
+        int64_t j = base + lane;
+        int32_t q = j < P ? pins[j] : -1;
+        unsigned same = __match_any_sync(FULL, q);
+        if (q >= 0 && lane == __ffs(same) - 1) atomicAdd(&deg[q], __popc(same));
+    }
 }
 
 // a group of G lanes per hyperedge

@@ -459,7 +459,8 @@ struct RowPol {
         int64_t r = (int64_t)row * Kp + p;
         C[r] = (int32_t)conn;
         O[r] = (int32_t)o;
-        atomicOr(&M[row], 1ull << (p / cw));
+        unsigned long long bit = 1ull << (p / cw);
+        if (!(M[row] & bit)) atomicOr(&M[row], bit);   // a set bit is never cleared here
     }
     __device__ void write(int32_t, int64_t, int32_t, uint32_t, const Acc&) const {}
 };
@@ -622,7 +623,8 @@ __global__ void __launch_bounds__(256)
                         int32_t rw = rowid[L.hpins[j]];
                         int64_t r = (int64_t)rw * Kp + p;
                         if (cs) atomicAdd(&C[r], (int32_t)(cs * w));
-                        if (cs > 0) atomicOr(&M[rw], 1ull << (p / cw));
+                        unsigned long long bit = 1ull << (p / cw);
+                        if (cs > 0 && !(M[rw] & bit)) atomicOr(&M[rw], bit);
                         if (ds && (j != b || sd)) atomicAdd(&O[r], ds * k);
                     }
                 }
