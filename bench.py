@@ -294,7 +294,7 @@ def cpu_baseline(warm=0, steps=1):
     t = statistics.median(times)
     host = host_cpu()
     return {"value": hg.P / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{SAMPLE_DESC}; P={hg.P}; {t:.2f} s per pass",
+            "sample": f"{SAMPLE_DESC}; P={hg.P}; {t:.2f} s per pass (median of {steps})",
             "s_per_pass": t, "pins": hg.P, "pinned_cpu": pin.cpu,
             "host_cpus": host["cpus"], "host_model": host["model"]}
 
@@ -502,7 +502,7 @@ def run_ours(args):
 
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cb = cpu_baseline()
+        cb = cpu_baseline(steps=3)   # median of three passes, ~13 s of one core
         cb = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample", "pinned_cpu",
                                  "host_cpus", "host_model")}
 
