@@ -360,7 +360,7 @@ int snnmap_peak_bytes(const snnmap_hgraph* h, int64_t* bytes);
  * Device memory of handles comes from one stream-ordered memory pool per
  * device that the library creates: memory a handle frees stays in the pool
  * for the next allocation of any handle, and the pool hands all of it back to
- * the driver when the last live handle is freed (and after
+ * the CUDA driver when the last live handle is freed (and after
  * snnmap_partition_host, snnmap_batch_partition or snnmap_serve_destroy when
  * no handle is live). NULL is ignored.
  */

@@ -146,7 +146,7 @@ struct Carver {
 
 // Device memory of a handle: stream-ordered allocations from one memory pool
 // per device that keeps freed blocks for reuse across stream
-// synchronizations. (The default pool hands unused memory back to the driver
+// synchronizations. (The default pool hands unused memory back to the CUDA driver
 // at every synchronization, so each level's and each refinement round's
 // arrays would be mapped afresh.) The pool is trimmed to nothing when the
 // last live handle is freed (pool_handles(-1) returns 0).
