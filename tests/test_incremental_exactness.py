@@ -230,3 +230,106 @@ def test_rows_of_unmatched_vertices_survive_projection(k):
             for p in range(int(rho1.max()) + 1 if a1["V"] else 0):
                 assert c0.get((n, p), 0) == c1.get((x, p), 0)
                 assert o0.get((n, p), 0) == o1.get((x, p), 0)
+
+
+# ---------------------------------------------------------------------------
+# 6. Proposal update after an enacted prefix (refinement rounds after a
+#    level's first). Moves between the partitions of P* (the sources and
+#    targets of the enacted moves) change no other partition's contents, so
+#    for a vertex n that did not move, a partition q outside P* keeps its
+#    feasibility for n and conn(n, q), and the gain of every move of n to a
+#    partition outside P* shifts by the same amount, the change of save(n)
+#    (gain = conn(n, q) - W(n) + save(n)). So n's best move after the round
+#    lies in {its previous proposal} + P*, unless n moved, its previous
+#    proposal pointed into P*, or it had none and its save grew.
+
+
+def _proposals(hg, rho, K, prm):
+    """Best feasible move of every vertex on the original neurons: gain as
+    the Conn it removes, ties to the lower partition; (-1, 0) if no move has
+    a positive gain."""
+    ins = bf.in_sets(hg)
+    axons = [({s} | d) for s, d, w in bf.hedges(hg) if d]
+    base = bf.conn(hg, rho)
+    members = {}
+    for n in range(hg.V):
+        members.setdefault(int(rho[n]), set()).add(n)
+    out = []
+    for n in range(hg.V):
+        adj = {int(rho[q]) for e in axons if n in e for q in e}
+        best = None
+        for p in sorted(adj):
+            if p == rho[n] or not bf.group_ok(hg, members.get(p, set()) | {n}, prm, ins):
+                continue
+            r2 = list(rho)
+            r2[n] = p
+            g = base - bf.conn(hg, r2)
+            if best is None or (g, -p) > best:
+                best = (g, -p)
+        out.append((-best[1], best[0]) if best is not None and best[0] > 0 else (-1, 0))
+    return out
+
+
+def _gain(hg, rho, n, p):
+    r2 = list(rho)
+    r2[n] = p
+    return bf.conn(hg, rho) - bf.conn(hg, r2)
+
+
+def _save(hg, rho, n):
+    """Summed weight of n's axons in which n is the only neuron of its partition."""
+    t = 0
+    for s, d, w in bf.hedges(hg):
+        if not d:
+            continue
+        e = {s} | d
+        if n in e and sum(1 for q in e if rho[q] == rho[n]) == 1:
+            t += w
+    return t
+
+
+@pytest.mark.parametrize("seed", range(60))
+def test_proposal_update_after_prefix(seed):
+    hg = snngen.tiny_random(5000 + seed, V=int(8 + seed % 9), E=int(10 + seed % 17))
+    ins = bf.in_sets(hg)
+    # limits every neuron meets alone, tight enough that some moves are refused
+    top = max(len(x) for x in ins)
+    prm = oracle.params(2 + seed % 3, top + seed % 4, 2 * top + seed % 7)
+    assert all(bf.group_ok(hg, {n}, prm, ins) for n in range(hg.V))
+    rho = list(range(hg.V))
+    K = hg.V
+    img = np.arange(hg.V)
+    props = _proposals(hg, rho, K, prm)
+    checked = 0
+    for _ in range(6):
+        rho1, n_props, istar, gain = bf.refine_round(hg, img, hg.V, rho, K, prm)
+        if istar == 0:
+            break
+        moved = {n for n in range(hg.V) if rho1[n] != rho[n]}
+        pstar = {rho[n] for n in moved} | {rho1[n] for n in moved}
+        props1 = _proposals(hg, rho1, K, prm)
+        for n in range(hg.V):
+            pto, g0 = props[n]
+            dsave = _save(hg, rho1, n) - _save(hg, rho, n)
+            if n in moved or pto in pstar or (pto < 0 and dsave > 0):
+                continue                                # rescanned in full
+            if pto >= 0:
+                assert _gain(hg, rho1, n, pto) == g0 + dsave
+            # the best of {previous proposal} + P*, positive gains only
+            best = None
+            for p in sorted(pstar | ({pto} if pto >= 0 else set())):
+                if p == rho1[n]:
+                    continue
+                if not any(rho1[q] == p for s, d, w in bf.hedges(hg) if d
+                           for e in [{s} | d] if n in e for q in e):
+                    continue                            # not adjacent
+                grp = {q for q in range(hg.V) if rho1[q] == p} | {n}
+                if not bf.group_ok(hg, grp, prm, ins):
+                    continue
+                g = _gain(hg, rho1, n, p)
+                if best is None or (g, -p) > best:
+                    best = (g, -p)
+            want = (-best[1], best[0]) if best is not None and best[0] > 0 else (-1, 0)
+            assert props1[n] == want, (n, props[n], props1[n], want, sorted(pstar))
+            checked += 1
+        rho, props = rho1, props1
